@@ -75,6 +75,28 @@ class ShiftInvert:
         return omega[o], X[:, o]
 
 
+    def left_eigs(self, k, ncv, v0=None, tol=1e-13, maxiter=10000):
+        """Left eigenvectors from ARPACK on the adjoint T^H = B^H (A - sigma B)^{-H}.
+
+        If T^H z = conj(mu) z then y = (A - sigma B)^{-H} z satisfies
+        y^H (A - omega B) = 0 with omega = sigma + 1/mu.  Returns (omega, Y)
+        sorted by |omega - sigma|.
+        """
+        n = self.B.shape[0]
+        mv = lambda z: self.B.conj().T @ sla.lu_solve(self.lu, z, trans=2, check_finite=False)
+        op = spla.LinearOperator((n, n), matvec=mv, dtype=np.complex128)
+        nu_, Z = spla.eigs(op, k=k, which="LM", v0=v0, ncv=ncv, tol=tol, maxiter=maxiter)
+        Y = np.stack([sla.lu_solve(self.lu, Z[:, i], trans=2, check_finite=False) for i in range(k)], axis=1)
+        omega = self.sigma + 1.0 / nu_.conj()
+        o = np.argsort(np.abs(omega - self.sigma), kind="stable")
+        return omega[o], Y[:, o]
+
+
+def condition_numbers(B, X, Y):
+    """kappa_i = ||x_i|| ||y_i|| / |y_i^H B x_i| for paired right/left eigenvectors."""
+    return np.linalg.norm(X, axis=0) * np.linalg.norm(Y, axis=0) / np.abs(np.sum(Y.conj() * (B @ X), axis=0))
+
+
 def residuals(spec, data, omega, X):
     """||A x - omega B x||_2 / ||x||_2 per column, with the matrix-free A and B."""
     X = np.asarray(X).reshape(X.shape[0], -1)
