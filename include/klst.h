@@ -1,0 +1,191 @@
+/*
+ * klst.h -- C ABI of the B300 kLST shift-and-invert eigensolver.
+ *
+ * The library computes eigenpairs of the kinetic linear-stability pencil
+ *     A q = omega B q                               (Sec. 4, Eq. MatrixProblem)
+ * of the linearised Boltzmann-BGK equations for a 1-D normal shock: the
+ * perturbed reduced distributions q = [g^; h^] are discretised by mapped
+ * Chebyshev collocation in x (Sec. 3.1) and Gauss-Hermite micro-velocity nodes
+ * (Sec. 3.2); the rows are Eqs. comp_ghat1Dshock / comp_hhat1Dshock with the
+ * inflow boundary rows of Sec. 2.2.  omega is the paper's i*varpi.
+ *
+ * Unknown ordering: q[(c * Nxi + k) * Nx + j], component c in {g^, h^},
+ * micro-velocity node k = kx * qy + ky, collocation point j (fastest).
+ * Complex numbers are interleaved (re, im) float64 pairs (C99 double complex,
+ * cuDoubleComplex, torch.complex128) unless stated otherwise.
+ *
+ * Conventions
+ *  - Every call returns an int status (klst_status); no exception crosses the ABI.
+ *  - Handles (klst_pencil, klst_factor, klst_batch, klst_server) own their device
+ *    memory.  The caller owns every buffer it passes.  A failed create call
+ *    leaves *out == NULL and frees what it allocated.
+ *  - "device" buffers are CUDA global-memory pointers on the current device;
+ *    "host" buffers are ordinary host memory.
+ *  - Calls are ordered on the given stream (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls documented as synchronising wait for the stream.
+ *  - Handles are not thread-safe; klst_server_* is internally locked.
+ *  - klst_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef KLST_H
+#define KLST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* klst_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    KLST_OK = 0,
+    KLST_EINVAL = -1,     /* bad argument (sizes, NULL pointers, unsupported shape) */
+    KLST_ENOMEM = -2,     /* device allocation failed */
+    KLST_ESINGULAR = -3,  /* zero pivot: a shifted block or the capacitance matrix is singular */
+    KLST_ENOCONV = -4,    /* eigensolver reached max_restarts before nev pairs converged */
+    KLST_EREFINE = -5,    /* mixed-precision refinement did not reach its tolerance */
+    KLST_ETIMEOUT = -6,   /* a bounded device-side wait gave up (grid barrier) */
+    KLST_ECUDA = -7       /* a CUDA runtime call failed */
+} klst_status;
+
+typedef enum { KLST_FP64 = 0, KLST_MIXED = 1 } klst_precision;
+typedef enum { KLST_BASE_TANH_MAXWELL = 0, KLST_BASE_MOTT_SMITH = 1 } klst_base;
+
+/* Pencil description (all nondimensional: T by T_inf, rho by rho_inf, velocity by
+ * sqrt(2 R T_inf), length by the shock thickness; Sec. 2.2). */
+typedef struct {
+    int32_t nx;          /* Chebyshev-Gauss-Lobatto points (N + 1), 4 <= nx <= 128 */
+    int32_t qx, qy;      /* Gauss-Hermite nodes in xi_x and xi_y, 1..256 each */
+    double map_L;        /* algebraic map length scale L (Eq. Chebmapping) */
+    double map_sinf;     /* domain half-width s_inf (Eq. Chebmapping) */
+    double mach;         /* free-stream Mach number */
+    double gamma;        /* ratio of specific heats (5/3 for argon) */
+    double visc_s;       /* viscosity exponent s in mu ~ T^s */
+    double re_delta;     /* Reynolds number on the shock thickness */
+    double beta;         /* transverse wavenumber (normal-mode ansatz, Sec. 2.2) */
+    double width;        /* tanh width of the synthetic base flow */
+    int32_t base;        /* klst_base */
+    int32_t noneq;       /* 0: EQ (f_c := f_c^e), 1: NONEQ base flow */
+    int32_t conservative;/* 1: discrete-conservative equilibrium and coefficients */
+} klst_pencil_desc;
+
+typedef struct {
+    int32_t nev;          /* eigenpairs wanted (nearest sigma), >= 1 */
+    int32_t ncv;          /* Krylov basis size, nev + 2 <= ncv <= 160 */
+    int32_t max_restarts; /* Krylov-Schur restarts before KLST_ENOCONV */
+    int32_t max_refine;   /* mixed precision: refinement sweeps per solve (>= 0) */
+    double tol;           /* Ritz residual tolerance relative to |mu| */
+    double refine_tol;    /* mixed precision: target ||r|| / ||rhs|| of each solve */
+    const void* v0;       /* device complex128 start vector (length n) or NULL */
+    uint64_t seed;        /* start vector seed when v0 == NULL */
+} klst_eigs_opts;
+
+typedef struct {
+    int32_t nconv;        /* converged pairs returned (<= nev) */
+    int32_t restarts;     /* Krylov-Schur restarts performed */
+    int32_t applies;      /* shift-invert operator applications */
+    int32_t refine_sweeps;/* refinement sweeps executed in total (mixed) */
+    double t_factor_ms;   /* time of klst_factor_shift for this factor */
+    double t_eigs_ms;     /* wall time of the eigs call */
+    double max_resid;     /* max explicit ||A q - omega B q|| over returned pairs, ||q|| = 1 */
+    double max_refine_resid; /* worst final relative refinement residual (mixed) */
+} klst_eigs_info;
+
+typedef struct klst_pencil_s* klst_pencil;
+typedef struct klst_factor_s* klst_factor;
+
+/* Status text ("KLST_OK", ...) and the calling thread's last error message. */
+const char* klst_status_string(int status);
+const char* klst_last_error(void);
+
+/*
+ * klst_build_pencil -- assemble the structured pencil on the device (Sec. 2.2, 3.1, 3.2).
+ * Builds the Gauss-Hermite grid (Golub-Welsch nodes, full-line weights), the mapped
+ * Chebyshev derivative D_x = diag(dy/dx) D_y, the synthetic base flow, its discrete
+ * moments and equilibrium, the moment functionals w^c_a(j,k), the coupling
+ * coefficients G^c_a(j,k) of Eq. Comp1DHarm and the inflow boundary mask.
+ * desc: host.  Errors: KLST_EINVAL for out-of-range sizes, KLST_ENOMEM.
+ * Synchronising (the handle is usable on any stream afterwards).
+ */
+int klst_build_pencil(const klst_pencil_desc* desc, klst_stream stream, klst_pencil* out);
+void klst_pencil_destroy(klst_pencil p);
+
+/* Sizes: n = 2 nx nxi unknowns; footprint = device bytes the handle owns. Any out may be NULL. */
+int klst_pencil_dims(klst_pencil p, int64_t* n, int32_t* nx, int32_t* nxi, int64_t* footprint_bytes);
+
+/*
+ * klst_pencil_tables -- copy the assembled tables to host float64 buffers (tests, diagnostics).
+ * x[nx], Dx[nx*nx] (row-major), xi_x[nxi], xi_y[nxi], W[nxi], nu[nx],
+ * G[nxi*2*4*nx] and w[nxi*2*4*nx] (index ((k*2 + c)*4 + a)*nx + j), bc[nx*nxi] (j*nxi + k, 1 = inflow row).
+ * Any pointer may be NULL.  Synchronising.
+ */
+int klst_pencil_tables(klst_pencil p, double* x, double* Dx, double* xi_x, double* xi_y, double* W,
+                       double* nu, double* G, double* w, uint8_t* bc);
+
+/*
+ * klst_export_dense -- write the dense pencil to host memory (n <= 16384):
+ * A_host[n*n] = A - sigma B (row-major complex128), B_host[n] = diag(B) as float64 (0/1).
+ * Either pointer may be NULL.  Synchronising.
+ */
+int klst_export_dense(klst_pencil p, double sigma_re, double sigma_im, double* A_host, double* B_host);
+
+/*
+ * klst_apply_pencil -- y[:, r] = (A - omega_r B) x[:, r] in float64 without forming A
+ * (the residual operator of Eq. MatrixProblem).  x, y: device complex128, n x nrhs
+ * column-major (column stride n); omega: host complex128[nrhs] (NULL = all zero).
+ */
+int klst_apply_pencil(klst_pencil p, const void* x, void* y, int32_t nrhs, const double* omega,
+                      klst_stream stream);
+
+/*
+ * klst_factor_shift -- factor A - sigma B for the shift-and-invert transform
+ * (Eqs. parShiftInvert, parLUfactor).  A - sigma B = K - U V^H where K is block
+ * diagonal with one Nx x Nx block per node k (xi_x,k D_x + nu + i beta xi_y,k - sigma,
+ * inflow rows replaced by identity rows; shared by g^ and h^) and U V^H is the
+ * rank-4-per-point BGK moment coupling.  Computes every K_k^{-1} (batched
+ * Gauss-Jordan with partial pivoting), the capacitance C = I - V^H K^{-1} U
+ * (4 Nx x 4 Nx) and C^{-1}.  precision: KLST_FP64 (all float64) or KLST_MIXED
+ * (K_k^{-1} in complex float32, corrected by float64 refinement in the apply).
+ * Errors: KLST_ESINGULAR (zero pivot), KLST_ENOMEM, KLST_ETIMEOUT.  Synchronising.
+ */
+int klst_factor_shift(klst_pencil p, double sigma_re, double sigma_im, int32_t precision,
+                      klst_stream stream, klst_factor* out);
+void klst_factor_destroy(klst_factor f);
+
+/* Factor metadata: the pencil it belongs to, its shift and precision; any out may be NULL. */
+int klst_factor_info(klst_factor f, double* sigma_re, double* sigma_im, int32_t* precision,
+                     int64_t* footprint_bytes, double* t_factor_ms);
+
+/*
+ * klst_apply_shift_invert -- y = (A - sigma B)^{-1} B x  (the operator T of Eq. parShiftInvert).
+ * x, y: device complex128, n x nrhs column-major, may not alias.  Woodbury form:
+ * z = K^{-1} B x, s = C^{-1} V^H z, y = K^{-1} (B x + U s).  MIXED factors run the two
+ * block solves in complex float32 and then max_refine sweeps of float64 iterative
+ * refinement y += T~ (B x - (A - sigma B) y) (stopping early at refine_tol).
+ * Stream-ordered, not synchronising.
+ */
+int klst_apply_shift_invert(klst_factor f, const void* x, void* y, int32_t nrhs, klst_stream stream);
+
+/* Refinement controls for klst_apply_shift_invert on MIXED factors (defaults 3 and 1e-14). */
+int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol);
+
+/*
+ * klst_eigs -- the nev eigenvalues nearest sigma by Krylov-Schur restarted Arnoldi on T
+ * (Sec. 4.1: implicitly restarted Arnoldi with shift-and-invert), with classical
+ * Gram-Schmidt plus one reorthogonalisation in float64 and the small Schur/reorder
+ * step in float64 on the device.  Eigenvalues omega = sigma + 1/mu are returned
+ * nearest-first in evals_host (host complex128[nev]); evecs (device complex128,
+ * n x nev column-major, may be NULL) receive unit-norm purified eigenvectors
+ * q = T x / ||T x||; resid_host (host float64[nev], may be NULL) receives
+ * ||A q - omega B q||_2.  info may be NULL.
+ * Errors: KLST_ENOCONV (fewer than nev converged; the converged ones are still
+ * returned and info->nconv says how many), KLST_EINVAL.  Synchronising.
+ */
+int klst_eigs(klst_factor f, const klst_eigs_opts* opts, double* evals_host, void* evecs,
+              double* resid_host, klst_eigs_info* info, klst_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KLST_H */

@@ -1,0 +1,152 @@
+// Internal helpers shared by the kLST CUDA sources (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "klst.h"
+
+namespace klst {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define KLST_CK(call)                                                            \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) return ::klst::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define KLST_CK_LAUNCH() KLST_CK(cudaGetLastError())
+
+// device status bits (klst::Status::flags)
+enum : int {
+    ST_SINGULAR = 1,   // zero pivot in a block or capacitance inverse
+    ST_TIMEOUT = 2,    // bounded grid barrier gave up
+    ST_NOCONV_QR = 4,  // small Schur QR iteration limit
+    ST_BREAKDOWN = 8   // Arnoldi breakdown (invariant subspace)
+};
+
+// ------------------------------------------------------------------ complex arithmetic
+template <typename T> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float> { using type = float2; };
+
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mkf(float a, float b) { return make_float2(a, b); }
+
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a) { return mk(-a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double2 b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return mk(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double2 conj(double2 a) { return mk(a.x, -a.y); }
+__host__ __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double2 cinv(double2 a) {
+    double d = 1.0 / abs2(a);
+    return mk(a.x * d, -a.y * d);
+}
+// a += b * c
+__host__ __device__ __forceinline__ void cfma(double2& a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, a.x); a.x = fma(-b.y, c.y, a.x);
+    a.y = fma(b.x, c.y, a.y); a.y = fma(b.y, c.x, a.y);
+}
+// a += conj(b) * c
+__host__ __device__ __forceinline__ void cfma_conj(double2& a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, a.x); a.x = fma(b.y, c.y, a.x);
+    a.y = fma(b.x, c.y, a.y); a.y = fma(-b.y, c.x, a.y);
+}
+
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return mkf(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return mkf(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a) { return mkf(-a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+    return mkf(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float2 cinv(float2 a) {
+    float d = 1.0f / abs2(a);
+    return mkf(a.x * d, -a.y * d);
+}
+__host__ __device__ __forceinline__ void cfma(float2& a, float2 b, float2 c) {
+    a.x = fmaf(b.x, c.x, a.x); a.x = fmaf(-b.y, c.y, a.x);
+    a.y = fmaf(b.x, c.y, a.y); a.y = fmaf(b.y, c.x, a.y);
+}
+
+template <typename C> __device__ __forceinline__ C to_c(double2 v);
+template <> __device__ __forceinline__ double2 to_c<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_c<float2>(double2 v) { return mkf((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return mk(v.x, v.y); }
+
+// ------------------------------------------------------------------ handles
+struct Status {            // device-resident status word
+    int flags;
+    int pad[31];
+};
+
+}  // namespace klst
+
+struct klst_pencil_s {
+    klst_pencil_desc desc;
+    int nx, nxi, qx, qy;
+    int64_t n;
+    // device tables (float64)
+    double* x;      // [nx] mapped collocation points (j = 0 is +s_inf)
+    double* Dx;     // [nx*nx] row-major D_x
+    double* DxT;    // [nx*nx] column-major D_x (DxT[m*nx + j] = D_x[j][m])
+    double* xi_x;   // [nxi]
+    double* xi_y;   // [nxi]
+    double* W;      // [nxi] full-line product weights
+    double* nu;     // [nx] collision frequency P/mu
+    double* macro;  // [4*nx] rho, u, E, T of the base state
+    double* G;      // [((k*2 + c)*4 + a)*nx + j] coupling coefficients (zero on inflow rows)
+    double* w;      // [((k*2 + c)*4 + a)*nx + j] moment functionals
+    klst::Status* status;
+    int64_t footprint;
+};
+
+namespace klst {
+
+// inflow boundary row test (Sec. 2.2): j = nx-1 (x = -s_inf) with xi_x > 0, j = 0 (x = +s_inf) with xi_x < 0
+__host__ __device__ __forceinline__ bool is_bc(int j, int nx, double xix) {
+    return (j == nx - 1 && xix > 0.0) || (j == 0 && xix < 0.0);
+}
+
+// bounded, sense-reversing grid barrier for cooperative launches; returns false on timeout
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks,
+                                             int* flags) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = gen;
+        unsigned int my = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == my) {
+                if (++spins > (1ll << 24)) { atomicOr(flags, ST_TIMEOUT); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)flags & ST_TIMEOUT) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+int device_sm_count();
+
+}  // namespace klst

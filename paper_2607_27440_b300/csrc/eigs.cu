@@ -1,0 +1,386 @@
+// Krylov-Schur restarted Arnoldi on T = (A - sigma B)^{-1} B (Sec. 4.1, Eq. parShiftInvert):
+// basis expansion with the shift-invert apply, classical Gram-Schmidt with one
+// reorthogonalisation in float64 (the paper's -bv_orthog_type cgs plus the standard DGKS pass),
+// the float64 Schur restart (schur.cu), basis rotation, purification and explicit residuals.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "factor.cuh"
+
+namespace klst {
+
+
+// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]
+__global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ w,
+                       int64_t n, int chunk, double2* __restrict__ part, int ldp) {
+    extern __shared__ double2 sw[];
+    const int64_t r0 = (int64_t)blockIdx.x * chunk;
+    const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) sw[i] = w[r0 + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int col = wid; col < ncols; col += nw) {
+        const double2* vc = V + col * ldv + r0;
+        double2 a = mk(0, 0);
+        for (int i = lane; i < len; i += 32) cfma_conj(a, vc[i], sw[i]);
+        for (int o = 16; o > 0; o >>= 1) {
+            a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+            a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+        }
+        if (lane == 0) part[(size_t)blockIdx.x * ldp + col] = a;
+    }
+}
+
+// h[col] (+)= sum_chunk part[chunk][col]  (fixed order)
+__global__ void k_dots_reduce(const double2* __restrict__ part, int nchunks, int ncols, int ldp, double2* h, int add) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    double2 s = mk(0, 0);
+    for (int c = 0; c < nchunks; ++c) s = s + part[(size_t)c * ldp + col];
+    h[col] = add ? h[col] + s : s;
+}
+
+// w -= V h (ncols columns); optional per-block partial of |w|^2
+__global__ void k_update(const double2* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ h,
+                         double2* __restrict__ w, int64_t n, double* __restrict__ npart) {
+    extern __shared__ double2 sh[];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x) sh[i] = h[i];
+    __syncthreads();
+    double nrm = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc = w[i];
+        for (int c = 0; c < ncols; ++c) {
+            const double2 v = V[c * ldv + i], hc = sh[c];
+            acc.x -= v.x * hc.x - v.y * hc.y;
+            acc.y -= v.x * hc.y + v.y * hc.x;
+        }
+        w[i] = acc;
+        nrm += abs2(acc);
+    }
+    if (npart) {
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        __shared__ double red[32];
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+            npart[blockIdx.x] = s;
+        }
+    }
+}
+
+// column norm partials: npart[col * nblk + b]
+__global__ void k_colnorm_part(const double2* __restrict__ X, int64_t ldx, int64_t n, double* __restrict__ npart) {
+    const int col = blockIdx.y;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += abs2(X[col * ldx + i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q];
+        npart[(size_t)col * gridDim.x + blockIdx.x] = a;
+    }
+}
+
+__global__ void k_colnorm_fin(const double* __restrict__ npart, int nblk, int ncols, double* __restrict__ nrm) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    double s = 0;
+    for (int b = 0; b < nblk; ++b) s += npart[(size_t)col * nblk + b];
+    nrm[col] = sqrt(s);
+}
+
+// Finish the Arnoldi column j: S[0..j, j] = h1 + h2, S[j+1, j] = beta = ||w||; stores beta.
+__global__ void k_finish_col(const double* __restrict__ npart, int nblk, const double2* __restrict__ h, int j,
+                             double2* __restrict__ S, int lds, double* __restrict__ beta_out, Status* st) {
+    __shared__ double red[32];
+    double s = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += npart[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q];
+        const double beta = sqrt(a);
+        double hn = 0;
+        for (int i = 0; i <= j; ++i) hn += abs2(h[i]);
+        if (!(beta > 1e-13 * sqrt(hn))) atomicOr(&st->flags, ST_BREAKDOWN);
+        S[(size_t)j * lds + j + 1] = mk(beta, 0.0);
+        *beta_out = beta;
+    }
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) S[(size_t)j * lds + i] = h[i];
+}
+
+// x *= 1 / scale[col] (column-wise)
+__global__ void k_scale_cols(double2* __restrict__ X, int64_t ldx, int64_t n, const double* __restrict__ scale) {
+    const int col = blockIdx.y;
+    const double sc = scale[col];
+    const double inv = sc > 0 ? 1.0 / sc : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = X[col * ldx + i];
+        X[col * ldx + i] = mk(v.x * inv, v.y * inv);
+    }
+}
+
+// Vout[:, c] = sum_l V[:, l] Q[l, c] for c < ncol (8 output columns per block.y)
+__global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ V, int64_t ldv, int m,
+                                                const double2* __restrict__ Q, int ldq, int ncol,
+                                                double2* __restrict__ Vout, int64_t ldo, int64_t n) {
+    extern __shared__ double2 sq[];  // [m][8]
+    const int c0 = blockIdx.y * 8;
+    for (int idx = threadIdx.x; idx < m * 8; idx += blockDim.x) {
+        const int l = idx / 8, c = idx % 8;
+        sq[idx] = (c0 + c < ncol) ? Q[(size_t)(c0 + c) * ldq + l] : mk(0, 0);
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = mk(0, 0);
+        for (int l = 0; l < m; ++l) {
+            const double2 v = V[l * ldv + i];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cfma(acc[c], v, sq[l * 8 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c0 + c < ncol) Vout[(c0 + c) * ldo + i] = acc[c];
+    }
+}
+
+// Seeded complex Gaussian start vector (splitmix64 counter hash + Box-Muller).
+__device__ __forceinline__ uint64_t splitmix(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void k_randn(double2* x, int64_t n, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = splitmix(seed * 0x100000001b3ull + 2 * i), b = splitmix(seed * 0x100000001b3ull + 2 * i + 1);
+        const double u1 = ((a >> 11) + 0.5) * (1.0 / 9007199254740992.0), u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+        const double r = sqrt(-2.0 * log(u1));
+        x[i] = mk(r * cospi(2.0 * u2), r * sinpi(2.0 * u2));
+    }
+}
+
+struct EigsWork {
+    double2 *Va = nullptr, *Vb = nullptr, *S = nullptr, *H = nullptr, *Q = nullptr, *Yc = nullptr, *mu = nullptr;
+    double2 *h = nullptr, *dpart = nullptr, *X = nullptr, *Z = nullptr, *R = nullptr, *om = nullptr;
+    double2 *mw = nullptr, *mp = nullptr;
+    double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
+    int* nconv = nullptr;
+    void release() {
+        void* b[] = {Va, Vb, S, H, Q, Yc, mu, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
+        for (void* p : b) cudaFree(p);
+    }
+};
+
+}  // namespace klst
+
+using namespace klst;
+
+extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_host, void* evecs, double* resid_host,
+                         klst_eigs_info* info, klst_stream stream) {
+    if (!f || !o || !evals_host) { set_error("invalid arguments to klst_eigs"); return KLST_EINVAL; }
+    const int nev = o->nev, m = o->ncv;
+    if (nev < 1 || m < nev + 2 || m > 160 || (int64_t)m + 1 > f->n || o->max_restarts < 0 || o->max_refine < 0 ||
+        !(o->tol > 0)) {
+        set_error("invalid eigs options nev=%d ncv=%d (need 1 <= nev, nev+2 <= ncv <= min(160, n-1))", nev, m);
+        return KLST_EINVAL;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    klst_pencil p = f->p;
+    const int64_t n = f->n;
+    const int lds = m + 1;
+    const int sms = device_sm_count();
+    int chunk = 256;
+    while ((n + chunk - 1) / chunk > 2 * sms && chunk < 2048) chunk *= 2;
+    const int nchunks = (int)((n + chunk - 1) / chunk);
+    const int nblk = std::min<int64_t>((n + 255) / 256, 4 * sms);
+    const int ng = pencil_work_groups(p);
+    const int keep = std::min(m - 1, nev + (m - nev) / 2);
+    const int prev_refine = f->max_refine;
+    const double prev_rtol = f->refine_tol;
+    f->max_refine = o->max_refine;
+    if (o->refine_tol > 0) f->refine_tol = o->refine_tol;
+    EigsWork W;
+    cudaError_t e;
+    int rc = KLST_OK;
+    auto fail = [&](int code) {
+        W.release();
+        f->max_refine = prev_refine;
+        f->refine_tol = prev_rtol;
+        return code;
+    };
+#define EALLOC(ptr, cnt)                                                                     \
+    if ((e = cudaMalloc((void**)&(ptr), sizeof(*(ptr)) * (size_t)(cnt))) != cudaSuccess)      \
+        return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    EALLOC(W.Va, n * (m + 1));
+    EALLOC(W.Vb, n * (m + 1));
+    EALLOC(W.S, (size_t)lds * m);
+    EALLOC(W.H, (size_t)m * m);
+    EALLOC(W.Q, (size_t)m * m);
+    EALLOC(W.Yc, (size_t)m * std::max(nev, 2));
+    EALLOC(W.mu, m);
+    EALLOC(W.est, m);
+    EALLOC(W.h, 2 * (m + 1));
+    EALLOC(W.dpart, (size_t)nchunks * (m + 1));
+    EALLOC(W.npart, (size_t)std::max(nblk, 1) * std::max(nev, 1) + 64);
+    EALLOC(W.beta, 4);
+    EALLOC(W.nrm, nev + 4);
+    EALLOC(W.nconv, 4);
+    EALLOC(W.om, nev);
+    EALLOC(W.mw, (size_t)4 * p->nx * nev);
+    EALLOC(W.mp, (size_t)4 * p->nx * ng * nev);
+#undef EALLOC
+    KLST_CK(cudaMemsetAsync(W.S, 0, sizeof(double2) * lds * m, s));
+    KLST_CK(cudaMemsetAsync(f->status, 0, sizeof(Status), s));
+    KLST_CK(cudaMemsetAsync(f->worst, 0, sizeof(double), s));
+    KLST_CK(cudaMemsetAsync(f->sweeps, 0, sizeof(int), s));
+    if ((rc = factor_reserve(f, std::max(nev, 1))) != KLST_OK) return fail(rc);
+    double2 *V = W.Va, *Valt = W.Vb;
+    // start: v0 (given or seeded), V[:,0] = T v0 / ||T v0|| (range of T: no B-null components)
+    double2* v0 = Valt;
+    if (o->v0) KLST_CK(cudaMemcpyAsync(v0, o->v0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+    else k_randn<<<nblk, 256, 0, s>>>(v0, n, o->seed);
+    int applies = 0;
+    if ((rc = apply_T(f, v0, V, 1, s)) != KLST_OK) return fail(rc);
+    ++applies;
+    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.npart);
+    k_colnorm_fin<<<1, 32, 0, s>>>(W.npart, nblk, 1, W.nrm);
+    k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm);
+    KLST_CK_LAUNCH();
+    int k = 0, restarts = 0, nconv = 0;
+    const size_t dots_smem = sizeof(double2) * chunk;
+    const size_t upd_smem = sizeof(double2) * (m + 1);
+    bool converged = false;
+    for (;;) {
+        for (int j = k; j < m; ++j) {
+            double2* vj = V + (int64_t)j * n;
+            double2* w = V + (int64_t)(j + 1) * n;
+            if ((rc = apply_T(f, vj, w, 1, s)) != KLST_OK) return fail(rc);
+            ++applies;
+            const int nc = j + 1;
+            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1);
+            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h, 0);
+            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, nullptr);
+            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1);
+            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0);
+            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h + (m + 1), w, n, W.npart);
+            k_dots_reduce<<<1, 192, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1);  // h1 += h2
+            k_finish_col<<<1, 256, 0, s>>>(W.npart, nblk, W.h, j, W.S, lds, W.beta, f->status);
+            k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(w, n, n, W.beta);
+            KLST_CK_LAUNCH();
+        }
+        SchurArgs a;
+        a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
+        a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.st = f->status;
+        if ((rc = launch_schur(a, s)) != KLST_OK) return fail(rc);
+        Status hst;
+        int hconv = 0;
+        KLST_CK(cudaMemcpyAsync(&hconv, W.nconv, sizeof(int), cudaMemcpyDeviceToHost, s));
+        KLST_CK(cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s));
+        KLST_CK(cudaStreamSynchronize(s));
+        if (hconv < 0 || (hst.flags & ST_NOCONV_QR)) { set_error("small Schur QR iteration did not converge"); return fail(KLST_ENOCONV); }
+        if (hst.flags & ST_BREAKDOWN) { set_error("Arnoldi breakdown (invariant subspace found)"); return fail(KLST_ENOCONV); }
+        nconv = hconv;
+        if (nconv >= nev) { converged = true; break; }
+        if (restarts >= o->max_restarts) break;
+        // rotate: V'[:, 0:keep] = V[:, 0:m] Q[:, 0:keep], V'[:, keep] = V[:, m]
+        {
+            dim3 grd(std::max(1, nblk / std::max(1, (keep + 7) / 8)), (keep + 7) / 8);
+            k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n);
+            KLST_CK_LAUNCH();
+            KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
+                                    cudaMemcpyDeviceToDevice, s));
+            std::swap(V, Valt);
+        }
+        k = keep;
+        ++restarts;
+    }
+    // Ritz vectors x_i = V Q y_i (nev columns), purification q_i = T x_i / ||T x_i||, residuals
+    const int nret = nev;
+    double2* X = Valt;                          // n x nev
+    double2* Z = Valt + (int64_t)nev * n;        // n x nev (needs 2 nev <= m + 1 columns)
+    double2* Rr = nullptr;
+    const bool room = 3 * nev <= m + 1;
+    if (!room) {
+        if ((e = cudaMalloc(&W.Z, sizeof(double2) * n * nev)) != cudaSuccess ||
+            (e = cudaMalloc(&W.R, sizeof(double2) * n * nev)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+        if (2 * nev > m + 1) {
+            if ((e = cudaMalloc(&W.X, sizeof(double2) * n * nev)) != cudaSuccess)
+                return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+            X = W.X;
+        }
+        Z = W.Z;
+        Rr = W.R;
+    } else {
+        Rr = Valt + (int64_t)2 * nev * n;
+    }
+    {
+        dim3 grd(std::max(1, nblk / std::max(1, (nret + 7) / 8)), (nret + 7) / 8);
+        k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Yc, m, nret, X, n, n);
+        KLST_CK_LAUNCH();
+    }
+    if ((rc = apply_T(f, X, Z, nret, s)) != KLST_OK) return fail(rc);
+    applies += nret;
+    k_colnorm_part<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.npart);
+    k_colnorm_fin<<<(nret + 63) / 64, 64, 0, s>>>(W.npart, nblk, nret, W.nrm);
+    k_scale_cols<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.nrm);
+    KLST_CK_LAUNCH();
+    std::vector<double2> mu(m);
+    KLST_CK(cudaMemcpyAsync(mu.data(), W.mu, sizeof(double2) * m, cudaMemcpyDeviceToHost, s));
+    KLST_CK(cudaStreamSynchronize(s));
+    std::vector<double2> om(nret);
+    for (int i = 0; i < nret; ++i) {
+        const double d = mu[i].x * mu[i].x + mu[i].y * mu[i].y;
+        om[i] = mk(f->sigma.x + mu[i].x / d, f->sigma.y - mu[i].y / d);
+    }
+    KLST_CK(cudaMemcpyAsync(W.om, om.data(), sizeof(double2) * nret, cudaMemcpyHostToDevice, s));
+    if ((rc = apply_pencil_dev(p, Z, Rr, nret, W.om, s, W.mw, W.mp, ng)) != KLST_OK) return fail(rc);
+    k_colnorm_part<<<dim3(nblk, nret), 256, 0, s>>>(Rr, n, n, W.npart);
+    k_colnorm_fin<<<(nret + 63) / 64, 64, 0, s>>>(W.npart, nblk, nret, W.nrm);
+    KLST_CK_LAUNCH();
+    std::vector<double> res(nret);
+    double worst = 0;
+    int sweeps = 0;
+    KLST_CK(cudaMemcpyAsync(res.data(), W.nrm, sizeof(double) * nret, cudaMemcpyDeviceToHost, s));
+    KLST_CK(cudaMemcpyAsync(&worst, f->worst, sizeof(double), cudaMemcpyDeviceToHost, s));
+    KLST_CK(cudaMemcpyAsync(&sweeps, f->sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (evecs) KLST_CK(cudaMemcpyAsync(evecs, Z, sizeof(double2) * n * nret, cudaMemcpyDeviceToDevice, s));
+    KLST_CK(cudaStreamSynchronize(s));
+    double maxres = 0;
+    for (int i = 0; i < nret; ++i) {
+        evals_host[2 * i] = om[i].x;
+        evals_host[2 * i + 1] = om[i].y;
+        if (resid_host) resid_host[i] = res[i];
+        maxres = std::max(maxres, res[i]);
+    }
+    if (info) {
+        info->nconv = converged ? nev : nconv;
+        info->restarts = restarts;
+        info->applies = applies;
+        info->refine_sweeps = sweeps;
+        info->t_factor_ms = f->t_factor_ms;
+        info->t_eigs_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        info->max_resid = maxres;
+        info->max_refine_resid = worst;
+    }
+    W.release();
+    f->max_refine = prev_refine;
+    f->refine_tol = prev_rtol;
+    if (!converged) { set_error("only %d of %d eigenpairs converged after %d restarts", nconv, nev, restarts); return KLST_ENOCONV; }
+    return KLST_OK;
+}

@@ -1,0 +1,398 @@
+// Shifted factorisation for the shift-and-invert transform (Eqs. parShiftInvert, parLUfactor),
+// restated for the structure of the kLST pencil: A - sigma B = K - U V^H with one Nx x Nx block
+// K_k per micro-velocity node (shared by g^ and h^) and the rank-4-per-point moment coupling.
+// K_k^{-1} by batched Gauss-Jordan with partial pivoting, the capacitance C = I - V^H K^{-1} U
+// and C^{-1} by a cooperative Gauss-Jordan over all SMs.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "factor.cuh"
+
+namespace klst {
+
+template <typename C> struct real_of;
+template <> struct real_of<double2> { using type = double; };
+template <> struct real_of<float2> { using type = float; };
+
+// One CTA per node k.  Builds M_k = xi_x,k D_x + diag(nu + i beta xi_y,k - sigma) with inflow rows
+// replaced by unit rows, inverts it in place by Gauss-Jordan with row pivoting, undoes the
+// pivoting by column swaps, and stores K_k^{-1} column-major: out[k][m][j] = (K_k^{-1})_{jm}.
+// The working matrix lives in shared memory when it fits, otherwise in the output slot.
+template <typename C>
+__global__ void __launch_bounds__(256) k_block_gj(int nx, int nxi, double beta, double2 sigma,
+                                                  const double* __restrict__ Dx, const double* __restrict__ xi_x,
+                                                  const double* __restrict__ xi_y, const double* __restrict__ nu,
+                                                  C* __restrict__ out, int use_smem, Status* st) {
+    using R = typename real_of<C>::type;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ C prow[128], pcol[128];
+    __shared__ R rv[8];
+    __shared__ int ri[8];
+    __shared__ int perm[128];
+    __shared__ int s_piv;
+    const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    C* A = use_smem ? (C*)dsm : out + (size_t)k * nx * nx;
+    const double xix = xi_x[k], xiy = xi_y[k];
+    for (int idx = tid; idx < nx * nx; idx += nt) {
+        int j = idx / nx, m = idx % nx;
+        double2 v;
+        if (is_bc(j, nx, xix)) v = mk(j == m ? 1.0 : 0.0, 0.0);
+        else {
+            v = mk(xix * Dx[j * nx + m], 0.0);
+            if (j == m) { v.x += nu[j] - sigma.x; v.y += beta * xiy - sigma.y; }
+        }
+        A[idx] = to_c<C>(v);
+    }
+    __syncthreads();
+    for (int p = 0; p < nx; ++p) {
+        // pivot search in column p, rows p..nx-1 (largest |a|^2, lowest row on ties)
+        R best = -1;
+        int bi = nx;
+        for (int i = p + tid; i < nx; i += nt) {
+            R v = abs2(A[i * nx + p]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            R ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            R b = rv[0];
+            int i0 = ri[0];
+            for (int w = 1; w < (nt >> 5); ++w)
+                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+            if (!(b > 0)) { atomicOr(&st->flags, ST_SINGULAR); }
+            s_piv = i0 < nx ? i0 : p;
+            perm[p] = s_piv;
+        }
+        __syncthreads();
+        const int r = s_piv;
+        if (r != p)
+            for (int c = tid; c < nx; c += nt) { C t = A[p * nx + c]; A[p * nx + c] = A[r * nx + c]; A[r * nx + c] = t; }
+        __syncthreads();
+        for (int c = tid; c < nx; c += nt) { prow[c] = A[p * nx + c]; pcol[c] = A[c * nx + p]; }
+        __syncthreads();
+        C inv = prow[p];
+        if (!(abs2(inv) > 0)) inv.x = 1;
+        inv = cinv(inv);
+        for (int idx = tid; idx < nx * nx; idx += nt) {
+            int i = idx / nx, c = idx % nx;
+            C v;
+            if (i == p) v = (c == p) ? inv : prow[c] * inv;
+            else {
+                C f = pcol[i] * inv;
+                v = (c == p) ? -f : A[idx] - f * prow[c];
+            }
+            A[idx] = v;
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, in reverse order
+    for (int p = nx - 1; p >= 0; --p) {
+        int q = perm[p];
+        if (q != p)
+            for (int i = tid; i < nx; i += nt) { C t = A[i * nx + p]; A[i * nx + p] = A[i * nx + q]; A[i * nx + q] = t; }
+        __syncthreads();
+    }
+    // store transposed (column-major)
+    C* O = out + (size_t)k * nx * nx;
+    if (use_smem) {
+        for (int idx = tid; idx < nx * nx; idx += nt) {
+            int m = idx / nx, j = idx % nx;
+            O[idx] = A[j * nx + m];
+        }
+    } else {
+        for (int idx = tid; idx < nx * nx; idx += nt) {
+            int j = idx / nx, m = idx % nx;
+            if (j < m) { C t = A[j * nx + m]; A[j * nx + m] = A[m * nx + j]; A[m * nx + j] = t; }
+        }
+    }
+}
+
+// Partial capacitance sums over a k range: Cp[s][(a,j)][(b,j')] = sum_k sum_c w^c_a(j,k) (K_k^{-1})_{jj'} G^c_b(j',k)
+template <typename C>
+__global__ void __launch_bounds__(256) k_cap_partial(int nx, int nxi, const C* __restrict__ KinvT,
+                                                     const double* __restrict__ G, const double* __restrict__ w,
+                                                     int kper, double2* __restrict__ Cp) {
+    const int j = blockIdx.x * 16 + threadIdx.x, jp = blockIdx.y * 16 + threadIdx.y, sp = blockIdx.z;
+    const int r = 4 * nx;
+    if (j >= nx || jp >= nx) return;
+    double2 acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = mk(0, 0);
+    const int k0 = sp * kper, k1 = min(nxi, k0 + kper);
+    for (int k = k0; k < k1; ++k) {
+        const double2 kin = to_d(KinvT[((size_t)k * nx + jp) * nx + j]);
+        const double* wk = w + (size_t)k * 8 * nx;
+        const double* Gk = G + (size_t)k * 8 * nx;
+        double wg[4], Gg[4], Gh[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { wg[a] = wk[a * nx + j]; Gg[a] = Gk[a * nx + jp]; Gh[a] = Gk[(4 + a) * nx + jp]; }
+        const double whE = wk[7 * nx + j];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                double cf = wg[a] * Gg[b] + (a == 3 ? whE * Gh[b] : 0.0);
+                acc[a * 4 + b].x = fma(cf, kin.x, acc[a * 4 + b].x);
+                acc[a * 4 + b].y = fma(cf, kin.y, acc[a * 4 + b].y);
+            }
+    }
+    double2* o = Cp + (size_t)sp * r * r;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) o[(size_t)(a * nx + j) * r + b * nx + jp] = acc[a * 4 + b];
+}
+
+__global__ void k_cap_reduce(int r, int nsplit, const double2* __restrict__ Cp, double2* __restrict__ Cm) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)r * r; idx += gridDim.x * (size_t)blockDim.x) {
+        double2 s = mk(0, 0);
+        for (int q = 0; q < nsplit; ++q) s = s + Cp[(size_t)q * r * r + idx];
+        const size_t i = idx / r, l = idx % r;
+        Cm[idx] = mk((i == l ? 1.0 : 0.0) - s.x, -s.y);
+    }
+}
+
+// Cooperative Gauss-Jordan inverse of an r x r complex128 matrix (row-major) over all CTAs.
+// Step p reads buffer p%2 and writes buffer (p+1)%2 (every entry is rewritten), so one grid
+// barrier per step suffices.  Every CTA repeats the pivot search on the same data, so all
+// agree on the pivot row without communication.  The final column un-permutation writes
+// buffer (r+1)%2.
+__global__ void __launch_bounds__(256) k_gj_coop(int r, double2* buf0, double2* buf1, unsigned int* bar,
+                                                 Status* st) {
+    extern __shared__ double2 sh[];
+    double2* prow = sh;       // pivot row
+    double2* rowp = sh + r;   // row p of the source (moves to the pivot row's slot)
+    int* perm = (int*)(sh + 2 * r);
+    __shared__ double rv[8];
+    __shared__ int ri[8];
+    __shared__ int s_piv;
+    const int tid = threadIdx.x, nt = blockDim.x, G = gridDim.x;
+    const int rows_per = (r + G - 1) / G;
+    const int r0 = blockIdx.x * rows_per, r1 = min(r, r0 + rows_per);
+    for (int p = 0; p < r; ++p) {
+        const double2* src = (p & 1) ? buf1 : buf0;
+        double2* dst = (p & 1) ? buf0 : buf1;
+        double best = -1;
+        int bi = r;
+        for (int i = p + tid; i < r; i += nt) {
+            double v = abs2(src[(size_t)i * r + p]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = rv[0];
+            int i0 = ri[0];
+            for (int w = 1; w < (nt >> 5); ++w)
+                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+            if (!(b > 0) && blockIdx.x == 0) atomicOr(&st->flags, ST_SINGULAR);
+            s_piv = i0 < r ? i0 : p;
+            perm[p] = s_piv;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        for (int c = tid; c < r; c += nt) { prow[c] = src[(size_t)piv * r + c]; rowp[c] = src[(size_t)p * r + c]; }
+        __syncthreads();
+        double2 inv = prow[p];
+        if (!(abs2(inv) > 0)) inv.x = 1;
+        inv = cinv(inv);
+        for (int idx = tid; idx < (r1 - r0) * r; idx += nt) {
+            const int i = r0 + idx / r, c = idx % r;
+            double2 v;
+            if (i == p) v = (c == p) ? inv : prow[c] * inv;
+            else {
+                const double2 sv = (i == piv) ? rowp[c] : src[(size_t)i * r + c];
+                const double2 f = ((i == piv) ? rowp[p] : src[(size_t)i * r + p]) * inv;
+                v = (c == p) ? -f : sv - f * prow[c];
+            }
+            dst[(size_t)i * r + c] = v;
+        }
+        if (!grid_barrier(bar, bar + 1, G, &st->flags)) return;
+    }
+    // column un-permutation: apply the swaps (p, perm[p]) for p = r-1..0 as a gather
+    int* idxmap = perm + r;
+    if (tid == 0) {
+        for (int c = 0; c < r; ++c) idxmap[c] = c;
+        for (int p = r - 1; p >= 0; --p) { int q = perm[p], t = idxmap[p]; idxmap[p] = idxmap[q]; idxmap[q] = t; }
+    }
+    __syncthreads();
+    const double2* fin = (r & 1) ? buf1 : buf0;
+    double2* res = (r & 1) ? buf0 : buf1;
+    for (int idx = tid; idx < (r1 - r0) * r; idx += nt) {
+        const int i = r0 + idx / r, c = idx % r;
+        res[(size_t)i * r + c] = fin[(size_t)i * r + idxmap[c]];
+    }
+}
+
+template <typename C>
+static int launch_block_gj(klst_factor f, cudaStream_t s) {
+    klst_pencil p = f->p;
+    const size_t bytes = sizeof(C) * p->nx * p->nx;
+    const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
+    if (use_smem) KLST_CK(cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    k_block_gj<C><<<p->nxi, 256, use_smem ? bytes : 0, s>>>(p->nx, p->nxi, p->desc.beta, f->sigma, p->Dx, p->xi_x,
+                                                           p->xi_y, p->nu, (C*)f->KinvT, use_smem, f->status);
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+
+template <typename C>
+static int launch_cap(klst_factor f, double2* Cp, int nsplit, cudaStream_t s) {
+    klst_pencil p = f->p;
+    const int kper = (p->nxi + nsplit - 1) / nsplit;
+    dim3 blk(16, 16), grd((p->nx + 15) / 16, (p->nx + 15) / 16, nsplit);
+    k_cap_partial<C><<<grd, blk, 0, s>>>(p->nx, p->nxi, (const C*)f->KinvT, p->G, p->w, kper, Cp);
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+
+int factor_reserve(klst_factor f, int nrhs) {
+    if (nrhs <= f->nrhs_cap) return KLST_OK;
+    cudaFree(f->tpart); cudaFree(f->t); cudaFree(f->sv); cudaFree(f->bwork); cudaFree(f->rwork);
+    cudaFree(f->normpart); cudaFree(f->done); cudaFree(f->sigma_dev);
+    f->sigma_dev = nullptr;
+    f->tpart = f->t = f->sv = f->bwork = f->rwork = nullptr;
+    f->normpart = nullptr;
+    f->done = nullptr;
+    f->nrhs_cap = 0;
+    const size_t r = f->r, n = f->n;
+    KLST_CK(cudaMalloc(&f->tpart, sizeof(double2) * nrhs * (size_t)f->ngroups * r));
+    KLST_CK(cudaMalloc(&f->t, sizeof(double2) * nrhs * r));
+    KLST_CK(cudaMalloc(&f->sv, sizeof(double2) * nrhs * r));
+    if (f->precision == KLST_MIXED) {
+        KLST_CK(cudaMalloc(&f->bwork, sizeof(double2) * nrhs * n));
+        KLST_CK(cudaMalloc(&f->rwork, sizeof(double2) * nrhs * n));
+    }
+    KLST_CK(cudaMalloc(&f->normpart, sizeof(double) * nrhs * 2 * 4096));
+    KLST_CK(cudaMalloc(&f->done, sizeof(int) * nrhs));
+    KLST_CK(cudaMalloc(&f->sigma_dev, sizeof(double2) * nrhs));
+    {
+        std::vector<double2> sg(nrhs, f->sigma);
+        KLST_CK(cudaMemcpy(f->sigma_dev, sg.data(), sizeof(double2) * nrhs, cudaMemcpyHostToDevice));
+    }
+    f->nrhs_cap = nrhs;
+    return KLST_OK;
+}
+
+}  // namespace klst
+
+using namespace klst;
+
+extern "C" void klst_factor_destroy(klst_factor f) {
+    if (!f) return;
+    cudaFree(f->KinvT); cudaFree(f->Cinv);
+    cudaFree(f->tpart); cudaFree(f->t); cudaFree(f->sv); cudaFree(f->bwork); cudaFree(f->rwork);
+    cudaFree(f->normpart); cudaFree(f->done); cudaFree(f->sigma_dev); cudaFree(f->worst); cudaFree(f->sweeps); cudaFree(f->status);
+    delete f;
+}
+
+extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t precision, klst_stream stream,
+                                 klst_factor* out) {
+    if (!out) { set_error("out is NULL"); return KLST_EINVAL; }
+    *out = nullptr;
+    if (!p || (precision != KLST_FP64 && precision != KLST_MIXED)) { set_error("invalid factor arguments"); return KLST_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    klst_factor f = new klst_factor_s();
+    memset(f, 0, sizeof(*f));
+    f->p = p;
+    f->sigma = mk(sr, si);
+    f->precision = precision;
+    f->nx = p->nx; f->nxi = p->nxi; f->r = 4 * p->nx; f->n = p->n;
+    f->ngroups = pencil_work_groups(p);
+    f->max_refine = 3;
+    f->refine_tol = 1e-14;
+    const int r = f->r;
+    const size_t esz = precision == KLST_FP64 ? sizeof(double2) : sizeof(float2);
+    const int nsplit = std::max(1, std::min(p->nxi, 8));
+    double2 *Cp = nullptr, *b0 = nullptr, *b1 = nullptr;
+    unsigned int* bar = nullptr;
+    auto fail = [&](int code) {
+        cudaFree(Cp); cudaFree(b0); cudaFree(b1); cudaFree(bar);
+        klst_factor_destroy(f);
+        return code;
+    };
+    cudaError_t e;
+#define FALLOC(ptr, bytes)                                                                       \
+    if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__)); \
+    f->footprint += (int64_t)(bytes);
+    FALLOC(f->KinvT, esz * (size_t)p->nxi * p->nx * p->nx);
+    FALLOC(f->Cinv, sizeof(double2) * (size_t)r * r);
+    FALLOC(f->worst, sizeof(double));
+    FALLOC(f->sweeps, sizeof(int));
+    FALLOC(f->status, sizeof(Status));
+#undef FALLOC
+    if ((e = cudaMalloc(&Cp, sizeof(double2) * (size_t)nsplit * r * r)) != cudaSuccess ||
+        (e = cudaMalloc(&b0, sizeof(double2) * (size_t)r * r)) != cudaSuccess ||
+        (e = cudaMalloc(&b1, sizeof(double2) * (size_t)r * r)) != cudaSuccess ||
+        (e = cudaMalloc(&bar, sizeof(unsigned int) * 2)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    cudaMemsetAsync(f->status, 0, sizeof(Status), s);
+    cudaMemsetAsync(f->worst, 0, sizeof(double), s);
+    cudaMemsetAsync(f->sweeps, 0, sizeof(int), s);
+    cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 2, s);
+    int rc = precision == KLST_FP64 ? launch_block_gj<double2>(f, s) : launch_block_gj<float2>(f, s);
+    if (rc) return fail(rc);
+    rc = precision == KLST_FP64 ? launch_cap<double2>(f, Cp, nsplit, s) : launch_cap<float2>(f, Cp, nsplit, s);
+    if (rc) return fail(rc);
+    k_cap_reduce<<<std::min(1024, (r * r + 255) / 256), 256, 0, s>>>(r, nsplit, Cp, b0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "cap reduce", __FILE__, __LINE__));
+    {
+        int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
+        size_t smem = sizeof(double2) * 2 * r + sizeof(int) * 2 * r;
+        int rr = r;
+        double2 *pb0 = b0, *pb1 = b1;
+        Status* pst = f->status;
+        void* args[] = {&rr, &pb0, &pb1, &bar, &pst};
+        e = cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3(nb), dim3(256), args, smem, s);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cooperative capacitance inverse", __FILE__, __LINE__));
+    }
+    double2* res = (r & 1) ? b0 : b1;
+    if ((e = cudaMemcpyAsync(f->Cinv, res, sizeof(double2) * (size_t)r * r, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return fail(cuda_fail(e, "copy Cinv", __FILE__, __LINE__));
+    Status hst;
+    if ((e = cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(cuda_fail(e, "factor sync", __FILE__, __LINE__));
+    cudaFree(Cp); cudaFree(b0); cudaFree(b1); cudaFree(bar);
+    Cp = b0 = b1 = nullptr;
+    bar = nullptr;
+    if (hst.flags & ST_TIMEOUT) { set_error("capacitance inverse: grid barrier timed out"); return fail(KLST_ETIMEOUT); }
+    if (hst.flags & ST_SINGULAR) {
+        set_error("zero pivot: a shifted block K_k - sigma or the capacitance matrix is singular");
+        return fail(KLST_ESINGULAR);
+    }
+    if ((rc = factor_reserve(f, 1)) != KLST_OK) return fail(rc);
+    f->t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = f;
+    return KLST_OK;
+}
+
+extern "C" int klst_factor_info(klst_factor f, double* sr, double* si, int32_t* prec, int64_t* fp, double* tms) {
+    if (!f) { set_error("factor is NULL"); return KLST_EINVAL; }
+    if (sr) *sr = f->sigma.x;
+    if (si) *si = f->sigma.y;
+    if (prec) *prec = f->precision;
+    if (fp) *fp = f->footprint;
+    if (tms) *tms = f->t_factor_ms;
+    return KLST_OK;
+}
+
+extern "C" int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol) {
+    if (!f || max_refine < 0 || !(refine_tol >= 0)) { set_error("invalid refinement settings"); return KLST_EINVAL; }
+    f->max_refine = max_refine;
+    f->refine_tol = refine_tol;
+    return KLST_OK;
+}

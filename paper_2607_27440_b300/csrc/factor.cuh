@@ -1,0 +1,59 @@
+// Internal factor handle shared by factor.cu, apply.cu and eigs.cu.
+#pragma once
+#include "common.cuh"
+
+struct klst_factor_s {
+    klst_pencil p;
+    double2 sigma;
+    int precision;     // KLST_FP64 / KLST_MIXED
+    int nx, nxi, r;    // r = 4 nx (capacitance size)
+    int64_t n;
+    void* KinvT;       // [nxi][nx(m)][nx(j)] column-major inverse blocks, double2 or float2
+    double2* Cinv;     // [r][r] row-major capacitance inverse (float64)
+    // apply workspace (sized for nrhs_cap right-hand sides)
+    int nrhs_cap;
+    int ngroups;       // k-groups of the moment reductions
+    double2* tpart;    // [nrhs][ngroups][r]
+    double2* t;        // [nrhs][r]
+    double2* sv;       // [nrhs][r]
+    double2* bwork;    // [nrhs][n] masked right-hand side B x (mixed)
+    double2* rwork;    // [nrhs][n] refinement residual
+    double* normpart;  // [nrhs][nblk][2]
+    int* done;         // [nrhs] refinement converged flags
+    double2* sigma_dev;// [nrhs] the shift replicated per right-hand side
+    double* worst;     // [1] worst final refinement residual since the last reset
+    int* sweeps;       // [1] refinement sweeps executed since the last reset
+    int max_refine;
+    double refine_tol;
+    double t_factor_ms;
+    int64_t footprint;
+    klst::Status* status;
+};
+
+namespace klst {
+struct SchurArgs {
+    int m;             // current basis size (columns of S)
+    int lds;           // leading dimension of S (>= m + 1)
+    double2* S;        // (m+1) x m Rayleigh quotient + last row, column-major; overwritten by the truncation
+    double2* H;        // m x m scratch -> T
+    double2* Q;        // m x m scratch -> Schur vectors
+    double2* Yc;       // m x nev: Ritz vector coefficients Q y_i / ||y_i||
+    double2* mu;       // m Ritz values (sorted)
+    double* est;       // nev residual estimates
+    int* nconv;        // out: converged among the first nev
+    int keep;          // columns kept by the truncation (nev <= keep < m)
+    int nev;
+    double tol;
+    Status* st;
+};
+int launch_schur(const SchurArgs& a, cudaStream_t s);
+int factor_reserve(klst_factor f, int nrhs);
+// y = T x on the factor's stream; x, y complex128 n x nrhs
+int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t s);
+// y = (A - omega_r B) x_r (omega on device, nrhs entries)
+int apply_pencil_dev(klst_pencil p, const double2* x, double2* y, int nrhs, const double2* omega_dev,
+                     cudaStream_t s, double2* mwork, double2* mpart, int ngroups);
+int pencil_work_groups(klst_pencil p);
+void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,
+                         cudaStream_t s);
+}  // namespace klst

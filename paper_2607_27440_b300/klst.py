@@ -1,0 +1,235 @@
+"""Thin Python binding over the C ABI of ``include/klst.h`` (argument marshalling only).
+
+Device memory and streams come from PyTorch; every step of the eigensolve runs in
+the CUDA library ``libklst.so``.  There is no CPU fallback: if the library or a
+CUDA device is missing, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+c_int32, c_int64, c_double, c_void_p, c_uint64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64
+
+KLST_OK, KLST_EINVAL, KLST_ENOMEM, KLST_ESINGULAR, KLST_ENOCONV, KLST_EREFINE, KLST_ETIMEOUT, KLST_ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, MIXED = 0, 1
+BASES = {"tanh": 0, "mott_smith": 1}
+
+
+class PencilDesc(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("qx", c_int32), ("qy", c_int32), ("map_L", c_double), ("map_sinf", c_double),
+                ("mach", c_double), ("gamma", c_double), ("visc_s", c_double), ("re_delta", c_double),
+                ("beta", c_double), ("width", c_double), ("base", c_int32), ("noneq", c_int32),
+                ("conservative", c_int32)]
+
+
+class EigsOpts(ctypes.Structure):
+    _fields_ = [("nev", c_int32), ("ncv", c_int32), ("max_restarts", c_int32), ("max_refine", c_int32),
+                ("tol", c_double), ("refine_tol", c_double), ("v0", c_void_p), ("seed", c_uint64)]
+
+
+class EigsInfo(ctypes.Structure):
+    _fields_ = [("nconv", c_int32), ("restarts", c_int32), ("applies", c_int32), ("refine_sweeps", c_int32),
+                ("t_factor_ms", c_double), ("t_eigs_ms", c_double), ("max_resid", c_double),
+                ("max_refine_resid", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KlstError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} [{code}]")
+        self.code = code
+
+
+_lib = None
+
+EXPORTS = {
+    "klst_status_string": (ctypes.c_char_p, [c_int32]),
+    "klst_last_error": (ctypes.c_char_p, []),
+    "klst_build_pencil": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, ctypes.POINTER(c_void_p)]),
+    "klst_pencil_destroy": (None, [c_void_p]),
+    "klst_pencil_dims": (c_int32, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int32),
+                                   ctypes.POINTER(c_int32), ctypes.POINTER(c_int64)]),
+    "klst_pencil_tables": (c_int32, [c_void_p] + [c_void_p] * 9),
+    "klst_export_dense": (c_int32, [c_void_p, c_double, c_double, c_void_p, c_void_p]),
+    "klst_apply_pencil": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "klst_factor_shift": (c_int32, [c_void_p, c_double, c_double, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
+    "klst_factor_destroy": (None, [c_void_p]),
+    "klst_factor_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "klst_apply_shift_invert": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    "klst_factor_set_refine": (c_int32, [c_void_p, c_int32, c_double]),
+    "klst_eigs": (c_int32, [c_void_p, ctypes.POINTER(EigsOpts), c_void_p, c_void_p, c_void_p,
+                            ctypes.POINTER(EigsInfo), c_void_p]),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_stale=True):
+    """Load libklst.so (building it in-tree first when missing or older than its sources)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != KLST_OK:
+        lib = load()
+        raise KlstError(code, f"{lib.klst_status_string(code).decode()}: {lib.klst_last_error().decode()}")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the kLST library has no CPU path")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def make_desc(spec):
+    g = spec if isinstance(spec, dict) else spec.as_dict()
+    return PencilDesc(nx=g["nx"], qx=g["qx"], qy=g["qy"], map_L=g["map_L"], map_sinf=g["map_sinf"], mach=g["mach"],
+                      gamma=g["gamma"], visc_s=g["visc_s"], re_delta=g["re_delta"], beta=g["beta"], width=g["width"],
+                      base=BASES[g["base"]], noneq=int(g["noneq"]), conservative=int(g["conservative"]))
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr())
+
+
+class Pencil:
+    """Device-resident kLST pencil (klst_build_pencil)."""
+
+    def __init__(self, spec, stream=None):
+        lib = load()
+        _torch()
+        self.spec = spec
+        self._desc = make_desc(spec)
+        h = c_void_p()
+        _check(lib.klst_build_pencil(ctypes.byref(self._desc), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        n, nx, nxi, fp = c_int64(), c_int32(), c_int32(), c_int64()
+        _check(lib.klst_pencil_dims(h, ctypes.byref(n), ctypes.byref(nx), ctypes.byref(nxi), ctypes.byref(fp)))
+        self.n, self.nx, self.nxi, self.footprint = n.value, nx.value, nxi.value, fp.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().klst_pencil_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def tables(self):
+        nx, nxi = self.nx, self.nxi
+        out = dict(x=np.zeros(nx), Dx=np.zeros((nx, nx)), xi_x=np.zeros(nxi), xi_y=np.zeros(nxi), W=np.zeros(nxi),
+                   nu=np.zeros(nx), G=np.zeros((nxi, 2, 4, nx)), w=np.zeros((nxi, 2, 4, nx)),
+                   bc=np.zeros((nx, nxi), dtype=np.uint8))
+        args = [out[k].ctypes.data_as(c_void_p) for k in ("x", "Dx", "xi_x", "xi_y", "W", "nu", "G", "w", "bc")]
+        _check(load().klst_pencil_tables(self.handle, *args))
+        return out
+
+    def export_dense(self, sigma=0.0):
+        n = self.n
+        A = np.zeros((n, n), dtype=np.complex128)
+        B = np.zeros(n)
+        sigma = complex(sigma)
+        _check(load().klst_export_dense(self.handle, sigma.real, sigma.imag, A.ctypes.data_as(c_void_p),
+                                        B.ctypes.data_as(c_void_p)))
+        return A, B
+
+    def apply(self, x, omega=None, stream=None):
+        """(A - omega_r B) x_r for x of shape (nrhs, n) (or (n,)), complex128 on the device."""
+        torch = _torch()
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = torch.empty_like(x)
+        om = None
+        if omega is not None:
+            om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, dtype=np.complex128), (nrhs,)))
+        _check(load().klst_apply_pencil(self.handle, _ptr(x), _ptr(y), nrhs,
+                                        om.ctypes.data_as(c_void_p) if om is not None else None, _stream(stream)))
+        return y
+
+    def factor(self, sigma, precision=FP64, stream=None):
+        return Factor(self, sigma, precision, stream)
+
+
+class Factor:
+    """Shifted factorisation of a pencil (klst_factor_shift)."""
+
+    def __init__(self, pencil, sigma, precision=FP64, stream=None):
+        lib = load()
+        self.pencil = pencil
+        self.sigma = complex(sigma)
+        self.precision = precision
+        h = c_void_p()
+        _check(lib.klst_factor_shift(pencil.handle, self.sigma.real, self.sigma.imag, precision, _stream(stream),
+                                     ctypes.byref(h)))
+        self.handle = h
+        fp, tms = c_int64(), c_double()
+        _check(lib.klst_factor_info(h, None, None, None, ctypes.byref(fp), ctypes.byref(tms)))
+        self.footprint, self.t_factor_ms = fp.value, tms.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().klst_factor_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def set_refine(self, max_refine, refine_tol):
+        _check(load().klst_factor_set_refine(self.handle, max_refine, refine_tol))
+
+    def apply(self, x, out=None, stream=None):
+        """y = (A - sigma B)^{-1} B x for x of shape (nrhs, n) or (n,), complex128 on the device."""
+        torch = _torch()
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = torch.empty_like(x) if out is None else out
+        _check(load().klst_apply_shift_invert(self.handle, _ptr(x), _ptr(y), nrhs, _stream(stream)))
+        return y
+
+    def eigs(self, nev, ncv, tol=1e-12, max_restarts=200, max_refine=3, refine_tol=1e-14, v0=None, seed=0,
+             vectors=False, stream=None, check=True):
+        """Krylov-Schur shift-invert eigensolve; returns (omega[nev], vecs (nev, n) or None, resid[nev], info)."""
+        torch = _torch()
+        n = self.pencil.n
+        ev = np.zeros(2 * nev)
+        res = np.zeros(nev)
+        vec = torch.empty((nev, n), dtype=torch.complex128, device="cuda") if vectors else None
+        if v0 is not None:
+            v0 = v0.contiguous()
+        opts = EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
+                        refine_tol=refine_tol, v0=v0.data_ptr() if v0 is not None else None, seed=seed)
+        info = EigsInfo()
+        code = load().klst_eigs(self.handle, ctypes.byref(opts), ev.ctypes.data_as(c_void_p),
+                                _ptr(vec) if vec is not None else None, res.ctypes.data_as(c_void_p),
+                                ctypes.byref(info), _stream(stream))
+        if check:
+            _check(code)
+        omega = ev[0::2] + 1j * ev[1::2]
+        d = info.as_dict()
+        d["status"] = code
+        return omega, vec, res, d

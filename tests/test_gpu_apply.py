@@ -1,0 +1,90 @@
+"""GPU shift-and-invert apply (Eq. parShiftInvert, Woodbury form) vs the oracle's dense LU solve."""
+import numpy as np
+import pytest
+
+from oracle import eig, gas, pencil
+from paper_2607_27440_b300 import workloads as wl
+from tests.helpers import cond1, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    (wl.tiny(nx=9, qx=4, qy=2, mach=3.0), 0.1j),
+    (wl.tiny(nx=7, qx=5, qy=3, mach=4.0, beta=0.7), 0.3 + 0.05j),
+    (wl.tiny(nx=33, qx=9, qy=6, mach=3.5), 0.05 + 0.2j),
+    (wl.c1()[0], 0.1j),
+    (wl.tiny(nx=48, qx=10, qy=6, mach=2.5, beta=1.4), 0.1j),
+]
+
+
+@pytest.fixture(scope="module")
+def klst():
+    from paper_2607_27440_b300 import klst as k
+    k.load()
+    return k
+
+
+def _oracle(spec, sigma):
+    d = gas.pencil_data(spec.as_dict())
+    A, B = pencil.assemble_dense(spec.as_dict(), d)
+    return d, A, B, eig.ShiftInvert(A, B, sigma)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("spec,sigma", SMALL, ids=lambda v: str(v)[:40])
+def test_apply_matches_dense_lu(klst, spec, sigma, prec):
+    """||y_gpu - y_oracle|| / ||y_oracle|| <= max(1e-12, 64 cond(A - sigma B) eps) on three seeded vectors."""
+    d, A, B, si = _oracle(spec, sigma)
+    X = wl.random_vectors(A.shape[0], 3, 17)
+    ref = np.stack([si.apply(x) for x in X])
+    cond = cond1(A - sigma * B, si.lu)
+    tol = max(1e-12, 64 * cond * 2.220446049250313e-16)
+    P = klst.Pencil(spec)
+    F = P.factor(sigma, precision=prec)
+    if prec == 1:
+        F.set_refine(6, 1e-15)
+    Y = to_host(F.apply(to_dev(X)))
+    err = np.linalg.norm(Y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= tol), (err, tol, cond)
+    # inflow rows of T x vanish (range of T excludes the B-null space)
+    br = pencil.boundary_rows(d)
+    assert np.max(np.abs(Y[:, br])) <= tol * np.max(np.abs(Y))
+
+
+def test_multi_rhs_equals_single(klst):
+    spec, sigma = SMALL[2]
+    P = klst.Pencil(spec)
+    F = P.factor(sigma)
+    X = to_dev(wl.random_vectors(P.n, 4, 3))
+    Y = to_host(F.apply(X))
+    for i in range(4):
+        yi = to_host(F.apply(X[i]))
+        assert np.array_equal(yi, Y[i])
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("which", ["c2", "c3"])
+def test_apply_full_size_residual(klst, which, prec):
+    """Full workload sizes: the oracle's matrix-free rows give ||(A - sigma B) y - B x|| / ||B x||."""
+    spec, es = getattr(wl, which)()
+    d = gas.pencil_data(spec.as_dict())
+    P = klst.Pencil(spec)
+    F = P.factor(es.sigma, precision=prec)
+    x = wl.start_vector(P.n, 21)
+    y = to_host(F.apply(to_dev(x)))
+    r = pencil.apply_A(spec.as_dict(), d, y) - es.sigma * pencil.apply_B(d, y) - pencil.apply_B(d, x)
+    rel = np.linalg.norm(r) / np.linalg.norm(pencil.apply_B(d, x))
+    # backward error of a float64 solve: O(eps * ||A - sigma B|| * ||y|| / ||B x||)
+    normA = np.abs(d["Dx"]).sum(axis=1).max() * np.abs(d["xi_x"]).max() + np.abs(d["nu"]).max() + abs(es.sigma)
+    bound = 1e3 * 2.220446049250313e-16 * normA * np.linalg.norm(y) / np.linalg.norm(pencil.apply_B(d, x))
+    assert rel <= max(bound, 1e-12), (rel, bound)
+
+
+def test_exactly_singular_block_is_reported(klst):
+    """beta = 0 and odd qx: the xi_x = 0 block is diag(nu - sigma); sigma = nu_j makes it exactly singular."""
+    spec = wl.tiny(nx=8, qx=5, qy=2, beta=0.0)
+    P = klst.Pencil(spec)
+    nu = P.tables()["nu"]
+    with pytest.raises(klst.KlstError) as ei:
+        P.factor(complex(nu[3], 0.0))
+    assert ei.value.code == klst.KLST_ESINGULAR
