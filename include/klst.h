@@ -78,7 +78,12 @@ typedef struct {
     double refine_tol;    /* mixed precision: target ||r|| / ||rhs|| of each solve */
     const void* v0;       /* device complex128 start vector (length n) or NULL */
     uint64_t seed;        /* start vector seed when v0 == NULL */
+    int32_t conv;         /* KLST_CONV_REL: est <= tol |mu|;  KLST_CONV_RESID: est <= tol |mu|^2, which
+                             bounds the purified residual ||A q - omega B q|| (||q|| = 1) by ~tol */
+    double* est_out;      /* host float64[nev] or NULL: final Ritz residual estimates ||T x - mu x|| */
 } klst_eigs_opts;
+
+typedef enum { KLST_CONV_REL = 0, KLST_CONV_RESID = 1 } klst_conv;
 
 typedef struct {
     int32_t nconv;        /* converged pairs returned (<= nev) */
@@ -89,6 +94,10 @@ typedef struct {
     double t_eigs_ms;     /* wall time of the eigs call */
     double max_resid;     /* max explicit ||A q - omega B q|| over returned pairs, ||q|| = 1 */
     double max_refine_resid; /* worst final relative refinement residual (mixed) */
+    double t_apply_ms;    /* device time in shift-invert applies (CUDA events) */
+    double t_orth_ms;     /* device time in Gram-Schmidt orthogonalisation */
+    double t_restart_ms;  /* device time in Schur restarts and basis rotations */
+    double t_schur_ms;    /* of which the small Schur/reorder step */
 } klst_eigs_info;
 
 typedef struct klst_pencil_s* klst_pencil;
@@ -166,7 +175,7 @@ int klst_factor_info(klst_factor f, double* sigma_re, double* sigma_im, int32_t*
  */
 int klst_apply_shift_invert(klst_factor f, const void* x, void* y, int32_t nrhs, klst_stream stream);
 
-/* Refinement controls for klst_apply_shift_invert on MIXED factors (defaults 3 and 1e-14). */
+/* Refinement controls for klst_apply_shift_invert on MIXED factors (defaults 4 sweeps and 1e-12). */
 int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol);
 
 /*
@@ -178,6 +187,10 @@ int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol)
  * n x nev column-major, may be NULL) receive unit-norm purified eigenvectors
  * q = T x / ||T x||; resid_host (host float64[nev], may be NULL) receives
  * ||A q - omega B q||_2.  info may be NULL.
+ * Stopping rule: the nev Ritz pairs nearest sigma that meet the convergence test (opts->conv);
+ * an unconverged Ritz value nearer sigma may be passed over only when its |omega - sigma| is
+ * within 1% of the last returned one (a cluster straddling the nev boundary, whose internal
+ * order is not resolved); any separated nearer Ritz value keeps the iteration going.
  * Errors: KLST_ENOCONV (fewer than nev converged; the converged ones are still
  * returned and info->nconv says how many), KLST_EINVAL.  Synchronising.
  */

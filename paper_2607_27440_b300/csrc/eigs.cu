@@ -175,13 +175,18 @@ __global__ void k_randn(double2* x, int64_t n, uint64_t seed) {
 
 struct EigsWork {
     double2 *Va = nullptr, *Vb = nullptr, *S = nullptr, *H = nullptr, *Q = nullptr, *Yc = nullptr, *mu = nullptr;
+    double2 *Ysel = nullptr, *musel = nullptr;
+    double* estsel = nullptr;
     double2 *h = nullptr, *dpart = nullptr, *X = nullptr, *Z = nullptr, *R = nullptr, *om = nullptr;
     double2 *mw = nullptr, *mp = nullptr;
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
+    std::vector<cudaEvent_t> evs;
     void release() {
-        void* b[] = {Va, Vb, S, H, Q, Yc, mu, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
+        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
         for (void* p : b) cudaFree(p);
+        for (auto& ev : evs) cudaEventDestroy(ev);
+        evs.clear();
     }
 };
 
@@ -231,9 +236,12 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     EALLOC(W.S, (size_t)lds * m);
     EALLOC(W.H, (size_t)m * m);
     EALLOC(W.Q, (size_t)m * m);
-    EALLOC(W.Yc, (size_t)m * std::max(nev, 2));
+    EALLOC(W.Yc, (size_t)m * m);
+    EALLOC(W.Ysel, (size_t)m * nev);
     EALLOC(W.mu, m);
+    EALLOC(W.musel, nev);
     EALLOC(W.est, m);
+    EALLOC(W.estsel, nev);
     EALLOC(W.h, 2 * (m + 1));
     EALLOC(W.dpart, (size_t)nchunks * (m + 1));
     EALLOC(W.npart, (size_t)std::max(nblk, 1) * std::max(nev, 1) + 64);
@@ -261,6 +269,12 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     k_colnorm_fin<<<1, 32, 0, s>>>(W.npart, nblk, 1, W.nrm);
     k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm);
     KLST_CK_LAUNCH();
+    // phase timers: event pairs recorded per step and read after each restart synchronisation
+    W.evs.assign(3 * (m + 1) + 4, nullptr);
+    for (auto& ev : W.evs)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__));
+    std::vector<cudaEvent_t>& evs = W.evs;
+    double t_apply = 0, t_orth = 0, t_restart = 0, t_schur = 0;
     int k = 0, restarts = 0, nconv = 0;
     const size_t dots_smem = sizeof(double2) * chunk;
     const size_t upd_smem = sizeof(double2) * (m + 1);
@@ -269,7 +283,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         for (int j = k; j < m; ++j) {
             double2* vj = V + (int64_t)j * n;
             double2* w = V + (int64_t)(j + 1) * n;
+            cudaEventRecord(evs[3 * j], s);
             if ((rc = apply_T(f, vj, w, 1, s)) != KLST_OK) return fail(rc);
+            cudaEventRecord(evs[3 * j + 1], s);
             ++applies;
             const int nc = j + 1;
             k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1);
@@ -281,17 +297,35 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             k_dots_reduce<<<1, 192, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1);  // h1 += h2
             k_finish_col<<<1, 256, 0, s>>>(W.npart, nblk, W.h, j, W.S, lds, W.beta, f->status);
             k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(w, n, n, W.beta);
+            cudaEventRecord(evs[3 * j + 2], s);
             KLST_CK_LAUNCH();
         }
+        const int jfirst = k;
         SchurArgs a;
         a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
-        a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.st = f->status;
+        a.Ysel = W.Ysel; a.mu_sel = W.musel; a.est_sel = W.estsel;
+        a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.conv = o->conv; a.st = f->status;
+        cudaEventRecord(evs[3 * (m + 1)], s);
         if ((rc = launch_schur(a, s)) != KLST_OK) return fail(rc);
+        cudaEventRecord(evs[3 * (m + 1) + 1], s);
         Status hst;
         int hconv = 0;
         KLST_CK(cudaMemcpyAsync(&hconv, W.nconv, sizeof(int), cudaMemcpyDeviceToHost, s));
         KLST_CK(cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s));
         KLST_CK(cudaStreamSynchronize(s));
+        for (int j = jfirst; j < m; ++j) {
+            float a1 = 0, a2 = 0;
+            cudaEventElapsedTime(&a1, evs[3 * j], evs[3 * j + 1]);
+            cudaEventElapsedTime(&a2, evs[3 * j + 1], evs[3 * j + 2]);
+            t_apply += a1;
+            t_orth += a2;
+        }
+        {
+            float a3 = 0;
+            cudaEventElapsedTime(&a3, evs[3 * (m + 1)], evs[3 * (m + 1) + 1]);
+            t_restart += a3;
+            t_schur += a3;
+        }
         if (hconv < 0 || (hst.flags & ST_NOCONV_QR)) { set_error("small Schur QR iteration did not converge"); return fail(KLST_ENOCONV); }
         if (hst.flags & ST_BREAKDOWN) { set_error("Arnoldi breakdown (invariant subspace found)"); return fail(KLST_ENOCONV); }
         nconv = hconv;
@@ -299,11 +333,17 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         if (restarts >= o->max_restarts) break;
         // rotate: V'[:, 0:keep] = V[:, 0:m] Q[:, 0:keep], V'[:, keep] = V[:, m]
         {
+            cudaEventRecord(evs[3 * (m + 1) + 2], s);
             dim3 grd(std::max(1, nblk / std::max(1, (keep + 7) / 8)), (keep + 7) / 8);
             k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n);
             KLST_CK_LAUNCH();
             KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
                                     cudaMemcpyDeviceToDevice, s));
+            cudaEventRecord(evs[3 * (m + 1) + 3], s);
+            KLST_CK(cudaEventSynchronize(evs[3 * (m + 1) + 3]));
+            float a4 = 0;
+            cudaEventElapsedTime(&a4, evs[3 * (m + 1) + 2], evs[3 * (m + 1) + 3]);
+            t_restart += a4;
             std::swap(V, Valt);
         }
         k = keep;
@@ -331,7 +371,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     {
         dim3 grd(std::max(1, nblk / std::max(1, (nret + 7) / 8)), (nret + 7) / 8);
-        k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Yc, m, nret, X, n, n);
+        k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n);
         KLST_CK_LAUNCH();
     }
     if ((rc = apply_T(f, X, Z, nret, s)) != KLST_OK) return fail(rc);
@@ -341,7 +381,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     k_scale_cols<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.nrm);
     KLST_CK_LAUNCH();
     std::vector<double2> mu(m);
-    KLST_CK(cudaMemcpyAsync(mu.data(), W.mu, sizeof(double2) * m, cudaMemcpyDeviceToHost, s));
+    KLST_CK(cudaMemcpyAsync(mu.data(), W.musel, sizeof(double2) * nev, cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaStreamSynchronize(s));
     std::vector<double2> om(nret);
     for (int i = 0; i < nret; ++i) {
@@ -360,7 +400,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     KLST_CK(cudaMemcpyAsync(&worst, f->worst, sizeof(double), cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaMemcpyAsync(&sweeps, f->sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (evecs) KLST_CK(cudaMemcpyAsync(evecs, Z, sizeof(double2) * n * nret, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> esth(nret);
+    KLST_CK(cudaMemcpyAsync(esth.data(), W.estsel, sizeof(double) * nret, cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaStreamSynchronize(s));
+    if (o->est_out) memcpy(o->est_out, esth.data(), sizeof(double) * nret);
     double maxres = 0;
     for (int i = 0; i < nret; ++i) {
         evals_host[2 * i] = om[i].x;
@@ -377,6 +420,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         info->t_eigs_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         info->max_resid = maxres;
         info->max_refine_resid = worst;
+        info->t_apply_ms = t_apply;
+        info->t_orth_ms = t_orth;
+        info->t_restart_ms = t_restart;
+        info->t_schur_ms = t_schur;
     }
     W.release();
     f->max_refine = prev_refine;

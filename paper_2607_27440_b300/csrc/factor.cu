@@ -312,8 +312,8 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     f->precision = precision;
     f->nx = p->nx; f->nxi = p->nxi; f->r = 4 * p->nx; f->n = p->n;
     f->ngroups = pencil_work_groups(p);
-    f->max_refine = 3;
-    f->refine_tol = 1e-14;
+    f->max_refine = 4;
+    f->refine_tol = 1e-12;
     const int r = f->r;
     const size_t esz = precision == KLST_FP64 ? sizeof(double2) : sizeof(float2);
     const int nsplit = std::max(1, std::min(p->nxi, 8));

@@ -37,13 +37,17 @@ struct SchurArgs {
     double2* S;        // (m+1) x m Rayleigh quotient + last row, column-major; overwritten by the truncation
     double2* H;        // m x m scratch -> T
     double2* Q;        // m x m scratch -> Schur vectors
-    double2* Yc;       // m x nev: Ritz vector coefficients Q y_i / ||y_i||
+    double2* Yc;       // m x m scratch: eigenvectors y_p of T for p < keep
+    double2* Ysel;     // m x nev: Ritz vector coefficients Q y / ||y|| of the selected pairs
     double2* mu;       // m Ritz values (sorted)
-    double* est;       // nev residual estimates
+    double2* mu_sel;   // nev selected Ritz values
+    double* est;       // keep residual estimates (sorted positions)
+    double* est_sel;   // nev residual estimates of the selected pairs
     int* nconv;        // out: converged among the first nev
     int keep;          // columns kept by the truncation (nev <= keep < m)
     int nev;
     double tol;
+    int conv;          // 0: est <= tol |mu|, 1: est <= tol |mu|^2
     Status* st;
 };
 int launch_schur(const SchurArgs& a, cudaStream_t s);

@@ -234,12 +234,16 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
             __syncthreads();
         }
     }
-    // ---- Ritz values, eigenvectors y of T (back substitution) and residual estimates
+    // ---- Ritz values, eigenvectors y of T (back substitution) and residual estimates for the
+    //      first keep positions (sorted by |mu|, largest first)
+    __shared__ int s_sel[192];
+    __shared__ int s_nsel;
     for (int i = tid; i < m; i += nt) a.mu[i] = HH(i, i);
     const double ulp = 2.220446049250313e-16;
-    for (int p = tid; p < a.nev; p += nt) {
+    const int npos = a.keep;
+    for (int p = tid; p < npos; p += nt) {
         const double2 tp = HH(p, p);
-        double2* y = a.Yc + (size_t)p * m;  // temporary: y_p in column p
+        double2* y = a.Yc + (size_t)p * m;  // y_p in column p of the scratch
         for (int i = p + 1; i < m; ++i) y[i] = mk(0, 0);
         y[p] = mk(1, 0);
         double nrm = 1.0;
@@ -258,23 +262,47 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
         for (int i = 0; i <= p; ++i) y[i] = (1.0 / nrm) * y[i];
     }
     __syncthreads();
-    // Ritz vector coefficients Q y_p, written in place column by column from the last one
-    // (column p only reads y_p, which sits in column p itself: compute into registers first)
-    for (int p = a.nev - 1; p >= 0; --p) {
-        double2 acc = mk(0, 0);
-        const int row = tid;
-        if (row < m)
-            for (int i = 0; i <= p; ++i) cfma(acc, QQ(row, i), a.Yc[(size_t)p * m + i]);
-        __syncthreads();
-        if (row < m) a.Yc[(size_t)p * m + row] = acc;
-        __syncthreads();
-    }
+    // ---- selection: the nev nearest converged Ritz pairs.  An unconverged Ritz value nearer the
+    //      shift may only be passed over when it lies in a cluster with the last selected one
+    //      (|omega - sigma| within 1%), where the order inside the cluster is not resolved.
     if (tid == 0) {
-        int nc = 0;
-        for (int p = 0; p < a.nev; ++p)
-            if (a.est[p] <= a.tol * cabs(HH(p, p))) ++nc;
-        *a.nconv = nc;
+        int ns = 0, lead = 0;
+        bool leading = true;
+        for (int p = 0; p < npos && ns < a.nev; ++p) {
+            const double am = cabs(HH(p, p));
+            const bool ok = a.est[p] <= a.tol * (a.conv ? am * am : am);
+            if (ok) { s_sel[ns++] = p; if (leading) ++lead; }
+            else leading = false;
+        }
+        bool done = ns == a.nev;
+        if (done) {
+            const double mlast = cabs(HH(s_sel[a.nev - 1], s_sel[a.nev - 1]));
+            for (int p = 0; p < s_sel[a.nev - 1]; ++p) {
+                const double am = cabs(HH(p, p));
+                const bool ok = a.est[p] <= a.tol * (a.conv ? am * am : am);
+                if (!ok && am > mlast / 0.99) { done = false; break; }
+            }
+        }
+        if (!done) {
+            for (int i = 0; i < a.nev; ++i) s_sel[i] = i;
+            *a.nconv = lead;
+        } else {
+            *a.nconv = a.nev;
+        }
+        for (int i = 0; i < a.nev; ++i) {
+            a.mu_sel[i] = HH(s_sel[i], s_sel[i]);
+            a.est_sel[i] = a.est[s_sel[i]];
+        }
     }
+    __syncthreads();
+    // Ritz vector coefficients of the selected pairs: Ysel[:, i] = Q y_{sel_i}
+    for (int idx = tid; idx < m * a.nev; idx += nt) {
+        const int row = idx % m, i = idx / m, p = s_sel[i];
+        double2 acc = mk(0, 0);
+        for (int l = 0; l <= p; ++l) cfma(acc, QQ(row, l), a.Yc[(size_t)p * m + l]);
+        a.Ysel[(size_t)i * m + row] = acc;
+    }
+    __syncthreads();
     // ---- truncated Krylov-Schur relation: S[0:k,0:k] = T_kk, S[k,0:k] = beta Q[m-1, 0:k]
     const int k = a.keep;
     for (int idx = tid; idx < a.lds * m; idx += nt) {

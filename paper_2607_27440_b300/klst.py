@@ -15,6 +15,7 @@ c_int32, c_int64, c_double, c_void_p, c_uint64 = ctypes.c_int32, ctypes.c_int64,
 
 KLST_OK, KLST_EINVAL, KLST_ENOMEM, KLST_ESINGULAR, KLST_ENOCONV, KLST_EREFINE, KLST_ETIMEOUT, KLST_ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
+CONV_REL, CONV_RESID = 0, 1
 BASES = {"tanh": 0, "mott_smith": 1}
 
 
@@ -27,13 +28,15 @@ class PencilDesc(ctypes.Structure):
 
 class EigsOpts(ctypes.Structure):
     _fields_ = [("nev", c_int32), ("ncv", c_int32), ("max_restarts", c_int32), ("max_refine", c_int32),
-                ("tol", c_double), ("refine_tol", c_double), ("v0", c_void_p), ("seed", c_uint64)]
+                ("tol", c_double), ("refine_tol", c_double), ("v0", c_void_p), ("seed", c_uint64),
+                ("conv", c_int32), ("est_out", c_void_p)]
 
 
 class EigsInfo(ctypes.Structure):
     _fields_ = [("nconv", c_int32), ("restarts", c_int32), ("applies", c_int32), ("refine_sweeps", c_int32),
                 ("t_factor_ms", c_double), ("t_eigs_ms", c_double), ("max_resid", c_double),
-                ("max_refine_resid", c_double)]
+                ("max_refine_resid", c_double), ("t_apply_ms", c_double), ("t_orth_ms", c_double),
+                ("t_restart_ms", c_double), ("t_schur_ms", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -211,9 +214,12 @@ class Factor:
         _check(load().klst_apply_shift_invert(self.handle, _ptr(x), _ptr(y), nrhs, _stream(stream)))
         return y
 
-    def eigs(self, nev, ncv, tol=1e-12, max_restarts=200, max_refine=3, refine_tol=1e-14, v0=None, seed=0,
-             vectors=False, stream=None, check=True):
-        """Krylov-Schur shift-invert eigensolve; returns (omega[nev], vecs (nev, n) or None, resid[nev], info)."""
+    def eigs(self, nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, v0=None, seed=0,
+             vectors=False, stream=None, check=True, conv=CONV_REL):
+        """Krylov-Schur shift-invert eigensolve; returns (omega[nev], vecs (nev, n) or None, resid[nev], info).
+
+        info carries the klst_eigs_info fields plus ``status`` and ``ritz_est`` (final Ritz estimates).
+        """
         torch = _torch()
         n = self.pencil.n
         ev = np.zeros(2 * nev)
@@ -221,8 +227,10 @@ class Factor:
         vec = torch.empty((nev, n), dtype=torch.complex128, device="cuda") if vectors else None
         if v0 is not None:
             v0 = v0.contiguous()
+        est = np.zeros(nev)
         opts = EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
-                        refine_tol=refine_tol, v0=v0.data_ptr() if v0 is not None else None, seed=seed)
+                        refine_tol=refine_tol, v0=v0.data_ptr() if v0 is not None else None, seed=seed, conv=conv,
+                        est_out=est.ctypes.data)
         info = EigsInfo()
         code = load().klst_eigs(self.handle, ctypes.byref(opts), ev.ctypes.data_as(c_void_p),
                                 _ptr(vec) if vec is not None else None, res.ctypes.data_as(c_void_p),
@@ -232,4 +240,5 @@ class Factor:
         omega = ev[0::2] + 1j * ev[1::2]
         d = info.as_dict()
         d["status"] = code
+        d["ritz_est"] = est
         return omega, vec, res, d

@@ -45,3 +45,22 @@ def cond1(A, lu=None):
     op = spla.LinearOperator((n, n), matvec=lambda x: sla.lu_solve(lu, x),
                              rmatvec=lambda x: sla.lu_solve(lu, x, trans=2), dtype=np.complex128)
     return np.abs(A).sum(axis=0).max() * spla.onenormest(op)
+
+
+def pencil_norm2_est(data, beta):
+    """sqrt(||A||_1 ||A||_inf) >= ||A||_2, from the oracle's per-point tables (triangle-inequality sums)."""
+    d = data
+    nx, nxi = d["Dx"].shape[0], d["W"].size
+    axx = np.abs(d["xi_x"])
+    rows = axx[None, :] * np.abs(d["Dx"]).sum(axis=1)[:, None]          # (j, k) streaming row sums
+    cols = axx[None, :] * np.abs(d["Dx"]).sum(axis=0)[:, None]          # (m, p) streaming column sums
+    diag = np.abs(d["nu"][:, None] + 1j * beta * d["xi_y"][None, :])
+    cr = np.zeros((2, nx, nxi))
+    cc = np.zeros((2, nx, nxi))
+    for j in range(nx):
+        blk = np.abs(np.einsum("cak,dap->ckdp", d["G"][:, :, j, :], d["w"][:, :, j, :]))
+        cr[:, j, :] = blk.sum(axis=(2, 3))
+        cc[:, j, :] = blk.sum(axis=(0, 1))
+    ninf = np.max(rows[None] + diag[None] + cr)
+    n1 = np.max(cols[None] + diag[None] + cc)
+    return float(np.sqrt(ninf * n1))
