@@ -81,6 +81,7 @@ typedef struct {
     int32_t conv;         /* KLST_CONV_REL: est <= tol |mu|;  KLST_CONV_RESID: est <= tol |mu|^2, which
                              bounds the purified residual ||A q - omega B q|| (||q|| = 1) by ~tol */
     double* est_out;      /* host float64[nev] or NULL: final Ritz residual estimates ||T x - mu x|| */
+    int32_t keep;         /* Ritz vectors kept at each restart, nev <= keep < ncv; 0 = nev + (ncv - nev) / 2 */
 } klst_eigs_opts;
 
 typedef enum { KLST_CONV_REL = 0, KLST_CONV_RESID = 1 } klst_conv;

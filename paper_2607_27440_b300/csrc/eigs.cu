@@ -214,7 +214,11 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     const int nchunks = (int)((n + chunk - 1) / chunk);
     const int nblk = std::min<int64_t>((n + 255) / 256, 4 * sms);
     const int ng = pencil_work_groups(p);
-    const int keep = std::min(m - 1, nev + (m - nev) / 2);
+    if (o->keep != 0 && (o->keep < nev || o->keep >= m)) {
+        set_error("invalid keep=%d (need nev <= keep < ncv)", o->keep);
+        return KLST_EINVAL;
+    }
+    const int keep = o->keep ? o->keep : std::min(m - 1, nev + (m - nev) / 2);
     const int prev_refine = f->max_refine;
     const double prev_rtol = f->refine_tol;
     f->max_refine = o->max_refine;

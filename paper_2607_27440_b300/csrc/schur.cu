@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
     // ---- Ritz values, eigenvectors y of T (back substitution) and residual estimates for the
     //      first keep positions (sorted by |mu|, largest first)
     __shared__ int s_sel[192];
-    __shared__ int s_nsel;
     for (int i = tid; i < m; i += nt) a.mu[i] = HH(i, i);
     const double ulp = 2.220446049250313e-16;
     const int npos = a.keep;

@@ -29,7 +29,7 @@ class PencilDesc(ctypes.Structure):
 class EigsOpts(ctypes.Structure):
     _fields_ = [("nev", c_int32), ("ncv", c_int32), ("max_restarts", c_int32), ("max_refine", c_int32),
                 ("tol", c_double), ("refine_tol", c_double), ("v0", c_void_p), ("seed", c_uint64),
-                ("conv", c_int32), ("est_out", c_void_p)]
+                ("conv", c_int32), ("est_out", c_void_p), ("keep", c_int32)]
 
 
 class EigsInfo(ctypes.Structure):
@@ -215,7 +215,7 @@ class Factor:
         return y
 
     def eigs(self, nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, v0=None, seed=0,
-             vectors=False, stream=None, check=True, conv=CONV_REL):
+             vectors=False, stream=None, check=True, conv=CONV_REL, keep=0):
         """Krylov-Schur shift-invert eigensolve; returns (omega[nev], vecs (nev, n) or None, resid[nev], info).
 
         info carries the klst_eigs_info fields plus ``status`` and ``ritz_est`` (final Ritz estimates).
@@ -230,7 +230,7 @@ class Factor:
         est = np.zeros(nev)
         opts = EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
                         refine_tol=refine_tol, v0=v0.data_ptr() if v0 is not None else None, seed=seed, conv=conv,
-                        est_out=est.ctypes.data)
+                        est_out=est.ctypes.data, keep=keep)
         info = EigsInfo()
         code = load().klst_eigs(self.handle, ctypes.byref(opts), ev.ctypes.data_as(c_void_p),
                                 _ptr(vec) if vec is not None else None, res.ctypes.data_as(c_void_p),
