@@ -29,6 +29,7 @@
 #ifndef KLST_H
 #define KLST_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -146,6 +147,27 @@ int klst_export_dense(klst_pencil p, double sigma_re, double sigma_im, double* A
  */
 int klst_apply_pencil(klst_pencil p, const void* x, void* y, int32_t nrhs, const double* omega,
                       klst_stream stream);
+
+/*
+ * klst_apply_pencil_noalloc -- the same operator as klst_apply_pencil, y[:, r] = (A - omega_r B) x[:, r],
+ * without allocating any device memory.  (The paper has no counterpart: this is a library service.)
+ * For callers that cannot allocate when they apply the operator: hosts whose device memory is owned
+ * by their own pool and who forbid library allocations in their steady-state loop, latency-critical
+ * serving loops in which an allocation may synchronise or stall other streams, and code that must not
+ * run out of memory halfway through a solve.  The call uses a fixed scratch array of
+ * klst_apply_pencil_noalloc_capacity() bytes (4 MiB) that every GPU that loads this library holds
+ * until the process exits; it needs 16 * (nrhs + 4 nx nrhs (1 + min(nxi, 32))) bytes and returns
+ * KLST_EINVAL, with a message naming the limit, when that exceeds the capacity (e.g. nrhs > 15 at
+ * nx = 128).  The first call on each device resolves the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share the one array, so calls
+ * that may overlap on the GPU (different streams, or different threads without ordering) race: order
+ * them on one stream.  Nothing is carried between calls.  x, y: device complex128, n x nrhs
+ * column-major, no aliasing; omega: host complex128[nrhs] or NULL (all zero); a page-locked omega
+ * must stay valid until the stream reaches the call.
+ */
+int klst_apply_pencil_noalloc(klst_pencil p, const void* x, void* y, int32_t nrhs, const double* omega,
+                              klst_stream stream);
+size_t klst_apply_pencil_noalloc_capacity(void);
 
 /*
  * klst_factor_shift -- factor A - sigma B for the shift-and-invert transform

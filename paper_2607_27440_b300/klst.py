@@ -60,6 +60,8 @@ EXPORTS = {
     "klst_pencil_tables": (c_int32, [c_void_p] + [c_void_p] * 9),
     "klst_export_dense": (c_int32, [c_void_p, c_double, c_double, c_void_p, c_void_p]),
     "klst_apply_pencil": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "klst_apply_pencil_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "klst_apply_pencil_noalloc_capacity": (ctypes.c_size_t, []),
     "klst_factor_shift": (c_int32, [c_void_p, c_double, c_double, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
     "klst_factor_destroy": (None, [c_void_p]),
     "klst_factor_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -173,6 +175,23 @@ class Pencil:
             om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, dtype=np.complex128), (nrhs,)))
         _check(load().klst_apply_pencil(self.handle, _ptr(x), _ptr(y), nrhs,
                                         om.ctypes.data_as(c_void_p) if om is not None else None, _stream(stream)))
+        return y
+
+    def apply_noalloc(self, x, omega=None, out=None, stream=None):
+        """Same as ``apply`` through klst_apply_pencil_noalloc (fixed device scratch, no allocation).
+
+        ``out`` lets a caller that cannot allocate pass its own output buffer.
+        """
+        torch = _torch()
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = torch.empty_like(x) if out is None else out
+        om = None
+        if omega is not None:
+            om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, dtype=np.complex128), (nrhs,)))
+        _check(load().klst_apply_pencil_noalloc(self.handle, _ptr(x), _ptr(y), nrhs,
+                                                om.ctypes.data_as(c_void_p) if om is not None else None,
+                                                _stream(stream)))
         return y
 
     def factor(self, sigma, precision=FP64, stream=None):
