@@ -100,6 +100,7 @@ typedef struct {
     double t_orth_ms;     /* device time in Gram-Schmidt orthogonalisation */
     double t_restart_ms;  /* device time in Schur restarts and basis rotations */
     double t_schur_ms;    /* of which the small Schur/reorder step */
+    int32_t reorths;      /* Arnoldi steps that needed the second Gram-Schmidt pass (DGKS test) */
 } klst_eigs_info;
 
 typedef struct klst_pencil_s* klst_pencil;
@@ -204,7 +205,8 @@ int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol)
 /*
  * klst_eigs -- the nev eigenvalues nearest sigma by Krylov-Schur restarted Arnoldi on T
  * (Sec. 4.1: implicitly restarted Arnoldi with shift-and-invert), with classical
- * Gram-Schmidt plus one reorthogonalisation in float64 and the small Schur/reorder
+ * Gram-Schmidt in float64 with a second pass when the DGKS test
+ * (||w'|| < ||w|| / sqrt 2) asks for it and the small Schur/reorder
  * step in float64 on the device.  Eigenvalues omega = sigma + 1/mu are returned
  * nearest-first in evals_host (host complex128[nev]); evecs (device complex128,
  * n x nev column-major, may be NULL) receive unit-norm purified eigenvectors

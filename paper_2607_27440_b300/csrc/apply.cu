@@ -186,13 +186,19 @@ static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y,
     const int ng = f->ngroups, kpg = ((nxi + ng - 1) / ng + KB - 1) / KB * KB;
     dim3 blk(NXP, KB);
     const size_t sm1 = std::max(sizeof(C) * KB * 2 * NXP, sizeof(double2) * 4 * KB * NXP);
+    prof_begin(sizeof(C) == 16 ? "solve_pass1_f64" : "solve_pass1_f32", s);
     k_solve_pass1<C><<<dim3(ng, nrhs), blk, sm1, s>>>(nx, nxi, (const C*)f->KinvT, p->w, p->xi_x, b, p->n, mask, ng,
                                                       kpg, f->tpart, done);
+    prof_end(sizeof(C) == 16 ? "solve_pass1_f64" : "solve_pass1_f32", s);
+    prof_begin("cap_solve", s);
     k_reduce_groups_ext(f->r, ng, f->tpart, f->t, done, nrhs, s);
     k_cinv_gemv<<<dim3((f->r * 32 + 255) / 256, nrhs), 256, 0, s>>>(f->r, f->Cinv, f->t, f->sv, done);
+    prof_end("cap_solve", s);
+    prof_begin(sizeof(C) == 16 ? "solve_pass2_f64" : "solve_pass2_f32", s);
     const int nb2 = std::min((nxi + KB - 1) / KB, 4 * device_sm_count());
     k_solve_pass2<C><<<dim3(nb2, nrhs), blk, sizeof(C) * KB * 2 * NXP, s>>>(nx, nxi, (const C*)f->KinvT, p->G, p->xi_x,
                                                                            b, p->n, mask, f->sv, y, accumulate, done);
+    prof_end(sizeof(C) == 16 ? "solve_pass2_f64" : "solve_pass2_f32", s);
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
@@ -209,11 +215,13 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
     const int nblk = pencil_rows_blocks(p);
     for (int it = 0; it <= f->max_refine; ++it) {
         const int last = it == f->max_refine;
+        prof_begin("refine_residual", s);
         rc = moments_dev(p, y, p->n, nrhs, f->t, f->tpart, f->ngroups, s, f->done);
         if (rc) return rc;
         rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done);
         if (rc) return rc;
         k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last);
+        prof_end("refine_residual", s);
         KLST_CK_LAUNCH();
         if (last) break;
         rc = woodbury_solve<float2>(f, f->rwork, 0, y, 1, nrhs, s, f->done);

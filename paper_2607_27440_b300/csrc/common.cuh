@@ -150,3 +150,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
 int device_sm_count();
 
 }  // namespace klst
+
+namespace klst {
+// Opt-in per-kernel-group timing (environment KLST_TIMING=1): CUDA events around launch groups,
+// summed per name and printed to stderr by klst_eigs.  Off by default; no cost when off.
+bool prof_enabled();
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(const char* name, cudaStream_t s);
+void prof_report(cudaStream_t s);
+}  // namespace klst

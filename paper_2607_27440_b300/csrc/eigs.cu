@@ -13,17 +13,20 @@
 namespace klst {
 
 
-// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]
+// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]; with_self adds column ncols = |w|^2.
+// gate (optional): skip when *gate == 0 (reorthogonalisation not needed).
 __global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ w,
-                       int64_t n, int chunk, double2* __restrict__ part, int ldp) {
+                       int64_t n, int chunk, double2* __restrict__ part, int ldp, int with_self,
+                       const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ double2 sw[];
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
     for (int i = threadIdx.x; i < len; i += blockDim.x) sw[i] = w[r0 + i];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int col = wid; col < ncols; col += nw) {
-        const double2* vc = V + col * ldv + r0;
+    for (int col = wid; col < ncols + with_self; col += nw) {
+        const double2* vc = col < ncols ? V + col * ldv + r0 : sw;
         double2 a = mk(0, 0);
         for (int i = lane; i < len; i += 32) cfma_conj(a, vc[i], sw[i]);
         for (int o = 16; o > 0; o >>= 1) {
@@ -34,18 +37,43 @@ __global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int ncols, co
     }
 }
 
-// h[col] (+)= sum_chunk part[chunk][col]  (fixed order)
-__global__ void k_dots_reduce(const double2* __restrict__ part, int nchunks, int ncols, int ldp, double2* h, int add) {
+// h[col] (+)= sum_chunk part[chunk][col]  (fixed order); with a closed gate, h2 := 0
+__global__ void k_dots_reduce(const double2* __restrict__ part, int nchunks, int ncols, int ldp, double2* h, int add,
+                              const int* __restrict__ gate) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncols) return;
+    if (gate && *gate == 0) {
+        if (!add) h[col] = mk(0, 0);
+        return;
+    }
     double2 s = mk(0, 0);
     for (int c = 0; c < nchunks; ++c) s = s + part[(size_t)c * ldp + col];
     h[col] = add ? h[col] + s : s;
 }
 
+// DGKS test (Daniel, Gragg, Kaufman, Stewart): reorthogonalise only when the first projection
+// removed more than half of ||w||^2, i.e. ||w'|| < ||w|| / sqrt(2).
+__global__ void k_reorth_decide(const double* __restrict__ npart, int nblk, const double2* __restrict__ wself,
+                                int* __restrict__ gate, int* __restrict__ count) {
+    __shared__ double red[32];
+    double s = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += npart[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q];
+        const int g = a < 0.5 * wself->x ? 1 : 0;
+        *gate = g;
+        if (g) atomicAdd(count, 1);
+    }
+}
+
 // w -= V h (ncols columns); optional per-block partial of |w|^2
 __global__ void k_update(const double2* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ h,
-                         double2* __restrict__ w, int64_t n, double* __restrict__ npart) {
+                         double2* __restrict__ w, int64_t n, double* __restrict__ npart, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ double2 sh[];
     for (int i = threadIdx.x; i < ncols; i += blockDim.x) sh[i] = h[i];
     __syncthreads();
@@ -99,9 +127,11 @@ __global__ void k_colnorm_fin(const double* __restrict__ npart, int nblk, int nc
 }
 
 // Finish the Arnoldi column j: S[0..j, j] = h1 + h2, S[j+1, j] = beta = ||w||; stores beta.
-__global__ void k_finish_col(const double* __restrict__ npart, int nblk, const double2* __restrict__ h, int j,
+__global__ void k_finish_col(const double* __restrict__ npart1, const double* __restrict__ npart2,
+                             const int* __restrict__ gate, int nblk, const double2* __restrict__ h, int j,
                              double2* __restrict__ S, int lds, double* __restrict__ beta_out, Status* st) {
     __shared__ double red[32];
+    const double* npart = *gate ? npart2 : npart1;
     double s = 0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += npart[b];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -175,15 +205,19 @@ __global__ void k_randn(double2* x, int64_t n, uint64_t seed) {
 
 struct EigsWork {
     double2 *Va = nullptr, *Vb = nullptr, *S = nullptr, *H = nullptr, *Q = nullptr, *Yc = nullptr, *mu = nullptr;
-    double2 *Ysel = nullptr, *musel = nullptr;
-    double* estsel = nullptr;
+    double2 *Ysel = nullptr, *musel = nullptr, *Vh = nullptr;
+    double *estsel = nullptr, *tau = nullptr;
+    Rot* rlog = nullptr;
+    int* rcount = nullptr;
+    double* npart2 = nullptr;
+    int *gate = nullptr, *reorth = nullptr;
     double2 *h = nullptr, *dpart = nullptr, *X = nullptr, *Z = nullptr, *R = nullptr, *om = nullptr;
     double2 *mw = nullptr, *mp = nullptr;
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
     std::vector<cudaEvent_t> evs;
     void release() {
-        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
+        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
         for (void* p : b) cudaFree(p);
         for (auto& ev : evs) cudaEventDestroy(ev);
         evs.clear();
@@ -246,6 +280,14 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     EALLOC(W.musel, nev);
     EALLOC(W.est, m);
     EALLOC(W.estsel, nev);
+    EALLOC(W.Vh, (size_t)m * m);
+    EALLOC(W.tau, m);
+    const int log_cap = 31 * m * m;
+    EALLOC(W.rlog, log_cap);
+    EALLOC(W.rcount, 4);
+    EALLOC(W.npart2, std::max(nblk, 1));
+    EALLOC(W.gate, 4);
+    EALLOC(W.reorth, 4);
     EALLOC(W.h, 2 * (m + 1));
     EALLOC(W.dpart, (size_t)nchunks * (m + 1));
     EALLOC(W.npart, (size_t)std::max(nblk, 1) * std::max(nev, 1) + 64);
@@ -257,6 +299,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     EALLOC(W.mp, (size_t)4 * p->nx * ng * nev);
 #undef EALLOC
     KLST_CK(cudaMemsetAsync(W.S, 0, sizeof(double2) * lds * m, s));
+    KLST_CK(cudaMemsetAsync(W.reorth, 0, sizeof(int) * 4, s));
     KLST_CK(cudaMemsetAsync(f->status, 0, sizeof(Status), s));
     KLST_CK(cudaMemsetAsync(f->worst, 0, sizeof(double), s));
     KLST_CK(cudaMemsetAsync(f->sweeps, 0, sizeof(int), s));
@@ -292,14 +335,20 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             cudaEventRecord(evs[3 * j + 1], s);
             ++applies;
             const int nc = j + 1;
-            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1);
-            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h, 0);
-            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, nullptr);
-            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1);
-            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0);
-            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h + (m + 1), w, n, W.npart);
-            k_dots_reduce<<<1, 192, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1);  // h1 += h2
-            k_finish_col<<<1, 256, 0, s>>>(W.npart, nblk, W.h, j, W.S, lds, W.beta, f->status);
+            // classical Gram-Schmidt, then a second pass only when the DGKS test asks for it
+            prof_begin("orth_pass1", s);
+            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr);
+            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr);
+            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, W.npart, nullptr);
+            k_reorth_decide<<<1, 256, 0, s>>>(W.npart, nblk, W.h + nc, W.gate, W.reorth);
+            prof_end("orth_pass1", s);
+            prof_begin("orth_pass2", s);
+            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 0, W.gate);
+            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0, W.gate);
+            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h + (m + 1), w, n, W.npart2, W.gate);
+            k_dots_reduce<<<1, 192, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1, W.gate);  // h1 += h2
+            k_finish_col<<<1, 256, 0, s>>>(W.npart, W.npart2, W.gate, nblk, W.h, j, W.S, lds, W.beta, f->status);
+            prof_end("orth_pass2", s);
             k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(w, n, n, W.beta);
             cudaEventRecord(evs[3 * j + 2], s);
             KLST_CK_LAUNCH();
@@ -308,6 +357,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         SchurArgs a;
         a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
         a.Ysel = W.Ysel; a.mu_sel = W.musel; a.est_sel = W.estsel;
+        a.Vh = W.Vh; a.tau = W.tau; a.log = W.rlog; a.log_cap = log_cap; a.log_count = W.rcount;
         a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.conv = o->conv; a.st = f->status;
         cudaEventRecord(evs[3 * (m + 1)], s);
         if ((rc = launch_schur(a, s)) != KLST_OK) return fail(rc);
@@ -339,7 +389,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         {
             cudaEventRecord(evs[3 * (m + 1) + 2], s);
             dim3 grd(std::max(1, nblk / std::max(1, (keep + 7) / 8)), (keep + 7) / 8);
+            prof_begin("rotate", s);
             k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n);
+            prof_end("rotate", s);
             KLST_CK_LAUNCH();
             KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
                                     cudaMemcpyDeviceToDevice, s));
@@ -399,15 +451,17 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     KLST_CK_LAUNCH();
     std::vector<double> res(nret);
     double worst = 0;
-    int sweeps = 0;
+    int sweeps = 0, reorths = 0;
     KLST_CK(cudaMemcpyAsync(res.data(), W.nrm, sizeof(double) * nret, cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaMemcpyAsync(&worst, f->worst, sizeof(double), cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaMemcpyAsync(&sweeps, f->sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KLST_CK(cudaMemcpyAsync(&reorths, W.reorth, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (evecs) KLST_CK(cudaMemcpyAsync(evecs, Z, sizeof(double2) * n * nret, cudaMemcpyDeviceToDevice, s));
     std::vector<double> esth(nret);
     KLST_CK(cudaMemcpyAsync(esth.data(), W.estsel, sizeof(double) * nret, cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaStreamSynchronize(s));
     if (o->est_out) memcpy(o->est_out, esth.data(), sizeof(double) * nret);
+    prof_report(s);
     double maxres = 0;
     for (int i = 0; i < nret; ++i) {
         evals_host[2 * i] = om[i].x;
@@ -428,6 +482,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         info->t_orth_ms = t_orth;
         info->t_restart_ms = t_restart;
         info->t_schur_ms = t_schur;
+        info->reorths = reorths;
     }
     W.release();
     f->max_refine = prev_refine;

@@ -237,25 +237,33 @@ __global__ void __launch_bounds__(256) k_gj_coop(int r, double2* buf0, double2* 
 }
 
 template <typename C>
-static int launch_block_gj(klst_factor f, cudaStream_t s) {
+static int launch_block_gj(klst_factor f, C* out, cudaStream_t s) {
     klst_pencil p = f->p;
     const size_t bytes = sizeof(C) * p->nx * p->nx;
     const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
     if (use_smem) KLST_CK(cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     k_block_gj<C><<<p->nxi, 256, use_smem ? bytes : 0, s>>>(p->nx, p->nxi, p->desc.beta, f->sigma, p->Dx, p->xi_x,
-                                                           p->xi_y, p->nu, (C*)f->KinvT, use_smem, f->status);
+                                                           p->xi_y, p->nu, out, use_smem, f->status);
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
 
 template <typename C>
-static int launch_cap(klst_factor f, double2* Cp, int nsplit, cudaStream_t s) {
+static int launch_cap(klst_factor f, const C* Kinv, double2* Cp, int nsplit, cudaStream_t s) {
     klst_pencil p = f->p;
     const int kper = (p->nxi + nsplit - 1) / nsplit;
     dim3 blk(16, 16), grd((p->nx + 15) / 16, (p->nx + 15) / 16, nsplit);
-    k_cap_partial<C><<<grd, blk, 0, s>>>(p->nx, p->nxi, (const C*)f->KinvT, p->G, p->w, kper, Cp);
+    k_cap_partial<C><<<grd, blk, 0, s>>>(p->nx, p->nxi, Kinv, p->G, p->w, kper, Cp);
     KLST_CK_LAUNCH();
     return KLST_OK;
+}
+
+// complex128 -> complex64 rounding of the block inverses (mixed precision storage)
+__global__ void k_round_c64(const double2* __restrict__ in, float2* __restrict__ out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += gridDim.x * (size_t)blockDim.x) {
+        const double2 v = in[i];
+        out[i] = mkf((float)v.x, (float)v.y);
+    }
 }
 
 int factor_reserve(klst_factor f, int nrhs) {
@@ -343,10 +351,26 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     cudaMemsetAsync(f->worst, 0, sizeof(double), s);
     cudaMemsetAsync(f->sweeps, 0, sizeof(int), s);
     cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 2, s);
-    int rc = precision == KLST_FP64 ? launch_block_gj<double2>(f, s) : launch_block_gj<float2>(f, s);
-    if (rc) return fail(rc);
-    rc = precision == KLST_FP64 ? launch_cap<double2>(f, Cp, nsplit, s) : launch_cap<float2>(f, Cp, nsplit, s);
-    if (rc) return fail(rc);
+    // The block inverses are always formed in float64 (the capacitance is built from them); the
+    // mixed factor then stores them rounded to complex float32, so the float32 solve carries only
+    // the rounding of its operands and not the float32 elimination error.
+    double2* K64 = (double2*)f->KinvT;
+    if (precision == KLST_MIXED) {
+        if ((e = cudaMalloc(&K64, sizeof(double2) * (size_t)p->nxi * p->nx * p->nx)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    }
+    auto free64 = [&]() { if (precision == KLST_MIXED) cudaFree(K64); };
+    int rc = launch_block_gj<double2>(f, K64, s);
+    if (rc) { free64(); return fail(rc); }
+    rc = launch_cap<double2>(f, K64, Cp, nsplit, s);
+    if (rc) { free64(); return fail(rc); }
+    if (precision == KLST_MIXED) {
+        const size_t cnt = (size_t)p->nxi * p->nx * p->nx;
+        k_round_c64<<<(int)std::min<size_t>((cnt + 255) / 256, 8192), 256, 0, s>>>(K64, (float2*)f->KinvT, cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) { free64(); return fail(cuda_fail(e, "round", __FILE__, __LINE__)); }
+        cudaStreamSynchronize(s);
+        free64();
+    }
     k_cap_reduce<<<std::min(1024, (r * r + 255) / 256), 256, 0, s>>>(r, nsplit, Cp, b0);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "cap reduce", __FILE__, __LINE__));
     {

@@ -31,6 +31,12 @@ struct klst_factor_s {
 };
 
 namespace klst {
+struct Rot {           // rotation of columns (i, i+1): [c s; -conj(s) c] applied from the left to rows
+    double2 s;
+    double c;
+    int i;
+    int pad;
+};
 struct SchurArgs {
     int m;             // current basis size (columns of S)
     int lds;           // leading dimension of S (>= m + 1)
@@ -49,7 +55,13 @@ struct SchurArgs {
     double tol;
     int conv;          // 0: est <= tol |mu|, 1: est <= tol |mu|^2
     Status* st;
+    double2* Vh;       // m x m: Householder vectors (column c, rows c+1..m-1)
+    double* tau;       // m: Householder scalars (0 = no reflection)
+    Rot* log;          // Givens rotations of the QR sweeps and the reordering, in order
+    int log_cap;
+    int* log_count;
 };
+
 int launch_schur(const SchurArgs& a, cudaStream_t s);
 int factor_reserve(klst_factor f, int nrhs);
 // y = T x on the factor's stream; x, y complex128 n x nrhs

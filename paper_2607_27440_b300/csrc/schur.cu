@@ -1,19 +1,44 @@
 // Small dense float64 step of the Krylov-Schur restart (Sec. 4.1: restarted Arnoldi with a
-// filter that keeps the wanted Ritz values), run by one CTA on the device:
-//   S_m = Q T Q^H (Householder reduction to Hessenberg form, then shifted QR with Givens
-//   rotations to the complex Schur form), reorder T so the Ritz values mu with the largest
-//   |mu| (eigenvalues omega = sigma + 1/mu nearest the shift) lead, Ritz residual estimates
-//   beta |e_m^T Q y_i|, and the truncated Krylov-Schur relation for the next cycle.
+// filter that keeps the wanted Ritz values), on the device:
+//   S_m = Q T Q^H: Householder reduction to Hessenberg form, then shifted QR with Givens
+//   rotations to the complex Schur form; T is reordered so the Ritz values mu with the largest
+//   |mu| (eigenvalues omega = sigma + 1/mu nearest the shift) lead; Ritz residual estimates
+//   beta |e_m^T Q y_i|; the truncated Krylov-Schur relation for the next cycle.
+// Four kernels: k_schur_house (one CTA) reduces S and keeps the reflectors; k_schur_qr (one CTA)
+// runs the QR sweeps and the reordering on a packed copy of the Hessenberg matrix in shared
+// memory and logs every rotation; k_schur_q rebuilds Q from the reflectors and the rotation log,
+// one thread per row; k_schur_post forms the Ritz estimates, the selection and the truncation.
 #include "factor.cuh"
 
 namespace klst {
 
-
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 __device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }
 
+// 1/sqrt(x) by Newton-Raphson on y^-2 = x from a float32 seed: each step y <- y (3 - x y^2) / 2
+// doubles the correct bits (24 -> 48 -> full float64).  Only for x well inside the float32 range.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+
 // Givens rotation [c s; -conj(s) c] [f; g] = [r; 0] with real c (the LAPACK zlartg convention).
+// c = |f| / r and s = f conj(g) / (|f| r), r = sqrt(|f|^2 + |g|^2), formed with two reciprocal
+// square roots; magnitudes outside [1e-120, 1e120] take the hypot form below.
+__device__ void givens_ref(double2 f, double2 g, double& c, double2& s);
 __device__ void givens(double2 f, double2 g, double& c, double2& s) {
+    const double af2 = abs2(f), ag2 = abs2(g);
+    if (ag2 == 0.0) { c = 1.0; s = mk(0, 0); return; }
+    const double r2 = af2 + ag2;
+    if (af2 < 1e-240 || r2 > 1e240 || ag2 < 1e-240) { givens_ref(f, g, c, s); return; }
+    const double ir = rsqrt_nr(r2), iaf = rsqrt_nr(af2);
+    c = af2 * iaf * ir;
+    s = (iaf * ir) * (f * conj(g));
+}
+
+__device__ void givens_ref(double2 f, double2 g, double& c, double2& s) {
     const double af = cabs(f), ag = cabs(g);
     if (ag == 0.0) { c = 1.0; s = mk(0, 0); return; }
     if (af == 0.0) { c = 0.0; s = (1.0 / ag) * conj(g); return; }
@@ -42,27 +67,19 @@ __device__ double block_sum1(double v, double* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
+// ---------------------------------------------------------------- 1. Householder reduction
+__global__ void __launch_bounds__(256) k_schur_house(SchurArgs a) {
     const int m = a.m, tid = threadIdx.x, nt = blockDim.x;
-    double2 *H = a.H, *Q = a.Q;
+    double2* H = a.H;
     __shared__ double2 v[192];
-    __shared__ double rc[192];
-    __shared__ double2 rs[192];
     __shared__ double red[8];
-    __shared__ double s_c;
-    __shared__ double2 s_s, s_mu;
-    __shared__ int s_lo, s_q, s_fail;
-    const double2 beta = a.S[(size_t)(m - 1) * a.lds + m];
 #define HH(i, j) H[(size_t)(j) * m + (i)]
-#define QQ(i, j) Q[(size_t)(j) * m + (i)]
     for (int idx = tid; idx < m * m; idx += nt) {
         const int i = idx % m, j = idx / m;
         H[idx] = a.S[(size_t)j * a.lds + i];
-        Q[idx] = mk(i == j ? 1.0 : 0.0, 0.0);
     }
-    if (tid == 0) s_fail = 0;
+    for (int i = tid; i < m; i += nt) a.tau[i] = 0.0;
     __syncthreads();
-    // ---- Householder reduction to upper Hessenberg form
     for (int c = 0; c + 2 < m; ++c) {
         double tail = 0.0;
         for (int i = c + 2 + tid; i < m; i += nt) tail += abs2(HH(i, c));
@@ -74,9 +91,14 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
         const double2 ph = ax0 > 0 ? (1.0 / ax0) * x0 : mk(1, 0);
         const double2 bet = (-alpha) * ph;  // new subdiagonal entry
         const int len = m - c - 1;
-        for (int i = tid; i < len; i += nt) v[i] = (i == 0) ? x0 - bet : HH(c + 1 + i, c);
+        for (int i = tid; i < len; i += nt) {
+            const double2 vi = (i == 0) ? x0 - bet : HH(c + 1 + i, c);
+            v[i] = vi;
+            a.Vh[(size_t)c * m + c + 1 + i] = vi;
+        }
         __syncthreads();
         const double tau = 1.0 / (alpha * (alpha + ax0));  // 2 / ||v||^2
+        if (tid == 0) a.tau[c] = tau;
         // left: H[c+1:, col] -= tau v (v^H H[c+1:, col]) for col > c
         for (int col = c + 1 + tid; col < m; col += nt) {
             double2 g = mk(0, 0);
@@ -89,42 +111,58 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
             for (int i = c + 2; i < m; ++i) HH(i, c) = mk(0, 0);
         }
         __syncthreads();
-        // right: row[c+1:] -= tau (row[c+1:] v) v^H for H (all rows) and Q (all rows)
-        for (int row = tid; row < 2 * m; row += nt) {
-            double2* M = row < m ? H : Q;
-            const int rr = row < m ? row : row - m;
+        // right: row[c+1:] -= tau (row[c+1:] v) v^H for every row of H
+        for (int row = tid; row < m; row += nt) {
             double2 g = mk(0, 0);
-            for (int i = 0; i < len; ++i) cfma(g, M[(size_t)(c + 1 + i) * m + rr], v[i]);
+            for (int i = 0; i < len; ++i) cfma(g, HH(row, c + 1 + i), v[i]);
             g = tau * g;
-            for (int i = 0; i < len; ++i) M[(size_t)(c + 1 + i) * m + rr] = M[(size_t)(c + 1 + i) * m + rr] - g * conj(v[i]);
+            for (int i = 0; i < len; ++i) HH(row, c + 1 + i) = HH(row, c + 1 + i) - g * conj(v[i]);
         }
         __syncthreads();
     }
-    // ---- shifted QR iteration to the complex Schur form (full T and Q updates)
+#undef HH
+}
+
+// ---------------------------------------------------------------- 2. QR sweeps + reordering
+// Packed upper-Hessenberg storage: column j keeps rows 0..j+1 at offset j(j+3)/2.
+__device__ __forceinline__ int pk(int i, int j) { return j * (j + 3) / 2 + i; }
+
+__global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
+    extern __shared__ double2 sH[];
+    const int m = a.m, tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double rc[192];
+    __shared__ double2 rs[192];
+    __shared__ double s_c;
+    __shared__ double2 s_s, s_mu;
+    __shared__ int s_lo, s_q, s_fail, s_cnt;
+    for (int j = 0; j < m; ++j)
+        for (int i = tid; i <= min(j + 1, m - 1); i += nt) sH[pk(i, j)] = a.H[(size_t)j * m + i];
+    if (tid == 0) { s_fail = 0; s_cnt = 0; }
+    __syncthreads();
+#define TT(i, j) sH[pk(i, j)]
     int hi = m - 1, its = 0, total = 0;
-    const int max_total = 60 * m;
+    const int max_total = 30 * m;
     while (hi > 0) {
         if (tid == 0) {
             int l = hi;
             for (; l > 0; --l) {
-                const double sub = cabs1(HH(l, l - 1));
-                double sc = cabs1(HH(l - 1, l - 1)) + cabs1(HH(l, l));
+                const double sub = cabs1(TT(l, l - 1));
+                double sc = cabs1(TT(l - 1, l - 1)) + cabs1(TT(l, l));
                 if (sc == 0.0) sc = 1.0;
-                if (sub <= 2.220446049250313e-16 * sc || sub < 1e-300) { HH(l, l - 1) = mk(0, 0); break; }
+                if (sub <= 2.220446049250313e-16 * sc || sub < 1e-300) { TT(l, l - 1) = mk(0, 0); break; }
             }
             s_lo = l;
             if (l < hi) {
-                // Wilkinson shift from the trailing 2x2 of the active window; exceptional shifts
-                const double2 aa = HH(hi - 1, hi - 1), bb = HH(hi - 1, hi), cc = HH(hi, hi - 1), dd = HH(hi, hi);
+                const double2 aa = TT(hi - 1, hi - 1), bb = TT(hi - 1, hi), cc = TT(hi, hi - 1), dd = TT(hi, hi);
                 double2 mu;
                 if (its > 0 && its % 11 == 0) {
-                    mu = dd + mk(0.75 * cabs1(cc), 0.0);
+                    mu = dd + mk(0.75 * cabs1(cc), 0.0);  // exceptional shift
                 } else {
+                    // Wilkinson shift: eigenvalue of the trailing 2x2 nearer dd
                     const double2 hd = 0.5 * (aa - dd);
-                    double2 disc = hd * hd + bb * cc;
-                    // complex sqrt
+                    const double2 disc = hd * hd + bb * cc;
                     const double r = cabs(disc);
-                    double sr = sqrt(0.5 * (r + fabs(disc.x)));
+                    const double sr = sqrt(0.5 * (r + fabs(disc.x)));
                     double2 sq;
                     if (sr == 0.0) sq = mk(0, 0);
                     else if (disc.x >= 0) sq = mk(sr, disc.y / (2.0 * sr));
@@ -133,109 +171,164 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
                     mu = cabs(m1 - dd) < cabs(m2 - dd) ? m1 : m2;
                 }
                 s_mu = mu;
+                if (s_cnt + (hi - l) > a.log_cap) s_fail = 2;
             }
         }
         __syncthreads();
         const int lo = s_lo;
         if (lo == hi) { hi -= 1; its = 0; __syncthreads(); continue; }
-        if (++total > max_total) { if (tid == 0) { s_fail = 1; atomicOr(&a.st->flags, ST_NOCONV_QR); } break; }
+        if (s_fail || ++total > max_total) { if (tid == 0) s_fail = s_fail ? s_fail : 1; break; }
         ++its;
         const double2 mu = s_mu;
-        for (int i = lo + tid; i <= hi; i += nt) HH(i, i) = HH(i, i) - mu;
+        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = TT(i, i) - mu;
         __syncthreads();
-        // left rotations: triangularise the window of H - mu I
-        for (int i = lo; i < hi; ++i) {
-            if (tid == 0) {
-                double c; double2 s;
-                givens(HH(i, i), HH(i + 1, i), c, s);
-                s_c = c; s_s = s;
-                rc[i] = c; rs[i] = s;
-            }
-            __syncthreads();
-            const double c = s_c; const double2 s = s_s;
-            for (int col = i + tid; col < m; col += nt) {
-                double2 x = HH(i, col), y = HH(i + 1, col);
-                rot(x, y, c, s);
-                HH(i, col) = x; HH(i + 1, col) = y;
-            }
-            __syncthreads();
-        }
-        // right rotations: R Q^H, columns i, i+1, rows 0..i+1; accumulate into Q
+        if (tid == 0) givens(TT(lo, lo), TT(lo + 1, lo), rc[lo], rs[lo]);
+        __syncthreads();
+        // left sweep: rotation i on rows i, i+1 (columns i..m-1); the thread holding column i+1
+        // forms rotation i+1 from its freshly rotated diagonal entry
         for (int i = lo; i < hi; ++i) {
             const double c = rc[i];
             const double2 s = rs[i];
-            const double2 sc = conj(s);
-            for (int row = tid; row < m + (i + 2); row += nt) {
-                if (row < i + 2) {
-                    double2 x = HH(row, i), y = HH(row, i + 1);
-                    rot(x, y, c, sc);
-                    HH(row, i) = x; HH(row, i + 1) = y;
-                } else {
-                    const int qr = row - (i + 2);
-                    double2 x = QQ(qr, i), y = QQ(qr, i + 1);
-                    rot(x, y, c, sc);
-                    QQ(qr, i) = x; QQ(qr, i + 1) = y;
-                }
+            const int col = i + tid;
+            if (col < m) {
+                double2 x = TT(i, col), y = TT(i + 1, col);
+                rot(x, y, c, s);
+                TT(i, col) = x;
+                TT(i + 1, col) = (col == i) ? mk(0, 0) : y;
+                if (col == i + 1 && i + 1 < hi) givens(y, TT(i + 2, i + 1), rc[i + 1], rs[i + 1]);
             }
             __syncthreads();
         }
-        for (int i = lo + tid; i <= hi; i += nt) HH(i, i) = HH(i, i) + mu;
+        // right sweep in bulk: row r receives rotations i >= max(lo, r - 1), in order
+        for (int r = tid; r <= hi; r += nt) {
+            const int i0 = max(lo, r - 1);
+            if (i0 >= hi) continue;
+            double2 x = TT(r, i0);
+            for (int i = i0; i < hi; ++i) {
+                double2 y = TT(r, i + 1);
+                rot(x, y, rc[i], conj(rs[i]));
+                TT(r, i) = x;
+                x = y;
+            }
+            TT(r, hi) = x;
+        }
+        __syncthreads();
+        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = TT(i, i) + mu;
+        const int base = s_cnt;
+        for (int t = tid; t < hi - lo; t += nt) {
+            Rot g;
+            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = 0;
+            a.log[base + t] = g;
+        }
+        __syncthreads();
+        if (tid == 0) s_cnt = base + (hi - lo);
         __syncthreads();
     }
     __syncthreads();
-    if (s_fail) { if (tid == 0) *a.nconv = -1; return; }
-    for (int idx = tid; idx < m * m; idx += nt) {
-        const int i = idx % m, j = idx / m;
-        if (i > j) H[idx] = mk(0, 0);
+    if (s_fail) {
+        if (tid == 0) { atomicOr(&a.st->flags, ST_NOCONV_QR); *a.nconv = -1; *a.log_count = 0; }
+        return;
     }
+    for (int j = tid; j + 1 < m; j += nt) TT(j + 1, j) = mk(0, 0);
     __syncthreads();
-    // ---- reorder: bring the keep Ritz values of largest |mu| to the front (adjacent swaps)
+    // reorder: bring the keep Ritz values of largest |mu| to the front by adjacent swaps
     for (int p = 0; p < a.keep; ++p) {
         if (tid == 0) {
             int q = p;
-            double bv = cabs(HH(p, p));
+            double bv = cabs(TT(p, p));
             for (int i = p + 1; i < m; ++i) {
-                const double vv = cabs(HH(i, i));
+                const double vv = cabs(TT(i, i));
                 if (vv > bv) { bv = vv; q = i; }
             }
             s_q = q;
+            if (s_cnt + (q - p) > a.log_cap) { s_fail = 2; s_q = p; }
         }
         __syncthreads();
         const int q = s_q;
         for (int i = q - 1; i >= p; --i) {
             if (tid == 0) {
                 double c; double2 s;
-                givens(HH(i, i + 1), HH(i + 1, i + 1) - HH(i, i), c, s);
+                givens(TT(i, i + 1), TT(i + 1, i + 1) - TT(i, i), c, s);
                 s_c = c; s_s = s;
+                Rot g;
+                g.s = s; g.c = c; g.i = i; g.pad = 0;
+                a.log[s_cnt] = g;
+                s_cnt = s_cnt + 1;
             }
             __syncthreads();
-            const double c = s_c; const double2 s = s_s, sc = conj(s);
-            const double2 t11 = HH(i, i), t22 = HH(i + 1, i + 1);
-            __syncthreads();
-            for (int idx = tid; idx < (m - i - 2) + i + m; idx += nt) {
+            const double c = s_c;
+            const double2 s = s_s, sc = conj(s);
+            const double2 t11 = TT(i, i), t22 = TT(i + 1, i + 1);
+            for (int idx = tid; idx < (m - i - 2) + i; idx += nt) {
                 if (idx < m - i - 2) {
                     const int col = i + 2 + idx;
-                    double2 x = HH(i, col), y = HH(i + 1, col);
+                    double2 x = TT(i, col), y = TT(i + 1, col);
                     rot(x, y, c, s);
-                    HH(i, col) = x; HH(i + 1, col) = y;
-                } else if (idx < (m - i - 2) + i) {
-                    const int row = idx - (m - i - 2);
-                    double2 x = HH(row, i), y = HH(row, i + 1);
-                    rot(x, y, c, sc);
-                    HH(row, i) = x; HH(row, i + 1) = y;
+                    TT(i, col) = x; TT(i + 1, col) = y;
                 } else {
-                    const int row = idx - (m - i - 2) - i;
-                    double2 x = QQ(row, i), y = QQ(row, i + 1);
+                    const int row = idx - (m - i - 2);
+                    double2 x = TT(row, i), y = TT(row, i + 1);
                     rot(x, y, c, sc);
-                    QQ(row, i) = x; QQ(row, i + 1) = y;
+                    TT(row, i) = x; TT(row, i + 1) = y;
                 }
             }
-            if (tid == 0) { HH(i, i) = t22; HH(i + 1, i + 1) = t11; }
+            __syncthreads();
+            if (tid == 0) { TT(i, i) = t22; TT(i + 1, i + 1) = t11; }
             __syncthreads();
         }
     }
-    // ---- Ritz values, eigenvectors y of T (back substitution) and residual estimates for the
-    //      first keep positions (sorted by |mu|, largest first)
+    if (s_fail) {
+        if (tid == 0) { atomicOr(&a.st->flags, ST_NOCONV_QR); *a.nconv = -1; *a.log_count = 0; }
+        return;
+    }
+    // write T (upper triangular) back to global
+    for (int idx = tid; idx < m * m; idx += nt) {
+        const int i = idx % m, j = idx / m;
+        a.H[idx] = (i <= j) ? TT(i, j) : mk(0, 0);
+    }
+    if (tid == 0) *a.log_count = s_cnt;
+#undef TT
+}
+
+// ---------------------------------------------------------------- 3. Schur vectors
+// Row r of Q = e_r^T H_0 H_1 ... H_{m-3} G_1^H G_2^H ...: the reflectors, then every logged
+// rotation in order.  One thread per row; the row lives in shared memory (column-major over
+// the block's rows, so the 32 threads hit distinct banks).
+__global__ void __launch_bounds__(32) k_schur_q(SchurArgs a) {
+    extern __shared__ double2 q[];  // [m][32]
+    const int m = a.m, t = threadIdx.x, r = blockIdx.x * 32 + t;
+    for (int col = 0; col < m; ++col) q[col * 32 + t] = mk(col == r ? 1.0 : 0.0, 0.0);
+    for (int c = 0; c + 2 < m; ++c) {
+        const double tau = a.tau[c];
+        if (tau == 0.0) continue;
+        const double2* vc = a.Vh + (size_t)c * m;
+        double2 g = mk(0, 0);
+        for (int i = c + 1; i < m; ++i) cfma(g, q[i * 32 + t], vc[i]);
+        g = tau * g;
+        for (int i = c + 1; i < m; ++i) q[i * 32 + t] = q[i * 32 + t] - g * conj(vc[i]);
+    }
+    const int nrot = *a.log_count;
+    for (int k = 0; k < nrot; ++k) {
+        const Rot g = a.log[k];
+        double2 x = q[g.i * 32 + t], y = q[(g.i + 1) * 32 + t];
+        rot(x, y, g.c, conj(g.s));
+        q[g.i * 32 + t] = x;
+        q[(g.i + 1) * 32 + t] = y;
+    }
+    if (r < m)
+        for (int col = 0; col < m; ++col) a.Q[(size_t)col * m + r] = q[col * 32 + t];
+}
+
+// ---------------------------------------------------------------- 4. Ritz pairs, selection, truncation
+__global__ void __launch_bounds__(256) k_schur_post(SchurArgs a) {
+    const int m = a.m, tid = threadIdx.x, nt = blockDim.x;
+    if (*a.nconv < 0) return;  // the QR step failed; the host reports it
+    double2 *H = a.H, *Q = a.Q;
+    const double2 beta = a.S[(size_t)(m - 1) * a.lds + m];
+#define HH(i, j) H[(size_t)(j) * m + (i)]
+#define QQ(i, j) Q[(size_t)(j) * m + (i)]
+    // Ritz values, eigenvectors y of T (back substitution) and residual estimates for the
+    // first keep positions (sorted by |mu|, largest first)
     __shared__ int s_sel[192];
     for (int i = tid; i < m; i += nt) a.mu[i] = HH(i, i);
     const double ulp = 2.220446049250313e-16;
@@ -261,9 +354,9 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
         for (int i = 0; i <= p; ++i) y[i] = (1.0 / nrm) * y[i];
     }
     __syncthreads();
-    // ---- selection: the nev nearest converged Ritz pairs.  An unconverged Ritz value nearer the
-    //      shift may only be passed over when it lies in a cluster with the last selected one
-    //      (|omega - sigma| within 1%), where the order inside the cluster is not resolved.
+    // selection: the nev nearest converged Ritz pairs.  An unconverged Ritz value nearer the
+    // shift may only be passed over when it lies in a cluster with the last selected one
+    // (|omega - sigma| within 1%), where the order inside the cluster is not resolved.
     if (tid == 0) {
         int ns = 0, lead = 0;
         bool leading = true;
@@ -302,7 +395,7 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
         a.Ysel[(size_t)i * m + row] = acc;
     }
     __syncthreads();
-    // ---- truncated Krylov-Schur relation: S[0:k,0:k] = T_kk, S[k,0:k] = beta Q[m-1, 0:k]
+    // truncated Krylov-Schur relation: S[0:k,0:k] = T_kk, S[k,0:k] = beta Q[m-1, 0:k]
     const int k = a.keep;
     for (int idx = tid; idx < a.lds * m; idx += nt) {
         const int i = idx % a.lds, j = idx / a.lds;
@@ -318,7 +411,26 @@ __global__ void __launch_bounds__(256) k_schur(SchurArgs a) {
 }
 
 int launch_schur(const SchurArgs& a, cudaStream_t s) {
-    k_schur<<<1, 256, 0, s>>>(a);
+    static bool attr = false;
+    if (!attr) {
+        KLST_CK(cudaFuncSetAttribute(k_schur_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+        KLST_CK(cudaFuncSetAttribute(k_schur_q, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        attr = true;
+    }
+    const int m = a.m;
+    const size_t packed = sizeof(double2) * (size_t)m * (m + 3) / 2;
+    prof_begin("schur_house", s);
+    k_schur_house<<<1, 256, 0, s>>>(a);
+    prof_end("schur_house", s);
+    prof_begin("schur_qr", s);
+    k_schur_qr<<<1, 256, packed, s>>>(a);
+    prof_end("schur_qr", s);
+    prof_begin("schur_q", s);
+    k_schur_q<<<(m + 31) / 32, 32, sizeof(double2) * 32 * m, s>>>(a);
+    prof_end("schur_q", s);
+    prof_begin("schur_post", s);
+    k_schur_post<<<1, 256, 0, s>>>(a);
+    prof_end("schur_post", s);
     KLST_CK_LAUNCH();
     return KLST_OK;
 }

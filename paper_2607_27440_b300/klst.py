@@ -36,7 +36,8 @@ class EigsInfo(ctypes.Structure):
     _fields_ = [("nconv", c_int32), ("restarts", c_int32), ("applies", c_int32), ("refine_sweeps", c_int32),
                 ("t_factor_ms", c_double), ("t_eigs_ms", c_double), ("max_resid", c_double),
                 ("max_refine_resid", c_double), ("t_apply_ms", c_double), ("t_orth_ms", c_double),
-                ("t_restart_ms", c_double), ("t_schur_ms", c_double)]
+                ("t_restart_ms", c_double), ("t_schur_ms", c_double),
+                ("reorths", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
