@@ -45,7 +45,7 @@ typedef enum {
     KLST_ESINGULAR = -3,  /* zero pivot: a shifted block or the capacitance matrix is singular */
     KLST_ENOCONV = -4,    /* eigensolver reached max_restarts before nev pairs converged */
     KLST_EREFINE = -5,    /* mixed-precision refinement did not reach its tolerance */
-    KLST_ETIMEOUT = -6,   /* a bounded device-side wait gave up (grid barrier) */
+    KLST_ETIMEOUT = -6,   /* reserved: a bounded device-side wait gave up (no current call waits on the device) */
     KLST_ECUDA = -7       /* a CUDA runtime call failed */
 } klst_status;
 
@@ -177,9 +177,9 @@ size_t klst_apply_pencil_noalloc_capacity(void);
  * inflow rows replaced by identity rows; shared by g^ and h^) and U V^H is the
  * rank-4-per-point BGK moment coupling.  Computes every K_k^{-1} (batched
  * Gauss-Jordan with partial pivoting), the capacitance C = I - V^H K^{-1} U
- * (4 Nx x 4 Nx) and C^{-1}.  precision: KLST_FP64 (all float64) or KLST_MIXED
+ * (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan, one launch per pivot).  precision: KLST_FP64 (all float64) or KLST_MIXED
  * (K_k^{-1} in complex float32, corrected by float64 refinement in the apply).
- * Errors: KLST_ESINGULAR (zero pivot), KLST_ENOMEM, KLST_ETIMEOUT.  Synchronising.
+ * Errors: KLST_ESINGULAR (zero pivot), KLST_ENOMEM.  Synchronising.
  */
 int klst_factor_shift(klst_pencil p, double sigma_re, double sigma_im, int32_t precision,
                       klst_stream stream, klst_factor* out);
@@ -221,6 +221,42 @@ int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol)
  */
 int klst_eigs(klst_factor f, const klst_eigs_opts* opts, double* evals_host, void* evecs,
               double* resid_host, klst_eigs_info* info, klst_stream stream);
+
+/*
+ * klst_batch_eigs -- many independent pencils at once (wavenumber, shift and Mach sweeps): pencil i
+ * (descs[i], shift sigmas[2i] + i sigmas[2i+1]) is built, factored and solved for the opts->nev
+ * eigenvalues nearest its shift, exactly as klst_build_pencil + klst_factor_shift + klst_eigs would,
+ * with its start vector seeded by opts->seed + i (opts->v0 must be NULL).  nworkers host threads
+ * (0 = 16) each own one non-blocking stream, so pencils overlap on the device; each pencil's result
+ * is bit-for-bit the one it gets alone.  Outputs (host): evals_host complex128[npencils * nev]
+ * (pencil-major), resid_host float64[npencils * nev] (may be NULL), status_host int32[npencils],
+ * infos[npencils] (may be NULL).  Returns KLST_OK when every pencil succeeded, otherwise the first
+ * failing status (each pencil's own status is in status_host).  Synchronising.
+ */
+int klst_batch_eigs(int32_t npencils, const klst_pencil_desc* descs, const double* sigmas, int32_t precision,
+                    const klst_eigs_opts* opts, int32_t nworkers, double* evals_host, double* resid_host,
+                    int32_t* status_host, klst_eigs_info* infos);
+
+/*
+ * Serving: a request loop that admits eigensolve requests by device-memory footprint.
+ * klst_server_create starts max_slots worker threads (one stream each); a submitted request waits in
+ * arrival order until a slot is free and its footprint fits in hbm_budget_bytes together with the
+ * requests already running (a later, smaller request may pass a head request that must wait for
+ * memory).  Requests run concurrently, each on its worker's stream, with results bit-for-bit equal to
+ * a solve alone.  klst_server_submit copies its arguments (opts->v0 must be NULL; the seed is
+ * opts->seed); KLST_ENOMEM if the request alone exceeds the budget.  klst_server_poll (wait != 0
+ * blocks) reports done = 1 once finished, copies evals_host complex128[nev], resid_host float64[nev],
+ * info, and the latency from submit to completion in ms, releases the ticket and returns the solve's
+ * status; a finished ticket can be polled once.  Thread-safe (internally locked).
+ */
+typedef struct klst_server_s* klst_server;
+int klst_server_create(int64_t hbm_budget_bytes, int32_t max_slots, klst_server* out);
+int klst_server_submit(klst_server s, const klst_pencil_desc* desc, double sigma_re, double sigma_im,
+                       int32_t precision, const klst_eigs_opts* opts, uint64_t* ticket);
+int klst_server_poll(klst_server s, uint64_t ticket, int32_t wait, int32_t* done, double* evals_host,
+                     double* resid_host, klst_eigs_info* info, double* latency_ms);
+int klst_server_stats(klst_server s, int32_t* queued, int32_t* running, int64_t* bytes_in_flight);
+void klst_server_destroy(klst_server s);
 
 #ifdef __cplusplus
 }

@@ -204,7 +204,7 @@ static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y,
 }
 
 int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t s) {
-    int rc = factor_reserve(f, nrhs);
+    int rc = factor_reserve(f, nrhs, s);
     if (rc) return rc;
     if (f->precision == KLST_FP64) return woodbury_solve<double2>(f, x, 1, y, 0, nrhs, s, nullptr);
     klst_pencil p = f->p;

@@ -24,7 +24,6 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 // device status bits (klst::Status::flags)
 enum : int {
     ST_SINGULAR = 1,   // zero pivot in a block or capacitance inverse
-    ST_TIMEOUT = 2,    // bounded grid barrier gave up
     ST_NOCONV_QR = 4,  // small Schur QR iteration limit
     ST_BREAKDOWN = 8   // Arnoldi breakdown (invariant subspace)
 };
@@ -108,6 +107,7 @@ struct klst_pencil_s {
     double* w;      // [((k*2 + c)*4 + a)*nx + j] moment functionals
     klst::Status* status;
     int64_t footprint;
+    cudaStream_t stream;  // stream of the last call (the handle's memory is released on it)
 };
 
 namespace klst {
@@ -117,37 +117,13 @@ __host__ __device__ __forceinline__ bool is_bc(int j, int nx, double xix) {
     return (j == nx - 1 && xix > 0.0) || (j == 0 && xix < 0.0);
 }
 
-// bounded, sense-reversing grid barrier for cooperative launches; returns false on timeout
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks,
-                                             int* flags) {
-    __syncthreads();
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = gen;
-        unsigned int my = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(count, 1u);
-        int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == my) {
-                if (++spins > (1ll << 24)) { atomicOr(flags, ST_TIMEOUT); ok = 0; break; }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        if (*(volatile int*)flags & ST_TIMEOUT) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 int device_sm_count();
+
+// Stream-ordered device memory (cudaMallocAsync on the device's default pool, whose release
+// threshold is raised once so freed blocks stay cached): allocations on different streams do
+// not serialise the device the way cudaMalloc/cudaFree do.
+cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s);
+void dfree(void* ptr, cudaStream_t s);
 
 }  // namespace klst
 

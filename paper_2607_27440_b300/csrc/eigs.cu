@@ -216,9 +216,9 @@ struct EigsWork {
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
     std::vector<cudaEvent_t> evs;
-    void release() {
+    void release(cudaStream_t st) {
         void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
-        for (void* p : b) cudaFree(p);
+        for (void* p : b) dfree(p, st);
         for (auto& ev : evs) cudaEventDestroy(ev);
         evs.clear();
     }
@@ -261,13 +261,13 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     cudaError_t e;
     int rc = KLST_OK;
     auto fail = [&](int code) {
-        W.release();
+        W.release(s);
         f->max_refine = prev_refine;
         f->refine_tol = prev_rtol;
         return code;
     };
 #define EALLOC(ptr, cnt)                                                                     \
-    if ((e = cudaMalloc((void**)&(ptr), sizeof(*(ptr)) * (size_t)(cnt))) != cudaSuccess)      \
+    if ((e = dmalloc((void**)&(ptr), sizeof(*(ptr)) * (size_t)(cnt), s)) != cudaSuccess)      \
         return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     EALLOC(W.Va, n * (m + 1));
     EALLOC(W.Vb, n * (m + 1));
@@ -303,7 +303,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     KLST_CK(cudaMemsetAsync(f->status, 0, sizeof(Status), s));
     KLST_CK(cudaMemsetAsync(f->worst, 0, sizeof(double), s));
     KLST_CK(cudaMemsetAsync(f->sweeps, 0, sizeof(int), s));
-    if ((rc = factor_reserve(f, std::max(nev, 1))) != KLST_OK) return fail(rc);
+    if ((rc = factor_reserve(f, std::max(nev, 1), s)) != KLST_OK) return fail(rc);
     double2 *V = W.Va, *Valt = W.Vb;
     // start: v0 (given or seeded), V[:,0] = T v0 / ||T v0|| (range of T: no B-null components)
     double2* v0 = Valt;
@@ -412,11 +412,11 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     double2* Rr = nullptr;
     const bool room = 3 * nev <= m + 1;
     if (!room) {
-        if ((e = cudaMalloc(&W.Z, sizeof(double2) * n * nev)) != cudaSuccess ||
-            (e = cudaMalloc(&W.R, sizeof(double2) * n * nev)) != cudaSuccess)
+        if ((e = dmalloc((void**)&W.Z, sizeof(double2) * n * nev, s)) != cudaSuccess ||
+            (e = dmalloc((void**)&W.R, sizeof(double2) * n * nev, s)) != cudaSuccess)
             return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
         if (2 * nev > m + 1) {
-            if ((e = cudaMalloc(&W.X, sizeof(double2) * n * nev)) != cudaSuccess)
+            if ((e = dmalloc((void**)&W.X, sizeof(double2) * n * nev, s)) != cudaSuccess)
                 return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
             X = W.X;
         }
@@ -484,7 +484,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         info->t_schur_ms = t_schur;
         info->reorths = reorths;
     }
-    W.release();
+    W.release(s);
     f->max_refine = prev_refine;
     f->refine_tol = prev_rtol;
     if (!converged) { set_error("only %d of %d eigenpairs converged after %d restarts", nconv, nev, restarts); return KLST_ENOCONV; }

@@ -2,10 +2,11 @@
 // restated for the structure of the kLST pencil: A - sigma B = K - U V^H with one Nx x Nx block
 // K_k per micro-velocity node (shared by g^ and h^) and the rank-4-per-point moment coupling.
 // K_k^{-1} by batched Gauss-Jordan with partial pivoting, the capacitance C = I - V^H K^{-1} U
-// and C^{-1} by a cooperative Gauss-Jordan over all SMs.
+// and C^{-1} by Gauss-Jordan over all SMs, one launch per pivot step.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "factor.cuh"
@@ -159,80 +160,75 @@ __global__ void k_cap_reduce(int r, int nsplit, const double2* __restrict__ Cp, 
     }
 }
 
-// Cooperative Gauss-Jordan inverse of an r x r complex128 matrix (row-major) over all CTAs.
-// Step p reads buffer p%2 and writes buffer (p+1)%2 (every entry is rewritten), so one grid
-// barrier per step suffices.  Every CTA repeats the pivot search on the same data, so all
-// agree on the pivot row without communication.  The final column un-permutation writes
-// buffer (r+1)%2.
-__global__ void __launch_bounds__(256) k_gj_coop(int r, double2* buf0, double2* buf1, unsigned int* bar,
-                                                 Status* st) {
+// Gauss-Jordan inverse of an r x r complex128 matrix (row-major), one launch per pivot step.
+// Step p reads buffer p%2 and writes buffer (p+1)%2 (every entry is rewritten), so consecutive
+// launches on the stream order the steps without any grid-wide barrier.  Every CTA repeats the
+// pivot search on the same column, so all agree on the pivot row; CTA 0 records it.
+__global__ void __launch_bounds__(256) k_gj_step(int r, int p, const double2* __restrict__ src, double2* __restrict__ dst,
+                                                 int* __restrict__ perm, Status* st) {
     extern __shared__ double2 sh[];
     double2* prow = sh;       // pivot row
     double2* rowp = sh + r;   // row p of the source (moves to the pivot row's slot)
-    int* perm = (int*)(sh + 2 * r);
     __shared__ double rv[8];
     __shared__ int ri[8];
     __shared__ int s_piv;
-    const int tid = threadIdx.x, nt = blockDim.x, G = gridDim.x;
-    const int rows_per = (r + G - 1) / G;
-    const int r0 = blockIdx.x * rows_per, r1 = min(r, r0 + rows_per);
-    for (int p = 0; p < r; ++p) {
-        const double2* src = (p & 1) ? buf1 : buf0;
-        double2* dst = (p & 1) ? buf0 : buf1;
-        double best = -1;
-        int bi = r;
-        for (int i = p + tid; i < r; i += nt) {
-            double v = abs2(src[(size_t)i * r + p]);
-            if (v > best) { best = v; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-            double b = rv[0];
-            int i0 = ri[0];
-            for (int w = 1; w < (nt >> 5); ++w)
-                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
-            if (!(b > 0) && blockIdx.x == 0) atomicOr(&st->flags, ST_SINGULAR);
-            s_piv = i0 < r ? i0 : p;
-            perm[p] = s_piv;
-        }
-        __syncthreads();
-        const int piv = s_piv;
-        for (int c = tid; c < r; c += nt) { prow[c] = src[(size_t)piv * r + c]; rowp[c] = src[(size_t)p * r + c]; }
-        __syncthreads();
-        double2 inv = prow[p];
-        if (!(abs2(inv) > 0)) inv.x = 1;
-        inv = cinv(inv);
-        for (int idx = tid; idx < (r1 - r0) * r; idx += nt) {
-            const int i = r0 + idx / r, c = idx % r;
-            double2 v;
-            if (i == p) v = (c == p) ? inv : prow[c] * inv;
-            else {
-                const double2 sv = (i == piv) ? rowp[c] : src[(size_t)i * r + c];
-                const double2 f = ((i == piv) ? rowp[p] : src[(size_t)i * r + p]) * inv;
-                v = (c == p) ? -f : sv - f * prow[c];
-            }
-            dst[(size_t)i * r + c] = v;
-        }
-        if (!grid_barrier(bar, bar + 1, G, &st->flags)) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double best = -1;
+    int bi = r;
+    for (int i = p + tid; i < r; i += nt) {
+        const double v = abs2(src[(size_t)i * r + p]);
+        if (v > best) { best = v; bi = i; }
     }
-    // column un-permutation: apply the swaps (p, perm[p]) for p = r-1..0 as a gather
-    int* idxmap = perm + r;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+    __syncthreads();
     if (tid == 0) {
-        for (int c = 0; c < r; ++c) idxmap[c] = c;
-        for (int p = r - 1; p >= 0; --p) { int q = perm[p], t = idxmap[p]; idxmap[p] = idxmap[q]; idxmap[q] = t; }
+        double b = rv[0];
+        int i0 = ri[0];
+        for (int w = 1; w < (nt >> 5); ++w)
+            if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+        if (!(b > 0) && blockIdx.x == 0) atomicOr(&st->flags, ST_SINGULAR);
+        s_piv = i0 < r ? i0 : p;
+        if (blockIdx.x == 0) perm[p] = s_piv;
     }
     __syncthreads();
-    const double2* fin = (r & 1) ? buf1 : buf0;
-    double2* res = (r & 1) ? buf0 : buf1;
+    const int piv = s_piv;
+    for (int c = tid; c < r; c += nt) { prow[c] = src[(size_t)piv * r + c]; rowp[c] = src[(size_t)p * r + c]; }
+    __syncthreads();
+    double2 inv = prow[p];
+    if (!(abs2(inv) > 0)) inv.x = 1;
+    inv = cinv(inv);
+    const int rows_per = (r + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * rows_per, r1 = min(r, r0 + rows_per);
     for (int idx = tid; idx < (r1 - r0) * r; idx += nt) {
         const int i = r0 + idx / r, c = idx % r;
-        res[(size_t)i * r + c] = fin[(size_t)i * r + idxmap[c]];
+        double2 v;
+        if (i == p) v = (c == p) ? inv : prow[c] * inv;
+        else {
+            const double2 sv = (i == piv) ? rowp[c] : src[(size_t)i * r + c];
+            const double2 f = ((i == piv) ? rowp[p] : src[(size_t)i * r + p]) * inv;
+            v = (c == p) ? -f : sv - f * prow[c];
+        }
+        dst[(size_t)i * r + c] = v;
+    }
+}
+
+// Undo the row interchanges as column interchanges (p, perm[p]) for p = r-1..0, as a gather.
+__global__ void __launch_bounds__(256) k_gj_unpermute(int r, const double2* __restrict__ fin, double2* __restrict__ res,
+                                                      const int* __restrict__ perm) {
+    extern __shared__ int idxmap[];
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < r; ++c) idxmap[c] = c;
+        for (int p = r - 1; p >= 0; --p) { const int q = perm[p], t = idxmap[p]; idxmap[p] = idxmap[q]; idxmap[q] = t; }
+    }
+    __syncthreads();
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)r * r; idx += gridDim.x * (size_t)blockDim.x) {
+        const size_t i = idx / r, c = idx % r;
+        res[idx] = fin[i * r + idxmap[c]];
     }
 }
 
@@ -266,29 +262,31 @@ __global__ void k_round_c64(const double2* __restrict__ in, float2* __restrict__
     }
 }
 
-int factor_reserve(klst_factor f, int nrhs) {
+int factor_reserve(klst_factor f, int nrhs, cudaStream_t s) {
+    f->stream = s;
     if (nrhs <= f->nrhs_cap) return KLST_OK;
-    cudaFree(f->tpart); cudaFree(f->t); cudaFree(f->sv); cudaFree(f->bwork); cudaFree(f->rwork);
-    cudaFree(f->normpart); cudaFree(f->done); cudaFree(f->sigma_dev);
+    dfree(f->tpart, s); dfree(f->t, s); dfree(f->sv, s); dfree(f->bwork, s); dfree(f->rwork, s);
+    dfree(f->normpart, s); dfree(f->done, s); dfree(f->sigma_dev, s);
     f->sigma_dev = nullptr;
     f->tpart = f->t = f->sv = f->bwork = f->rwork = nullptr;
     f->normpart = nullptr;
     f->done = nullptr;
     f->nrhs_cap = 0;
     const size_t r = f->r, n = f->n;
-    KLST_CK(cudaMalloc(&f->tpart, sizeof(double2) * nrhs * (size_t)f->ngroups * r));
-    KLST_CK(cudaMalloc(&f->t, sizeof(double2) * nrhs * r));
-    KLST_CK(cudaMalloc(&f->sv, sizeof(double2) * nrhs * r));
+    KLST_CK(dmalloc((void**)&f->tpart, sizeof(double2) * nrhs * (size_t)f->ngroups * r, s));
+    KLST_CK(dmalloc((void**)&f->t, sizeof(double2) * nrhs * r, s));
+    KLST_CK(dmalloc((void**)&f->sv, sizeof(double2) * nrhs * r, s));
     if (f->precision == KLST_MIXED) {
-        KLST_CK(cudaMalloc(&f->bwork, sizeof(double2) * nrhs * n));
-        KLST_CK(cudaMalloc(&f->rwork, sizeof(double2) * nrhs * n));
+        KLST_CK(dmalloc((void**)&f->bwork, sizeof(double2) * nrhs * n, s));
+        KLST_CK(dmalloc((void**)&f->rwork, sizeof(double2) * nrhs * n, s));
     }
-    KLST_CK(cudaMalloc(&f->normpart, sizeof(double) * nrhs * 2 * 4096));
-    KLST_CK(cudaMalloc(&f->done, sizeof(int) * nrhs));
-    KLST_CK(cudaMalloc(&f->sigma_dev, sizeof(double2) * nrhs));
+    KLST_CK(dmalloc((void**)&f->normpart, sizeof(double) * nrhs * 2 * 4096, s));
+    KLST_CK(dmalloc((void**)&f->done, sizeof(int) * nrhs, s));
+    KLST_CK(dmalloc((void**)&f->sigma_dev, sizeof(double2) * nrhs, s));
     {
         std::vector<double2> sg(nrhs, f->sigma);
-        KLST_CK(cudaMemcpy(f->sigma_dev, sg.data(), sizeof(double2) * nrhs, cudaMemcpyHostToDevice));
+        KLST_CK(cudaMemcpyAsync(f->sigma_dev, sg.data(), sizeof(double2) * nrhs, cudaMemcpyHostToDevice, s));
+        KLST_CK(cudaStreamSynchronize(s));
     }
     f->nrhs_cap = nrhs;
     return KLST_OK;
@@ -300,9 +298,10 @@ using namespace klst;
 
 extern "C" void klst_factor_destroy(klst_factor f) {
     if (!f) return;
-    cudaFree(f->KinvT); cudaFree(f->Cinv);
-    cudaFree(f->tpart); cudaFree(f->t); cudaFree(f->sv); cudaFree(f->bwork); cudaFree(f->rwork);
-    cudaFree(f->normpart); cudaFree(f->done); cudaFree(f->sigma_dev); cudaFree(f->worst); cudaFree(f->sweeps); cudaFree(f->status);
+    cudaStream_t s = f->stream;
+    void* bufs[] = {f->KinvT, f->Cinv, f->tpart, f->t, f->sv, f->bwork, f->rwork, f->normpart, f->done,
+                    f->sigma_dev, f->worst, f->sweeps, f->status};
+    for (void* b : bufs) dfree(b, s);
     delete f;
 }
 
@@ -316,6 +315,7 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     klst_factor f = new klst_factor_s();
     memset(f, 0, sizeof(*f));
     f->p = p;
+    f->stream = s;
     f->sigma = mk(sr, si);
     f->precision = precision;
     f->nx = p->nx; f->nxi = p->nxi; f->r = 4 * p->nx; f->n = p->n;
@@ -326,15 +326,15 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     const size_t esz = precision == KLST_FP64 ? sizeof(double2) : sizeof(float2);
     const int nsplit = std::max(1, std::min(p->nxi, 8));
     double2 *Cp = nullptr, *b0 = nullptr, *b1 = nullptr;
-    unsigned int* bar = nullptr;
+    int* bar = nullptr;
     auto fail = [&](int code) {
-        cudaFree(Cp); cudaFree(b0); cudaFree(b1); cudaFree(bar);
+        dfree(Cp, s); dfree(b0, s); dfree(b1, s); dfree(bar, s);
         klst_factor_destroy(f);
         return code;
     };
     cudaError_t e;
 #define FALLOC(ptr, bytes)                                                                       \
-    if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__)); \
+    if ((e = dmalloc((void**)&(ptr), (bytes), s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__)); \
     f->footprint += (int64_t)(bytes);
     FALLOC(f->KinvT, esz * (size_t)p->nxi * p->nx * p->nx);
     FALLOC(f->Cinv, sizeof(double2) * (size_t)r * r);
@@ -342,24 +342,23 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     FALLOC(f->sweeps, sizeof(int));
     FALLOC(f->status, sizeof(Status));
 #undef FALLOC
-    if ((e = cudaMalloc(&Cp, sizeof(double2) * (size_t)nsplit * r * r)) != cudaSuccess ||
-        (e = cudaMalloc(&b0, sizeof(double2) * (size_t)r * r)) != cudaSuccess ||
-        (e = cudaMalloc(&b1, sizeof(double2) * (size_t)r * r)) != cudaSuccess ||
-        (e = cudaMalloc(&bar, sizeof(unsigned int) * 2)) != cudaSuccess)
+    if ((e = dmalloc((void**)&Cp, sizeof(double2) * (size_t)nsplit * r * r, s)) != cudaSuccess ||
+        (e = dmalloc((void**)&b0, sizeof(double2) * (size_t)r * r, s)) != cudaSuccess ||
+        (e = dmalloc((void**)&b1, sizeof(double2) * (size_t)r * r, s)) != cudaSuccess ||
+        (e = dmalloc((void**)&bar, sizeof(int) * r, s)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     cudaMemsetAsync(f->status, 0, sizeof(Status), s);
     cudaMemsetAsync(f->worst, 0, sizeof(double), s);
     cudaMemsetAsync(f->sweeps, 0, sizeof(int), s);
-    cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 2, s);
     // The block inverses are always formed in float64 (the capacitance is built from them); the
     // mixed factor then stores them rounded to complex float32, so the float32 solve carries only
     // the rounding of its operands and not the float32 elimination error.
     double2* K64 = (double2*)f->KinvT;
     if (precision == KLST_MIXED) {
-        if ((e = cudaMalloc(&K64, sizeof(double2) * (size_t)p->nxi * p->nx * p->nx)) != cudaSuccess)
+        if ((e = dmalloc((void**)&K64, sizeof(double2) * (size_t)p->nxi * p->nx * p->nx, s)) != cudaSuccess)
             return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     }
-    auto free64 = [&]() { if (precision == KLST_MIXED) cudaFree(K64); };
+    auto free64 = [&]() { if (precision == KLST_MIXED) dfree(K64, s); };
     int rc = launch_block_gj<double2>(f, K64, s);
     if (rc) { free64(); return fail(rc); }
     rc = launch_cap<double2>(f, K64, Cp, nsplit, s);
@@ -368,20 +367,19 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
         const size_t cnt = (size_t)p->nxi * p->nx * p->nx;
         k_round_c64<<<(int)std::min<size_t>((cnt + 255) / 256, 8192), 256, 0, s>>>(K64, (float2*)f->KinvT, cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) { free64(); return fail(cuda_fail(e, "round", __FILE__, __LINE__)); }
-        cudaStreamSynchronize(s);
         free64();
     }
     k_cap_reduce<<<std::min(1024, (r * r + 255) / 256), 256, 0, s>>>(r, nsplit, Cp, b0);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "cap reduce", __FILE__, __LINE__));
     {
-        int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
-        size_t smem = sizeof(double2) * 2 * r + sizeof(int) * 2 * r;
-        int rr = r;
-        double2 *pb0 = b0, *pb1 = b1;
-        Status* pst = f->status;
-        void* args[] = {&rr, &pb0, &pb1, &bar, &pst};
-        e = cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3(nb), dim3(256), args, smem, s);
-        if (e != cudaSuccess) return fail(cuda_fail(e, "cooperative capacitance inverse", __FILE__, __LINE__));
+        const int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
+        const size_t smem = sizeof(double2) * 2 * r;
+        int* perm = (int*)bar;
+        for (int p = 0; p < r; ++p)
+            k_gj_step<<<nb, 256, smem, s>>>(r, p, (p & 1) ? b1 : b0, (p & 1) ? b0 : b1, perm, f->status);
+        k_gj_unpermute<<<std::min(1024, (r * r + 255) / 256), 256, sizeof(int) * r, s>>>(r, (r & 1) ? b1 : b0,
+                                                                                        (r & 1) ? b0 : b1, perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "capacitance inverse", __FILE__, __LINE__));
     }
     double2* res = (r & 1) ? b0 : b1;
     if ((e = cudaMemcpyAsync(f->Cinv, res, sizeof(double2) * (size_t)r * r, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -390,15 +388,14 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if ((e = cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(cuda_fail(e, "factor sync", __FILE__, __LINE__));
-    cudaFree(Cp); cudaFree(b0); cudaFree(b1); cudaFree(bar);
+    dfree(Cp, s); dfree(b0, s); dfree(b1, s); dfree(bar, s);
     Cp = b0 = b1 = nullptr;
     bar = nullptr;
-    if (hst.flags & ST_TIMEOUT) { set_error("capacitance inverse: grid barrier timed out"); return fail(KLST_ETIMEOUT); }
     if (hst.flags & ST_SINGULAR) {
         set_error("zero pivot: a shifted block K_k - sigma or the capacitance matrix is singular");
         return fail(KLST_ESINGULAR);
     }
-    if ((rc = factor_reserve(f, 1)) != KLST_OK) return fail(rc);
+    if ((rc = factor_reserve(f, 1, s)) != KLST_OK) return fail(rc);
     f->t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = f;
     return KLST_OK;

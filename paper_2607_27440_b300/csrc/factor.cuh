@@ -28,6 +28,7 @@ struct klst_factor_s {
     double t_factor_ms;
     int64_t footprint;
     klst::Status* status;
+    cudaStream_t stream;  // stream of the last call (the handle's memory is released on it)
 };
 
 namespace klst {
@@ -63,7 +64,7 @@ struct SchurArgs {
 };
 
 int launch_schur(const SchurArgs& a, cudaStream_t s);
-int factor_reserve(klst_factor f, int nrhs);
+int factor_reserve(klst_factor f, int nrhs, cudaStream_t s);
 // y = T x on the factor's stream; x, y complex128 n x nrhs
 int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t s);
 // y = (A - omega_r B) x_r (omega on device, nrhs entries)

@@ -24,6 +24,27 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? KLST_ENOMEM : KLST_ECUDA;
 }
 
+cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s) {
+    static bool pool_ready[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !pool_ready[dev]) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        pool_ready[dev] = true;
+    }
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    return cudaMallocAsync(ptr, bytes, s);
+}
+
+void dfree(void* ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync(ptr, s);
+}
+
 int device_sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -406,8 +427,8 @@ extern "C" const char* klst_last_error(void) { return g_err; }
 extern "C" void klst_pencil_destroy(klst_pencil p) {
     if (!p) return;
     double* bufs[] = {p->x, p->Dx, p->DxT, p->xi_x, p->xi_y, p->W, p->nu, p->macro, p->G, p->w};
-    for (double* b : bufs) cudaFree(b);
-    cudaFree(p->status);
+    for (double* b : bufs) dfree(b, p->stream);
+    dfree(p->status, p->stream);
     delete p;
 }
 
@@ -432,10 +453,11 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
     p->n = 2ll * p->nx * p->nxi;
     const int nx = p->nx, nxi = p->nxi;
     double *gh = nullptr, *Wq = nullptr, *gbuf = nullptr;
-    auto fail = [&](int code) { cudaFree(gh); cudaFree(Wq); cudaFree(gbuf); klst_pencil_destroy(p); return code; };
+    p->stream = s;
+    auto fail = [&](int code) { dfree(gh, s); dfree(Wq, s); dfree(gbuf, s); klst_pencil_destroy(p); return code; };
 #define ALLOC(ptr, cnt)                                                              \
     do {                                                                             \
-        cudaError_t e_ = cudaMalloc((void**)&(ptr), (size_t)(cnt) * sizeof(*(ptr))); \
+        cudaError_t e_ = dmalloc((void**)&(ptr), (size_t)(cnt) * sizeof(*(ptr)), s); \
         if (e_ != cudaSuccess) return fail(cuda_fail(e_, "cudaMalloc", __FILE__, __LINE__)); \
         p->footprint += (int64_t)(cnt) * sizeof(*(ptr));                             \
     } while (0)
@@ -452,9 +474,9 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
     ALLOC(p->status, 1);
 #undef ALLOC
     cudaError_t e;
-    if ((e = cudaMalloc(&gh, sizeof(double) * (2 * 256))) != cudaSuccess ||
-        (e = cudaMalloc(&Wq, sizeof(double) * (2 * 256))) != cudaSuccess ||
-        (e = cudaMalloc(&gbuf, sizeof(double) * 2 * (size_t)nx * nxi)) != cudaSuccess)
+    if ((e = dmalloc((void**)&gh, sizeof(double) * (2 * 256), s)) != cudaSuccess ||
+        (e = dmalloc((void**)&Wq, sizeof(double) * (2 * 256), s)) != cudaSuccess ||
+        (e = dmalloc((void**)&gbuf, sizeof(double) * 2 * (size_t)nx * nxi, s)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     cudaMemsetAsync(p->status, 0, sizeof(Status), s);
     k_gauss_hermite<<<1, 256, 0, s>>>(d->qx, gh, Wq);
@@ -473,7 +495,7 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
                                     p->macro, p->G, p->w, p->status);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "pencil kernels", __FILE__, __LINE__));
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "build sync", __FILE__, __LINE__));
-    cudaFree(gh); cudaFree(Wq); cudaFree(gbuf);
+    dfree(gh, s); dfree(Wq, s); dfree(gbuf, s);
     gh = Wq = gbuf = nullptr;
     *out = p;
     return KLST_OK;

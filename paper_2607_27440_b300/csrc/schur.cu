@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) k_schur_house(SchurArgs a) {
         H[idx] = a.S[(size_t)j * a.lds + i];
     }
     for (int i = tid; i < m; i += nt) a.tau[i] = 0.0;
+    if (tid == 0) *a.nconv = 0;  // k_schur_qr sets -1 on failure; k_schur_post reads it
     __syncthreads();
     for (int c = 0; c + 2 < m; ++c) {
         double tail = 0.0;

@@ -70,6 +70,16 @@ EXPORTS = {
     "klst_factor_set_refine": (c_int32, [c_void_p, c_int32, c_double]),
     "klst_eigs": (c_int32, [c_void_p, ctypes.POINTER(EigsOpts), c_void_p, c_void_p, c_void_p,
                             ctypes.POINTER(EigsInfo), c_void_p]),
+    "klst_batch_eigs": (c_int32, [c_int32, c_void_p, c_void_p, c_int32, ctypes.POINTER(EigsOpts), c_int32,
+                                  c_void_p, c_void_p, c_void_p, c_void_p]),
+    "klst_server_create": (c_int32, [c_int64, c_int32, ctypes.POINTER(c_void_p)]),
+    "klst_server_submit": (c_int32, [c_void_p, ctypes.POINTER(PencilDesc), c_double, c_double, c_int32,
+                                     ctypes.POINTER(EigsOpts), ctypes.POINTER(c_uint64)]),
+    "klst_server_poll": (c_int32, [c_void_p, c_uint64, c_int32, ctypes.POINTER(c_int32), c_void_p, c_void_p,
+                                   ctypes.POINTER(EigsInfo), ctypes.POINTER(c_double)]),
+    "klst_server_stats": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                    ctypes.POINTER(c_int64)]),
+    "klst_server_destroy": (None, [c_void_p]),
 }
 
 
@@ -262,3 +272,78 @@ class Factor:
         d["status"] = code
         d["ritz_est"] = est
         return omega, vec, res, d
+
+
+def _opts(nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, seed=0, conv=CONV_REL, keep=0):
+    return EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
+                    refine_tol=refine_tol, v0=None, seed=seed, conv=conv, est_out=None, keep=keep)
+
+
+def batch_eigs(specs, sigmas, nev, ncv, precision=FP64, nworkers=0, **kw):
+    """klst_batch_eigs over a list of pencil specs and shifts; returns (omega (P, nev), resid (P, nev), status (P,), infos)."""
+    lib = load()
+    _torch()
+    P = len(specs)
+    descs = (PencilDesc * P)(*[make_desc(s) for s in specs])
+    sig = np.ascontiguousarray(np.asarray(sigmas, dtype=np.complex128))
+    ev = np.zeros((P, 2 * nev))
+    res = np.zeros((P, nev))
+    st = np.zeros(P, dtype=np.int32)
+    infos = (EigsInfo * P)()
+    opts = _opts(nev, ncv, **kw)
+    lib.klst_batch_eigs(P, ctypes.cast(descs, c_void_p), sig.ctypes.data_as(c_void_p), precision, ctypes.byref(opts),
+                        nworkers, ev.ctypes.data_as(c_void_p), res.ctypes.data_as(c_void_p),
+                        st.ctypes.data_as(c_void_p), ctypes.cast(infos, c_void_p))
+    return ev[:, 0::2] + 1j * ev[:, 1::2], res, st, [i.as_dict() for i in infos]
+
+
+class Server:
+    """klst_server_*: footprint-admitted, concurrently running eigensolve requests."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        lib = load()
+        _torch()
+        h = c_void_p()
+        _check(lib.klst_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+        self.handle = h
+        self._nev = {}
+
+    def submit(self, spec, sigma, nev, ncv, precision=FP64, **kw):
+        d = make_desc(spec)
+        o = _opts(nev, ncv, **kw)
+        t = c_uint64()
+        sigma = complex(sigma)
+        _check(load().klst_server_submit(self.handle, ctypes.byref(d), sigma.real, sigma.imag, precision,
+                                         ctypes.byref(o), ctypes.byref(t)))
+        self._nev[t.value] = nev
+        return t.value
+
+    def poll(self, ticket, wait=False):
+        """Returns None while running, else (omega, resid, info, latency_ms, status)."""
+        nev = self._nev[ticket]
+        done = c_int32()
+        ev = np.zeros(2 * nev)
+        res = np.zeros(nev)
+        info = EigsInfo()
+        lat = c_double()
+        code = load().klst_server_poll(self.handle, ticket, 1 if wait else 0, ctypes.byref(done),
+                                       ev.ctypes.data_as(c_void_p), res.ctypes.data_as(c_void_p), ctypes.byref(info),
+                                       ctypes.byref(lat))
+        if not done.value:
+            if code != KLST_OK:
+                _check(code)
+            return None
+        del self._nev[ticket]
+        return ev[0::2] + 1j * ev[1::2], res, info.as_dict(), lat.value, code
+
+    def stats(self):
+        q, r, b = c_int32(), c_int32(), c_int64()
+        _check(load().klst_server_stats(self.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)))
+        return q.value, r.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().klst_server_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
