@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
+    ap.add_argument("--serve-rate", type=float, default=5.0, help="Poisson arrival rate of the serving run (1/s)")
+    ap.add_argument("--serve-window", type=float, default=15.0, help="arrival window of the serving run (s)")
     return ap.parse_args()
 
 
@@ -152,6 +155,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = klst.load().klst_launch_count()
     ev0.record(stream)
     good_total, infos = 0, []
     for _ in range(args.steps):
@@ -160,6 +164,7 @@ def run_ours(args):
         infos.append(info)
     ev1.record(stream)
     barrier()
+    launches = int(klst.load().klst_launch_count() - launches0)
     clocks = sampler.stop()
     dev_ms = ev0.elapsed_time(ev1)
     # end to end through the public API: start vector from pinned host memory, eigenpairs back to host
@@ -243,17 +248,66 @@ def run_ours(args):
                      "achieved": orth_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": orth_tflops / FP64_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "nominal B300 float64 rate (1.25 TFLOP/s, profiling recipe); not in MEASURED_PEAKS.json"},
-        "gpu_launches": None,
+        "gpu_launches": launches,
         "clocks": clocks,
         "e2e": None if args.no_e2e else {"value": e2e_good / (e2e_ms / 1e3), "unit": "eigenpairs/s",
                                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "compare": compare,
         "peaks_source": src,
     }
+    if not args.no_batch:
+        line["batched"] = batched_sweep(klst, compare=not args.no_compare)
+        line["serving"] = serving_run(klst, args.serve_rate, args.serve_window)
     line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def batched_sweep(klst, compare=True):
+    """256-pencil sweep (Mach U[1.2,4], beta U[0,2], Nx {32,48,64,96}, Nxi {48,96,192,256}), 20 eigenpairs each."""
+    from paper_2607_27440_b300 import workloads as wl
+    sweep = wl.sweep(256, 4)
+    specs, sig = [s for s, _ in sweep], [z for _, z in sweep]
+    out = {"workload": "256 independent Mott-Smith pencils, Mach U[1.2,4], beta U[0,2], Nx in {32,48,64,96}, "
+                       "Nxi in {8x6,12x8,16x12,16x16}, sigma = 0.1i(1+U[0,1]), 20 eigenvalues, ncv 40",
+           "workers": 16}
+    for name, prec in (("mixed", klst.MIXED), ("fp64", klst.FP64)) if compare else (("mixed", klst.MIXED),):
+        t0 = time.perf_counter()
+        om, res, st, infos = klst.batch_eigs(specs, sig, 20, 40, precision=prec, nworkers=16, tol=CONV_TOL,
+                                             conv=klst.CONV_RESID, seed=4)
+        dt = time.perf_counter() - t0
+        good = int(np.sum(res <= RESID_MAX))
+        out[name] = {"eigenpairs_per_s": good / dt, "s": dt, "good_eigenpairs": good,
+                     "failed_pencils": int(np.sum(st != 0))}
+    return out
+
+
+def serving_run(klst, rate, window):
+    """Poisson arrivals of mixed-size requests (n log-uniform in [1,536, 281,088]); latency submit -> done."""
+    from paper_2607_27440_b300 import workloads as wl
+    reqs = wl.serving_requests(rate, window, seed=5)
+    S = klst.Server(hbm_budget_bytes=200 << 30, max_slots=8)
+    t0 = time.perf_counter()
+    tickets = []
+    for ta, spec, z in reqs:
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0005)
+        tickets.append(S.submit(spec, z, 20, 40, precision=klst.MIXED, tol=CONV_TOL, conv=klst.CONV_RESID, seed=5))
+    lats, good, fails = [], 0, 0
+    for t in tickets:
+        om, res, info, lat, code = S.poll(t, wait=True)
+        lats.append(lat)
+        if code in (0, klst.KLST_ENOCONV):
+            good += int(np.sum(res <= RESID_MAX))
+        if code != 0:
+            fails += 1
+    dt = time.perf_counter() - t0
+    S.close()
+    return {"rate_per_s": rate, "window_s": window, "requests": len(reqs), "slots": 8,
+            "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+            "eigenpairs_per_s": good / dt, "failed_requests": fails,
+            "workload": "M in {1.2,3,4}, n log-uniform [1,536, 281,088], sigma U[0,0.2]+iU[0,0.3], 20 eigenpairs"}
 
 
 def cpu_baseline(args, steps=1):

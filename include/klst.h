@@ -106,6 +106,9 @@ typedef struct {
 typedef struct klst_pencil_s* klst_pencil;
 typedef struct klst_factor_s* klst_factor;
 
+/* Number of CUDA kernels this library has launched in the process so far (all threads). */
+unsigned long long klst_launch_count(void);
+
 /* Status text ("KLST_OK", ...) and the calling thread's last error message. */
 const char* klst_status_string(int status);
 const char* klst_last_error(void);

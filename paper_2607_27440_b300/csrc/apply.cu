@@ -156,13 +156,19 @@ __global__ void k_solve_pass2(int nx, int nxi, const C* __restrict__ KinvT, cons
 }
 
 // Refinement bookkeeping: done[rhs] = ||r|| <= tol ||b||; worst residual; sweep counter.
+// One warp per right-hand side sums the per-block norms (fixed order).
 __global__ void k_refine_check(int nblk, const double* __restrict__ normpart, double tol, int* done, double* worst,
                                int* sweeps, int last) {
-    const int rhs = blockIdx.x;
-    if (threadIdx.x != 0) return;
+    const int rhs = blockIdx.x, lane = threadIdx.x;
     if (done[rhs]) return;
     double rr = 0, bb = 0;
-    for (int i = 0; i < nblk; ++i) { rr += normpart[((size_t)rhs * nblk + i) * 2]; bb += normpart[((size_t)rhs * nblk + i) * 2 + 1]; }
+    for (int i = lane; i < nblk; i += 32) {
+        rr += normpart[((size_t)rhs * nblk + i) * 2];
+        bb += normpart[((size_t)rhs * nblk + i) * 2 + 1];
+    }
+    rr = warp_sum(rr);
+    bb = warp_sum(bb);
+    if (lane != 0) return;
     const double rel = bb > 0 ? sqrt(rr / bb) : 0.0;
     const bool ok = rel <= tol;
     if (ok || last) {
@@ -188,16 +194,16 @@ static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y,
     const size_t sm1 = std::max(sizeof(C) * KB * 2 * NXP, sizeof(double2) * 4 * KB * NXP);
     prof_begin(sizeof(C) == 16 ? "solve_pass1_f64" : "solve_pass1_f32", s);
     k_solve_pass1<C><<<dim3(ng, nrhs), blk, sm1, s>>>(nx, nxi, (const C*)f->KinvT, p->w, p->xi_x, b, p->n, mask, ng,
-                                                      kpg, f->tpart, done);
+                                                      kpg, f->tpart, done); klst::note_launch();
     prof_end(sizeof(C) == 16 ? "solve_pass1_f64" : "solve_pass1_f32", s);
     prof_begin("cap_solve", s);
     k_reduce_groups_ext(f->r, ng, f->tpart, f->t, done, nrhs, s);
-    k_cinv_gemv<<<dim3((f->r * 32 + 255) / 256, nrhs), 256, 0, s>>>(f->r, f->Cinv, f->t, f->sv, done);
+    k_cinv_gemv<<<dim3((f->r * 32 + 255) / 256, nrhs), 256, 0, s>>>(f->r, f->Cinv, f->t, f->sv, done); klst::note_launch();
     prof_end("cap_solve", s);
     prof_begin(sizeof(C) == 16 ? "solve_pass2_f64" : "solve_pass2_f32", s);
     const int nb2 = std::min((nxi + KB - 1) / KB, 4 * device_sm_count());
     k_solve_pass2<C><<<dim3(nb2, nrhs), blk, sizeof(C) * KB * 2 * NXP, s>>>(nx, nxi, (const C*)f->KinvT, p->G, p->xi_x,
-                                                                           b, p->n, mask, f->sv, y, accumulate, done);
+                                                                           b, p->n, mask, f->sv, y, accumulate, done); klst::note_launch();
     prof_end(sizeof(C) == 16 ? "solve_pass2_f64" : "solve_pass2_f32", s);
     KLST_CK_LAUNCH();
     return KLST_OK;
@@ -220,7 +226,7 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
         if (rc) return rc;
         rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done);
         if (rc) return rc;
-        k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last);
+        k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last); klst::note_launch();
         prof_end("refine_residual", s);
         KLST_CK_LAUNCH();
         if (last) break;

@@ -119,6 +119,15 @@ __host__ __device__ __forceinline__ bool is_bc(int j, int nx, double xix) {
 
 int device_sm_count();
 
+// Deterministic warp sum: every lane adds its values in a fixed order, then a fixed xor tree.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Kernel launches issued by this library (process-wide counter, read by klst_launch_count).
+void note_launch();
+
 // Stream-ordered device memory (cudaMallocAsync on the device's default pool, whose release
 // threshold is raised once so freed blocks stay cached): allocations on different streams do
 // not serialise the device the way cudaMalloc/cudaFree do.

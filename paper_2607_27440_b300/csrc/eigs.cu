@@ -37,18 +37,26 @@ __global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int ncols, co
     }
 }
 
-// h[col] (+)= sum_chunk part[chunk][col]  (fixed order); with a closed gate, h2 := 0
+// h[col] (+)= sum_chunk part[chunk][col]: one warp per column, fixed lane stride + shuffle tree;
+// with a closed gate, h2 := 0
 __global__ void k_dots_reduce(const double2* __restrict__ part, int nchunks, int ncols, int ldp, double2* h, int add,
                               const int* __restrict__ gate) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (col >= ncols) return;
     if (gate && *gate == 0) {
-        if (!add) h[col] = mk(0, 0);
+        if (!add && lane == 0) h[col] = mk(0, 0);
         return;
     }
-    double2 s = mk(0, 0);
-    for (int c = 0; c < nchunks; ++c) s = s + part[(size_t)c * ldp + col];
-    h[col] = add ? h[col] + s : s;
+    double sx = 0.0, sy = 0.0;
+    for (int c = lane; c < nchunks; c += 32) {
+        const double2 v = part[(size_t)c * ldp + col];
+        sx += v.x;
+        sy += v.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) h[col] = add ? h[col] + mk(sx, sy) : mk(sx, sy);
 }
 
 // DGKS test (Daniel, Gragg, Kaufman, Stewart): reorthogonalise only when the first projection
@@ -119,11 +127,13 @@ __global__ void k_colnorm_part(const double2* __restrict__ X, int64_t ldx, int64
 }
 
 __global__ void k_colnorm_fin(const double* __restrict__ npart, int nblk, int ncols, double* __restrict__ nrm) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (col >= ncols) return;
     double s = 0;
-    for (int b = 0; b < nblk; ++b) s += npart[(size_t)col * nblk + b];
-    nrm[col] = sqrt(s);
+    for (int b = lane; b < nblk; b += 32) s += npart[(size_t)col * nblk + b];
+    s = warp_sum(s);
+    if (lane == 0) nrm[col] = sqrt(s);
 }
 
 // Finish the Arnoldi column j: S[0..j, j] = h1 + h2, S[j+1, j] = beta = ||w||; stores beta.
@@ -308,13 +318,13 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     // start: v0 (given or seeded), V[:,0] = T v0 / ||T v0|| (range of T: no B-null components)
     double2* v0 = Valt;
     if (o->v0) KLST_CK(cudaMemcpyAsync(v0, o->v0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
-    else k_randn<<<nblk, 256, 0, s>>>(v0, n, o->seed);
+    else { k_randn<<<nblk, 256, 0, s>>>(v0, n, o->seed); klst::note_launch(); }
     int applies = 0;
     if ((rc = apply_T(f, v0, V, 1, s)) != KLST_OK) return fail(rc);
     ++applies;
-    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.npart);
-    k_colnorm_fin<<<1, 32, 0, s>>>(W.npart, nblk, 1, W.nrm);
-    k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm);
+    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.npart); klst::note_launch();
+    k_colnorm_fin<<<1, 256, 0, s>>>(W.npart, nblk, 1, W.nrm); klst::note_launch();
+    k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm); klst::note_launch();
     KLST_CK_LAUNCH();
     // phase timers: event pairs recorded per step and read after each restart synchronisation
     W.evs.assign(3 * (m + 1) + 4, nullptr);
@@ -337,19 +347,19 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             const int nc = j + 1;
             // classical Gram-Schmidt, then a second pass only when the DGKS test asks for it
             prof_begin("orth_pass1", s);
-            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr);
-            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr);
-            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, W.npart, nullptr);
-            k_reorth_decide<<<1, 256, 0, s>>>(W.npart, nblk, W.h + nc, W.gate, W.reorth);
+            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr); klst::note_launch();
+            k_dots_reduce<<<(nc + 1 + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr); klst::note_launch();
+            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, W.npart, nullptr); klst::note_launch();
+            k_reorth_decide<<<1, 256, 0, s>>>(W.npart, nblk, W.h + nc, W.gate, W.reorth); klst::note_launch();
             prof_end("orth_pass1", s);
             prof_begin("orth_pass2", s);
-            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 0, W.gate);
-            k_dots_reduce<<<1, 192, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0, W.gate);
-            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h + (m + 1), w, n, W.npart2, W.gate);
-            k_dots_reduce<<<1, 192, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1, W.gate);  // h1 += h2
-            k_finish_col<<<1, 256, 0, s>>>(W.npart, W.npart2, W.gate, nblk, W.h, j, W.S, lds, W.beta, f->status);
+            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 0, W.gate); klst::note_launch();
+            k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0, W.gate); klst::note_launch();
+            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h + (m + 1), w, n, W.npart2, W.gate); klst::note_launch();
+            k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1, W.gate); klst::note_launch();  // h1 += h2
+            k_finish_col<<<1, 256, 0, s>>>(W.npart, W.npart2, W.gate, nblk, W.h, j, W.S, lds, W.beta, f->status); klst::note_launch();
             prof_end("orth_pass2", s);
-            k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(w, n, n, W.beta);
+            k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(w, n, n, W.beta); klst::note_launch();
             cudaEventRecord(evs[3 * j + 2], s);
             KLST_CK_LAUNCH();
         }
@@ -390,7 +400,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             cudaEventRecord(evs[3 * (m + 1) + 2], s);
             dim3 grd(std::max(1, nblk / std::max(1, (keep + 7) / 8)), (keep + 7) / 8);
             prof_begin("rotate", s);
-            k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n);
+            k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n); klst::note_launch();
             prof_end("rotate", s);
             KLST_CK_LAUNCH();
             KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
@@ -427,14 +437,14 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     {
         dim3 grd(std::max(1, nblk / std::max(1, (nret + 7) / 8)), (nret + 7) / 8);
-        k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n);
+        k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n); klst::note_launch();
         KLST_CK_LAUNCH();
     }
     if ((rc = apply_T(f, X, Z, nret, s)) != KLST_OK) return fail(rc);
     applies += nret;
-    k_colnorm_part<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.npart);
-    k_colnorm_fin<<<(nret + 63) / 64, 64, 0, s>>>(W.npart, nblk, nret, W.nrm);
-    k_scale_cols<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.nrm);
+    k_colnorm_part<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.npart); klst::note_launch();
+    k_colnorm_fin<<<(nret + 7) / 8, 256, 0, s>>>(W.npart, nblk, nret, W.nrm); klst::note_launch();
+    k_scale_cols<<<dim3(nblk, nret), 256, 0, s>>>(Z, n, n, W.nrm); klst::note_launch();
     KLST_CK_LAUNCH();
     std::vector<double2> mu(m);
     KLST_CK(cudaMemcpyAsync(mu.data(), W.musel, sizeof(double2) * nev, cudaMemcpyDeviceToHost, s));
@@ -446,8 +456,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     KLST_CK(cudaMemcpyAsync(W.om, om.data(), sizeof(double2) * nret, cudaMemcpyHostToDevice, s));
     if ((rc = apply_pencil_dev(p, Z, Rr, nret, W.om, s, W.mw, W.mp, ng)) != KLST_OK) return fail(rc);
-    k_colnorm_part<<<dim3(nblk, nret), 256, 0, s>>>(Rr, n, n, W.npart);
-    k_colnorm_fin<<<(nret + 63) / 64, 64, 0, s>>>(W.npart, nblk, nret, W.nrm);
+    k_colnorm_part<<<dim3(nblk, nret), 256, 0, s>>>(Rr, n, n, W.npart); klst::note_launch();
+    k_colnorm_fin<<<(nret + 7) / 8, 256, 0, s>>>(W.npart, nblk, nret, W.nrm); klst::note_launch();
     KLST_CK_LAUNCH();
     std::vector<double> res(nret);
     double worst = 0;

@@ -239,7 +239,7 @@ static int launch_block_gj(klst_factor f, C* out, cudaStream_t s) {
     const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
     if (use_smem) KLST_CK(cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     k_block_gj<C><<<p->nxi, 256, use_smem ? bytes : 0, s>>>(p->nx, p->nxi, p->desc.beta, f->sigma, p->Dx, p->xi_x,
-                                                           p->xi_y, p->nu, out, use_smem, f->status);
+                                                           p->xi_y, p->nu, out, use_smem, f->status); klst::note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
@@ -249,7 +249,7 @@ static int launch_cap(klst_factor f, const C* Kinv, double2* Cp, int nsplit, cud
     klst_pencil p = f->p;
     const int kper = (p->nxi + nsplit - 1) / nsplit;
     dim3 blk(16, 16), grd((p->nx + 15) / 16, (p->nx + 15) / 16, nsplit);
-    k_cap_partial<C><<<grd, blk, 0, s>>>(p->nx, p->nxi, Kinv, p->G, p->w, kper, Cp);
+    k_cap_partial<C><<<grd, blk, 0, s>>>(p->nx, p->nxi, Kinv, p->G, p->w, kper, Cp); klst::note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
@@ -365,20 +365,22 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if (rc) { free64(); return fail(rc); }
     if (precision == KLST_MIXED) {
         const size_t cnt = (size_t)p->nxi * p->nx * p->nx;
-        k_round_c64<<<(int)std::min<size_t>((cnt + 255) / 256, 8192), 256, 0, s>>>(K64, (float2*)f->KinvT, cnt);
+        k_round_c64<<<(int)std::min<size_t>((cnt + 255) / 256, 8192), 256, 0, s>>>(K64, (float2*)f->KinvT, cnt); klst::note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) { free64(); return fail(cuda_fail(e, "round", __FILE__, __LINE__)); }
         free64();
     }
-    k_cap_reduce<<<std::min(1024, (r * r + 255) / 256), 256, 0, s>>>(r, nsplit, Cp, b0);
+    k_cap_reduce<<<std::min(1024, (r * r + 255) / 256), 256, 0, s>>>(r, nsplit, Cp, b0); klst::note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "cap reduce", __FILE__, __LINE__));
     {
         const int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
         const size_t smem = sizeof(double2) * 2 * r;
         int* perm = (int*)bar;
-        for (int p = 0; p < r; ++p)
+        for (int p = 0; p < r; ++p) {
             k_gj_step<<<nb, 256, smem, s>>>(r, p, (p & 1) ? b1 : b0, (p & 1) ? b0 : b1, perm, f->status);
+            klst::note_launch();
+        }
         k_gj_unpermute<<<std::min(1024, (r * r + 255) / 256), 256, sizeof(int) * r, s>>>(r, (r & 1) ? b1 : b0,
-                                                                                        (r & 1) ? b0 : b1, perm);
+                                                                                        (r & 1) ? b0 : b1, perm); klst::note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "capacitance inverse", __FILE__, __LINE__));
     }
     double2* res = (r & 1) ? b0 : b1;

@@ -39,16 +39,24 @@ __global__ void k_moments_partial(int nx, int nxi, const double* __restrict__ w,
     }
 }
 
-// out[rhs*len + i] = sum_g part[(rhs*ngroups + g)*len + i]   (fixed order: deterministic)
+// out[rhs*len + i] = sum_g part[(rhs*ngroups + g)*len + i]: one warp per output, lanes over groups in
+// a fixed stride, then a fixed shuffle tree (deterministic, latency-parallel).
 __global__ void k_reduce_groups(int len, int ngroups, const double2* __restrict__ part, double2* __restrict__ out,
                                 const int* done) {
     const int rhs = blockIdx.y;
     if (done && done[rhs]) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-        double2 s = mk(0, 0);
-        for (int g = 0; g < ngroups; ++g) s = s + part[((size_t)rhs * ngroups + g) * len + i];
-        out[(size_t)rhs * len + i] = s;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= len) return;
+    double sx = 0.0, sy = 0.0;
+    for (int g = lane; g < ngroups; g += 32) {
+        const double2 v = part[((size_t)rhs * ngroups + g) * len + i];
+        sx += v.x;
+        sy += v.y;
     }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) out[(size_t)rhs * len + i] = mk(sx, sy);
 }
 
 // Rows of (A - omega B) x (mode 0) or the residual b - (A - sigma B) x (mode 1, b masked by B
@@ -134,7 +142,7 @@ __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __rest
 
 void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,
                          cudaStream_t s) {
-    k_reduce_groups<<<dim3((len + 255) / 256, nrhs), 256, 0, s>>>(len, ngroups, part, out, done);
+    k_reduce_groups<<<dim3((len + 7) / 8, nrhs), 256, 0, s>>>(len, ngroups, part, out, done); klst::note_launch();
 }
 
 int pencil_work_groups(klst_pencil p) {
@@ -160,8 +168,8 @@ int moments_dev(klst_pencil p, const double2* x, int64_t ldx, int nrhs, double2*
     const int NXP = nxp_of(p->nx), KB = 256 / NXP;
     const int kpg = (p->nxi + ngroups - 1) / ngroups;
     dim3 blk(NXP, KB), grd(ngroups, nrhs);
-    k_moments_partial<<<grd, blk, sizeof(double2) * 4 * KB * NXP, s>>>(p->nx, p->nxi, p->w, x, ldx, ngroups, kpg, mpart);
-    k_reduce_groups<<<dim3((4 * p->nx + 255) / 256, nrhs), 256, 0, s>>>(4 * p->nx, ngroups, mpart, mwork, done);
+    k_moments_partial<<<grd, blk, sizeof(double2) * 4 * KB * NXP, s>>>(p->nx, p->nxi, p->w, x, ldx, ngroups, kpg, mpart); klst::note_launch();
+    k_reduce_groups<<<dim3((4 * p->nx + 7) / 8, nrhs), 256, 0, s>>>(4 * p->nx, ngroups, mpart, mwork, done); klst::note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
@@ -178,7 +186,7 @@ int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t l
     }
     dim3 blk(NXP, KB), grd(pencil_rows_blocks(p), nrhs);
     k_pencil_rows<<<grd, blk, smem, s>>>(p->nx, p->nxi, p->desc.beta, p->DxT, p->xi_x, p->xi_y, p->nu, p->G, m, x,
-                                        ldx, omega, mode, b, mask_b, y, normpart, done);
+                                        ldx, omega, mode, b, mask_b, y, normpart, done); klst::note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
 }

@@ -479,10 +479,10 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
         (e = dmalloc((void**)&gbuf, sizeof(double) * 2 * (size_t)nx * nxi, s)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     cudaMemsetAsync(p->status, 0, sizeof(Status), s);
-    k_gauss_hermite<<<1, 256, 0, s>>>(d->qx, gh, Wq);
-    k_gauss_hermite<<<1, 256, 0, s>>>(d->qy, gh + 256, Wq + 256);
-    k_velocity_grid<<<(nxi + 255) / 256, 256, 0, s>>>(d->qx, d->qy, gh, Wq, gh + 256, Wq + 256, p->xi_x, p->xi_y, p->W);
-    k_cheb_map<<<(nx * nx + 255) / 256, 256, 0, s>>>(nx, d->map_L, d->map_sinf, p->x, p->Dx, p->DxT);
+    k_gauss_hermite<<<1, 256, 0, s>>>(d->qx, gh, Wq); klst::note_launch();
+    k_gauss_hermite<<<1, 256, 0, s>>>(d->qy, gh + 256, Wq + 256); klst::note_launch();
+    k_velocity_grid<<<(nxi + 255) / 256, 256, 0, s>>>(d->qx, d->qy, gh, Wq, gh + 256, Wq + 256, p->xi_x, p->xi_y, p->W); klst::note_launch();
+    k_cheb_map<<<(nx * nx + 255) / 256, 256, 0, s>>>(nx, d->map_L, d->map_sinf, p->x, p->Dx, p->DxT); klst::note_launch();
     BaseParams bp;
     bp.nx = nx; bp.nxi = nxi; bp.base = d->base; bp.noneq = d->noneq; bp.conservative = d->conservative;
     bp.mach = d->mach; bp.gamma = d->gamma; bp.visc_s = d->visc_s; bp.re_delta = d->re_delta; bp.width = d->width;
@@ -492,7 +492,7 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
     const double p1 = 0.5, p2 = p1 * (1.0 + 2.0 * g * (M * M - 1.0) / (g + 1.0));
     bp.rho2 = r; bp.u2 = bp.u1 / r; bp.T2 = 2.0 * p2 / bp.rho2;
     k_base_state<<<nx, 256, 0, s>>>(bp, p->x, p->xi_x, p->xi_y, p->W, gbuf, gbuf + (size_t)nx * nxi, p->nu,
-                                    p->macro, p->G, p->w, p->status);
+                                    p->macro, p->G, p->w, p->status); klst::note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "pencil kernels", __FILE__, __LINE__));
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "build sync", __FILE__, __LINE__));
     dfree(gh, s); dfree(Wq, s); dfree(gbuf, s);
@@ -542,7 +542,7 @@ extern "C" int klst_export_dense(klst_pencil p, double sr, double si, double* A_
         for (int64_t r0 = 0; r0 < n; r0 += chunk) {
             int64_t nr = std::min(chunk, n - r0);
             k_export_rows<<<(int)std::min<int64_t>(nr, 4096), 256>>>(nx, nxi, r0, nr, p->desc.beta, mk(sr, si), p->Dx,
-                                                                     p->xi_x, p->xi_y, p->nu, p->G, p->w, buf);
+                                                                     p->xi_x, p->xi_y, p->nu, p->G, p->w, buf); klst::note_launch();
             cudaError_t e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpy(A_host + 2 * r0 * n, buf, (size_t)nr * n * sizeof(double2), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) { cudaFree(buf); return cuda_fail(e, "export", __FILE__, __LINE__); }

@@ -1,5 +1,6 @@
 // Opt-in per-kernel-group timing (KLST_TIMING=1).  Events are recorded on the launching stream
 // and resolved when klst_eigs reports; the library's normal path never touches this code.
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -10,6 +11,9 @@
 #include "common.cuh"
 
 namespace klst {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct ProfRec {
     std::string name;
@@ -81,3 +85,5 @@ void prof_report(cudaStream_t s) {
 }
 
 }  // namespace klst
+
+extern "C" unsigned long long klst_launch_count(void) { return klst::g_launches.load(std::memory_order_relaxed); }

@@ -421,16 +421,16 @@ int launch_schur(const SchurArgs& a, cudaStream_t s) {
     const int m = a.m;
     const size_t packed = sizeof(double2) * (size_t)m * (m + 3) / 2;
     prof_begin("schur_house", s);
-    k_schur_house<<<1, 256, 0, s>>>(a);
+    k_schur_house<<<1, 256, 0, s>>>(a); klst::note_launch();
     prof_end("schur_house", s);
     prof_begin("schur_qr", s);
-    k_schur_qr<<<1, 256, packed, s>>>(a);
+    k_schur_qr<<<1, 256, packed, s>>>(a); klst::note_launch();
     prof_end("schur_qr", s);
     prof_begin("schur_q", s);
-    k_schur_q<<<(m + 31) / 32, 32, sizeof(double2) * 32 * m, s>>>(a);
+    k_schur_q<<<(m + 31) / 32, 32, sizeof(double2) * 32 * m, s>>>(a); klst::note_launch();
     prof_end("schur_q", s);
     prof_begin("schur_post", s);
-    k_schur_post<<<1, 256, 0, s>>>(a);
+    k_schur_post<<<1, 256, 0, s>>>(a); klst::note_launch();
     prof_end("schur_post", s);
     KLST_CK_LAUNCH();
     return KLST_OK;

@@ -54,6 +54,7 @@ _lib = None
 EXPORTS = {
     "klst_status_string": (ctypes.c_char_p, [c_int32]),
     "klst_last_error": (ctypes.c_char_p, []),
+    "klst_launch_count": (ctypes.c_ulonglong, []),
     "klst_build_pencil": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, ctypes.POINTER(c_void_p)]),
     "klst_pencil_destroy": (None, [c_void_p]),
     "klst_pencil_dims": (c_int32, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int32),
