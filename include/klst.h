@@ -83,7 +83,13 @@ typedef struct {
                              bounds the purified residual ||A q - omega B q|| (||q|| = 1) by ~tol */
     double* est_out;      /* host float64[nev] or NULL: final Ritz residual estimates ||T x - mu x|| */
     int32_t keep;         /* Ritz vectors kept at each restart, nev <= keep < ncv; 0 = nev + (ncv - nev) / 2 */
+    int32_t arith;        /* KLST_ARITH_F64: Krylov basis, Gram-Schmidt and rotations in native float64;
+                             KLST_ARITH_DF64: basis stored and combined in double-float (two float32 per
+                             real, error-free products and compensated sums, ~2^-48 unit roundoff) on the
+                             float32 pipes, which the B300 runs ~60x faster than float64 */
 } klst_eigs_opts;
+
+typedef enum { KLST_ARITH_F64 = 0, KLST_ARITH_DF64 = 1 } klst_arith;
 
 typedef enum { KLST_CONV_REL = 0, KLST_CONV_RESID = 1 } klst_conv;
 

@@ -14,7 +14,7 @@ int moments_dev(klst_pencil p, const double2* x, int64_t ldx, int nrhs, double2*
                 int ngroups, cudaStream_t s, const int* done);
 int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t ldx, int nrhs, const double2* omega,
                     int mode, const double2* b, int mask_b, double2* y, double* normpart, cudaStream_t s,
-                    const int* done);
+                    const int* done, int df_arith);
 int pencil_rows_blocks(klst_pencil p);
 
 // Pass 1: for each k in the block's group, z_{c,k} = K_k^{-1} b_{c,k} and accumulate
@@ -224,7 +224,8 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
         prof_begin("refine_residual", s);
         rc = moments_dev(p, y, p->n, nrhs, f->t, f->tpart, f->ngroups, s, f->done);
         if (rc) return rc;
-        rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done);
+        rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done,
+                             f->arith);
         if (rc) return rc;
         k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last); klst::note_launch();
         prof_end("refine_residual", s);

@@ -6,8 +6,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
+#include "df64.cuh"
 #include "factor.cuh"
 
 namespace klst {
@@ -197,6 +199,111 @@ __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ V, i
     }
 }
 
+// ---------------------------------------------------------------- double-float (df64) basis
+// The Krylov basis is stored as complex df64 (float4) and the Gram-Schmidt projections, updates
+// and basis rotations run in df64 arithmetic on the float32 pipes (see df64.cuh).
+
+// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]; with_self adds column ncols = |w|^2.
+__global__ void k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ w,
+                          int64_t n, int chunk, double2* __restrict__ part, int ldp, int with_self,
+                          const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
+    extern __shared__ float4 swf[];
+    const int64_t r0 = (int64_t)blockIdx.x * chunk;
+    const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) cdf_store(&swf[i], cdf_from(w[r0 + i]));
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int col = wid; col < ncols; col += nw) {
+        const float4* vc = V + col * ldv + r0;
+        cdf a = cdf_zero();
+        for (int i = lane; i < len; i += 32) cdf_fma_conj(a, cdf_load(vc + i), cdf_load(swf + i));
+        a = cdf_warp_sum(a);
+        if (lane == 0) part[(size_t)blockIdx.x * ldp + col] = cdf_to(a);
+    }
+    if (with_self && wid == 0) {  // |w|^2 of the chunk in float64
+        double s2 = 0.0;
+        for (int i = lane; i < len; i += 32) s2 += abs2(w[r0 + i]);
+        s2 = warp_sum(s2);
+        if (lane == 0) part[(size_t)blockIdx.x * ldp + ncols] = mk(s2, 0.0);
+    }
+}
+
+// w -= V h (ncols columns, df64 accumulation); per-block partials of |w|^2
+__global__ void k_update_df(const float4* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ h,
+                            double2* __restrict__ w, int64_t n, double* __restrict__ npart, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
+    extern __shared__ float4 shf[];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
+        const double2 hv = h[i];
+        cdf_store(&shf[i], cdf_from(mk(-hv.x, -hv.y)));
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        cdf acc = cdf_from(w[i]);
+        for (int c = 0; c < ncols; ++c) cdf_fma(acc, cdf_load(V + c * ldv + i), cdf_load(shf + c));
+        const double2 out = cdf_to(acc);
+        w[i] = out;
+        nrm += abs2(out);
+    }
+    if (npart) {
+        nrm = warp_sum(nrm);
+        __shared__ double red[32];
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+            npart[blockIdx.x] = s;
+        }
+    }
+}
+
+// basis column = w / scale (df64) and the float64 copy that feeds the next apply
+__global__ void k_scale_df(const double2* __restrict__ w, int64_t n, const double* __restrict__ scale,
+                           float4* __restrict__ vcol, double2* __restrict__ vcopy) {
+    const double sc = *scale;
+    const double inv = sc > 0 ? 1.0 / sc : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = mk(w[i].x * inv, w[i].y * inv);
+        cdf_store(vcol + i, cdf_from(v));
+        vcopy[i] = v;
+    }
+}
+
+// Vout[:, c] = sum_l V[:, l] Q[l, c] for c < ncol, V in df64; output df64 (float4) or float64 (double2)
+template <typename O>
+__global__ void __launch_bounds__(256) k_rotate_df(const float4* __restrict__ V, int64_t ldv, int m,
+                                                   const double2* __restrict__ Q, int ldq, int ncol,
+                                                   O* __restrict__ Vout, int64_t ldo, int64_t n) {
+    extern __shared__ float4 sqf[];  // [m][8]
+    const int c0 = blockIdx.y * 8;
+    for (int idx = threadIdx.x; idx < m * 8; idx += blockDim.x) {
+        const int l = idx / 8, c = idx % 8;
+        cdf_store(&sqf[idx], cdf_from((c0 + c < ncol) ? Q[(size_t)(c0 + c) * ldq + l] : mk(0, 0)));
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        cdf acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = cdf_zero();
+        for (int l = 0; l < m; ++l) {
+            const cdf v = cdf_load(V + l * ldv + i);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cdf_fma(acc[c], v, cdf_load(sqf + l * 8 + c));
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c0 + c >= ncol) continue;
+            if constexpr (sizeof(O) == sizeof(float4) && alignof(O) == 16 && std::is_same<O, float4>::value)
+                cdf_store(Vout + (c0 + c) * ldo + i, acc[c]);
+            else
+                Vout[(c0 + c) * ldo + i] = cdf_to(acc[c]);
+        }
+    }
+}
+
 // Seeded complex Gaussian start vector (splitmix64 counter hash + Box-Muller).
 __device__ __forceinline__ uint64_t splitmix(uint64_t z) {
     z += 0x9e3779b97f4a7c15ull;
@@ -222,12 +329,13 @@ struct EigsWork {
     double* npart2 = nullptr;
     int *gate = nullptr, *reorth = nullptr;
     double2 *h = nullptr, *dpart = nullptr, *X = nullptr, *Z = nullptr, *R = nullptr, *om = nullptr;
+    double2 *wbuf = nullptr, *vcur = nullptr;
     double2 *mw = nullptr, *mp = nullptr;
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
     std::vector<cudaEvent_t> evs;
     void release(cudaStream_t st) {
-        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
+        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, wbuf, vcur, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
         for (void* p : b) dfree(p, st);
         for (auto& ev : evs) cudaEventDestroy(ev);
         evs.clear();
@@ -263,9 +371,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         return KLST_EINVAL;
     }
     const int keep = o->keep ? o->keep : std::min(m - 1, nev + (m - nev) / 2);
-    const int prev_refine = f->max_refine;
+    const int prev_refine = f->max_refine, prev_arith = f->arith;
     const double prev_rtol = f->refine_tol;
     f->max_refine = o->max_refine;
+    f->arith = o->arith == KLST_ARITH_DF64 ? 1 : 0;
     if (o->refine_tol > 0) f->refine_tol = o->refine_tol;
     EigsWork W;
     cudaError_t e;
@@ -274,6 +383,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         W.release(s);
         f->max_refine = prev_refine;
         f->refine_tol = prev_rtol;
+        f->arith = prev_arith;
         return code;
     };
 #define EALLOC(ptr, cnt)                                                                     \
@@ -315,16 +425,30 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     KLST_CK(cudaMemsetAsync(f->sweeps, 0, sizeof(int), s));
     if ((rc = factor_reserve(f, std::max(nev, 1), s)) != KLST_OK) return fail(rc);
     double2 *V = W.Va, *Valt = W.Vb;
+    // df64 mode: the basis is complex df64 (float4, same bytes); the apply works on float64
+    // vectors wbuf (output) and vcur (the newest basis vector in float64)
+    const bool dfm = o->arith == KLST_ARITH_DF64;
+    double2 *wbuf = nullptr, *vcur = nullptr;
+    if (dfm) {
+        if ((e = dmalloc((void**)&W.wbuf, sizeof(double2) * n, s)) != cudaSuccess ||
+            (e = dmalloc((void**)&W.vcur, sizeof(double2) * n, s)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+        wbuf = W.wbuf;
+        vcur = W.vcur;
+    }
+    auto V4 = [&](double2* p0) { return reinterpret_cast<float4*>(p0); };
     // start: v0 (given or seeded), V[:,0] = T v0 / ||T v0|| (range of T: no B-null components)
     double2* v0 = Valt;
     if (o->v0) KLST_CK(cudaMemcpyAsync(v0, o->v0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
     else { k_randn<<<nblk, 256, 0, s>>>(v0, n, o->seed); klst::note_launch(); }
     int applies = 0;
-    if ((rc = apply_T(f, v0, V, 1, s)) != KLST_OK) return fail(rc);
+    double2* w0 = dfm ? wbuf : V;
+    if ((rc = apply_T(f, v0, w0, 1, s)) != KLST_OK) return fail(rc);
     ++applies;
-    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.npart); klst::note_launch();
+    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(w0, n, n, W.npart); klst::note_launch();
     k_colnorm_fin<<<1, 256, 0, s>>>(W.npart, nblk, 1, W.nrm); klst::note_launch();
-    k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm); klst::note_launch();
+    if (dfm) { k_scale_df<<<nblk, 256, 0, s>>>(wbuf, n, W.nrm, V4(V), vcur); klst::note_launch(); }
+    else { k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm); klst::note_launch(); }
     KLST_CK_LAUNCH();
     // phase timers: event pairs recorded per step and read after each restart synchronisation
     W.evs.assign(3 * (m + 1) + 4, nullptr);
@@ -338,8 +462,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     bool converged = false;
     for (;;) {
         for (int j = k; j < m; ++j) {
-            double2* vj = V + (int64_t)j * n;
-            double2* w = V + (int64_t)(j + 1) * n;
+            double2* vj = dfm ? vcur : V + (int64_t)j * n;
+            double2* w = dfm ? wbuf : V + (int64_t)(j + 1) * n;
             cudaEventRecord(evs[3 * j], s);
             if ((rc = apply_T(f, vj, w, 1, s)) != KLST_OK) return fail(rc);
             cudaEventRecord(evs[3 * j + 1], s);
@@ -347,6 +471,22 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             const int nc = j + 1;
             // classical Gram-Schmidt, then a second pass only when the DGKS test asks for it
             prof_begin("orth_pass1", s);
+            if (dfm) {
+                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr); klst::note_launch();
+                k_dots_reduce<<<(nc + 1 + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr); klst::note_launch();
+                k_update_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h, w, n, W.npart, nullptr); klst::note_launch();
+                k_reorth_decide<<<1, 256, 0, s>>>(W.npart, nblk, W.h + nc, W.gate, W.reorth); klst::note_launch();
+                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.dpart, m + 1, 0, W.gate); klst::note_launch();
+                k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0, W.gate); klst::note_launch();
+                k_update_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h + (m + 1), w, n, W.npart2, W.gate); klst::note_launch();
+                k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1, W.gate); klst::note_launch();
+                k_finish_col<<<1, 256, 0, s>>>(W.npart, W.npart2, W.gate, nblk, W.h, j, W.S, lds, W.beta, f->status); klst::note_launch();
+                k_scale_df<<<nblk, 256, 0, s>>>(w, n, W.beta, V4(V) + (int64_t)(j + 1) * n, vcur); klst::note_launch();
+                prof_end("orth_pass1", s);
+                cudaEventRecord(evs[3 * j + 2], s);
+                KLST_CK_LAUNCH();
+                continue;
+            }
             k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr); klst::note_launch();
             k_dots_reduce<<<(nc + 1 + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr); klst::note_launch();
             k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, W.npart, nullptr); klst::note_launch();
@@ -400,7 +540,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             cudaEventRecord(evs[3 * (m + 1) + 2], s);
             dim3 grd(std::max(1, nblk / std::max(1, (keep + 7) / 8)), (keep + 7) / 8);
             prof_begin("rotate", s);
-            k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n); klst::note_launch();
+            if (dfm) k_rotate_df<float4><<<grd, 256, sizeof(double2) * m * 8, s>>>(V4(V), n, m, W.Q, m, keep, V4(Valt), n, n);
+            else k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n);
+            klst::note_launch();
             prof_end("rotate", s);
             KLST_CK_LAUNCH();
             KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
@@ -437,7 +579,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     {
         dim3 grd(std::max(1, nblk / std::max(1, (nret + 7) / 8)), (nret + 7) / 8);
-        k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n); klst::note_launch();
+        if (dfm) k_rotate_df<double2><<<grd, 256, sizeof(double2) * m * 8, s>>>(V4(V), n, m, W.Ysel, m, nret, X, n, n);
+        else k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n);
+        klst::note_launch();
         KLST_CK_LAUNCH();
     }
     if ((rc = apply_T(f, X, Z, nret, s)) != KLST_OK) return fail(rc);
@@ -497,6 +641,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     W.release(s);
     f->max_refine = prev_refine;
     f->refine_tol = prev_rtol;
+    f->arith = prev_arith;
     if (!converged) { set_error("only %d of %d eigenpairs converged after %d restarts", nconv, nev, restarts); return KLST_ENOCONV; }
     return KLST_OK;
 }

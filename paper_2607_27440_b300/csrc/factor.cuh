@@ -25,6 +25,7 @@ struct klst_factor_s {
     int* sweeps;       // [1] refinement sweeps executed since the last reset
     int max_refine;
     double refine_tol;
+    int arith;         // refinement residual: 0 float64, 1 double-float (set per eigs call)
     double t_factor_ms;
     int64_t footprint;
     klst::Status* status;

@@ -18,7 +18,7 @@ int moments_dev(klst_pencil p, const double2* x, int64_t ldx, int nrhs, double2*
                 int ngroups, cudaStream_t s, const int* done);
 int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t ldx, int nrhs, const double2* omega,
                     int mode, const double2* b, int mask_b, double2* y, double* normpart, cudaStream_t s,
-                    const int* done);
+                    const int* done, int df_arith);
 
 // 4 MiB of scratch per device: shifts [nrhs], moments [nrhs][4 nx] and per-group moment
 // partial sums [nrhs][groups][4 nx], all complex128.
@@ -85,5 +85,5 @@ extern "C" int klst_apply_pencil_noalloc(klst_pencil p, const void* x, void* y, 
     rc = moments_dev(p, (const double2*)x, p->n, nrhs, mwork, mpart, ng, s, nullptr);
     if (rc) return rc;
     return pencil_rows_dev(p, mwork, (const double2*)x, p->n, nrhs, omega ? om : nullptr, 0, nullptr, 0, (double2*)y,
-                           nullptr, s, nullptr);
+                           nullptr, s, nullptr, 0);
 }

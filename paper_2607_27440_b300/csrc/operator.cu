@@ -1,5 +1,6 @@
 // Matrix-free float64 pencil operator y = (A - omega B) x and the refinement residual
 // r = b - (A - sigma B) y, from the rows of Eqs. comp_ghat1Dshock / comp_hhat1Dshock.
+#include "df64.cuh"
 #include "factor.cuh"
 
 namespace klst {
@@ -62,6 +63,9 @@ __global__ void k_reduce_groups(int len, int ngroups, const double2* __restrict_
 // Rows of (A - omega B) x (mode 0) or the residual b - (A - sigma B) x (mode 1, b masked by B
 // when mask_b).  Boundary rows: (A - omega B) x = x.  normpart receives per-block sums of |y|^2
 // and |b|^2 (mode 1).
+// DF = true forms the D_x product in double-float (df64) arithmetic on the float32 pipes; the
+// diagonal, coupling and residual terms stay float64.
+template <bool DF>
 __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __restrict__ DxT,
                               const double* __restrict__ xi_x, const double* __restrict__ xi_y,
                               const double* __restrict__ nu, const double* __restrict__ G,
@@ -77,7 +81,12 @@ __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __rest
     double2* sx = (double2*)(smem + nx * nx + (nx * nx & 1));  // [KB][2][NXP]
     double* sred = (double*)(sx + KB * 2 * NXP);         // [KB*NXP][2]
     const int tid = kk * NXP + j, nthr = NXP * KB;
-    for (int i = tid; i < nx * nx; i += nthr) sD[i] = DxT[i];
+    df* sDf = reinterpret_cast<df*>(sD);
+    float4* sxf = reinterpret_cast<float4*>(sx);
+    for (int i = tid; i < nx * nx; i += nthr) {
+        if constexpr (DF) sDf[i] = df_from(DxT[i]);
+        else sD[i] = DxT[i];
+    }
     const double2* xr = x + rhs * ldx;
     const double2* br = b ? b + rhs * ldx : nullptr;
     double2* yr = y + rhs * ldx;
@@ -89,8 +98,13 @@ __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __rest
         const bool valid = (k < nxi) && (j < nx);
         __syncthreads();
         if (valid) {
-            sx[(kk * 2 + 0) * NXP + j] = xr[(size_t)k * nx + j];
-            sx[(kk * 2 + 1) * NXP + j] = xr[((size_t)nxi + k) * nx + j];
+            if constexpr (DF) {
+                cdf_store(&sxf[(kk * 2 + 0) * NXP + j], cdf_from(xr[(size_t)k * nx + j]));
+                cdf_store(&sxf[(kk * 2 + 1) * NXP + j], cdf_from(xr[((size_t)nxi + k) * nx + j]));
+            } else {
+                sx[(kk * 2 + 0) * NXP + j] = xr[(size_t)k * nx + j];
+                sx[(kk * 2 + 1) * NXP + j] = xr[((size_t)nxi + k) * nx + j];
+            }
         }
         __syncthreads();
         if (!valid) continue;
@@ -99,12 +113,24 @@ __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __rest
         for (int c = 0; c < 2; ++c) {
             const double2* xs = sx + (kk * 2 + c) * NXP;
             double2 d = mk(0, 0);
-            for (int mm = 0; mm < nx; ++mm) {
-                double dv = sD[mm * nx + j];
-                d.x = fma(dv, xs[mm].x, d.x);
-                d.y = fma(dv, xs[mm].y, d.y);
+            if constexpr (DF) {
+                const float4* xsf = sxf + (kk * 2 + c) * NXP;
+                cdf dd = cdf_zero();
+                for (int mm = 0; mm < nx; ++mm) {
+                    const df dv = sDf[mm * nx + j];
+                    const cdf xv = cdf_load(xsf + mm);
+                    df_fma(dd.re, dv, xv.re);
+                    df_fma(dd.im, dv, xv.im);
+                }
+                d = cdf_to(dd);
+            } else {
+                for (int mm = 0; mm < nx; ++mm) {
+                    double dv = sD[mm * nx + j];
+                    d.x = fma(dv, xs[mm].x, d.x);
+                    d.y = fma(dv, xs[mm].y, d.y);
+                }
             }
-            const double2 xv = xs[j];
+            const double2 xv = xr[((size_t)c * nxi + k) * nx + j];
             double2 val;
             if (bc) {
                 val = xv;
@@ -176,17 +202,22 @@ int moments_dev(klst_pencil p, const double2* x, int64_t ldx, int nrhs, double2*
 
 int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t ldx, int nrhs, const double2* omega,
                     int mode, const double2* b, int mask_b, double2* y, double* normpart, cudaStream_t s,
-                    const int* done) {
+                    const int* done, int df_arith) {
     const int NXP = nxp_of(p->nx), KB = 256 / NXP;
     const size_t smem = pencil_rows_smem(p);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_pencil_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_pencil_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_pencil_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     dim3 blk(NXP, KB), grd(pencil_rows_blocks(p), nrhs);
-    k_pencil_rows<<<grd, blk, smem, s>>>(p->nx, p->nxi, p->desc.beta, p->DxT, p->xi_x, p->xi_y, p->nu, p->G, m, x,
-                                        ldx, omega, mode, b, mask_b, y, normpart, done); klst::note_launch();
+    if (df_arith)
+        k_pencil_rows<true><<<grd, blk, smem, s>>>(p->nx, p->nxi, p->desc.beta, p->DxT, p->xi_x, p->xi_y, p->nu, p->G,
+                                                  m, x, ldx, omega, mode, b, mask_b, y, normpart, done);
+    else
+        k_pencil_rows<false><<<grd, blk, smem, s>>>(p->nx, p->nxi, p->desc.beta, p->DxT, p->xi_x, p->xi_y, p->nu, p->G,
+                                                   m, x, ldx, omega, mode, b, mask_b, y, normpart, done); klst::note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
@@ -195,7 +226,7 @@ int apply_pencil_dev(klst_pencil p, const double2* x, double2* y, int nrhs, cons
                      cudaStream_t s, double2* mwork, double2* mpart, int ngroups) {
     int rc = moments_dev(p, x, p->n, nrhs, mwork, mpart, ngroups, s, nullptr);
     if (rc) return rc;
-    return pencil_rows_dev(p, mwork, x, p->n, nrhs, omega_dev, 0, nullptr, 0, y, nullptr, s, nullptr);
+    return pencil_rows_dev(p, mwork, x, p->n, nrhs, omega_dev, 0, nullptr, 0, y, nullptr, s, nullptr, 0);
 }
 
 }  // namespace klst

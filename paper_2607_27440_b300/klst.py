@@ -16,6 +16,7 @@ c_int32, c_int64, c_double, c_void_p, c_uint64 = ctypes.c_int32, ctypes.c_int64,
 KLST_OK, KLST_EINVAL, KLST_ENOMEM, KLST_ESINGULAR, KLST_ENOCONV, KLST_EREFINE, KLST_ETIMEOUT, KLST_ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
 CONV_REL, CONV_RESID = 0, 1
+ARITH_F64, ARITH_DF64 = 0, 1
 BASES = {"tanh": 0, "mott_smith": 1}
 
 
@@ -29,7 +30,8 @@ class PencilDesc(ctypes.Structure):
 class EigsOpts(ctypes.Structure):
     _fields_ = [("nev", c_int32), ("ncv", c_int32), ("max_restarts", c_int32), ("max_refine", c_int32),
                 ("tol", c_double), ("refine_tol", c_double), ("v0", c_void_p), ("seed", c_uint64),
-                ("conv", c_int32), ("est_out", c_void_p), ("keep", c_int32)]
+                ("conv", c_int32), ("est_out", c_void_p), ("keep", c_int32),
+                ("arith", c_int32)]
 
 
 class EigsInfo(ctypes.Structure):
@@ -246,7 +248,7 @@ class Factor:
         return y
 
     def eigs(self, nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, v0=None, seed=0,
-             vectors=False, stream=None, check=True, conv=CONV_REL, keep=0):
+             vectors=False, stream=None, check=True, conv=CONV_REL, keep=0, arith=ARITH_F64):
         """Krylov-Schur shift-invert eigensolve; returns (omega[nev], vecs (nev, n) or None, resid[nev], info).
 
         info carries the klst_eigs_info fields plus ``status`` and ``ritz_est`` (final Ritz estimates).
@@ -261,7 +263,7 @@ class Factor:
         est = np.zeros(nev)
         opts = EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
                         refine_tol=refine_tol, v0=v0.data_ptr() if v0 is not None else None, seed=seed, conv=conv,
-                        est_out=est.ctypes.data, keep=keep)
+                        est_out=est.ctypes.data, keep=keep, arith=arith)
         info = EigsInfo()
         code = load().klst_eigs(self.handle, ctypes.byref(opts), ev.ctypes.data_as(c_void_p),
                                 _ptr(vec) if vec is not None else None, res.ctypes.data_as(c_void_p),
@@ -275,9 +277,10 @@ class Factor:
         return omega, vec, res, d
 
 
-def _opts(nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, seed=0, conv=CONV_REL, keep=0):
+def _opts(nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, seed=0, conv=CONV_REL, keep=0,
+          arith=ARITH_F64):
     return EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
-                    refine_tol=refine_tol, v0=None, seed=seed, conv=conv, est_out=None, keep=keep)
+                    refine_tol=refine_tol, v0=None, seed=seed, conv=conv, est_out=None, keep=keep, arith=arith)
 
 
 def batch_eigs(specs, sigmas, nev, ncv, precision=FP64, nworkers=0, **kw):

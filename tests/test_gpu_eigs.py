@@ -45,15 +45,17 @@ def test_tiny_all_nearest(klst, prec):
     assert np.allclose(np.linalg.norm(V, axis=1), 1.0)
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-def test_c1_against_golden(klst, prec):
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (0, 1), (1, 1)],
+                         ids=["fp64", "mixed", "fp64-df64basis", "mixed-df64"])
+def test_c1_against_golden(klst, prec, arith):
     spec, es = wl.c1()
     ref, kap, _ = read_golden("c1_eigs.txt")
     d = gas.pencil_data(spec.as_dict())
     A, B = pencil.assemble_dense(spec.as_dict(), d)
     P = klst.Pencil(spec)
     F = P.factor(es.sigma, precision=prec)
-    om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)), vectors=True)
+    om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)), vectors=True,
+                                arith=arith)
     _check_against(om, ref, kap, pencil_norm2_est(d, spec.beta))
     assert np.max(res) <= 1e-10
     r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
@@ -62,15 +64,16 @@ def test_c1_against_golden(klst, prec):
     assert np.all(np.diff(np.abs(om - es.sigma)) >= -1e-12)
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-def test_c2_against_golden(klst, prec):
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (1, 1)], ids=["fp64", "mixed", "mixed-df64"])
+def test_c2_against_golden(klst, prec, arith):
     spec, es = wl.c2()
     ref, kap, _ = read_golden("c2_eigs.txt")
     d = gas.pencil_data(spec.as_dict())
     normA = pencil_norm2_est(d, spec.beta)
     P = klst.Pencil(spec)
     F = P.factor(es.sigma, precision=prec)
-    om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)), vectors=True)
+    om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)), vectors=True,
+                                arith=arith)
     _check_against(om, ref, kap, normA)
     assert np.max(res) <= 1e-10
     r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
