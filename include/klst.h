@@ -49,7 +49,7 @@ typedef enum {
     KLST_ECUDA = -7       /* a CUDA runtime call failed */
 } klst_status;
 
-typedef enum { KLST_FP64 = 0, KLST_MIXED = 1 } klst_precision;
+typedef enum { KLST_FP64 = 0, KLST_MIXED = 1, KLST_DF64 = 2 } klst_precision;
 typedef enum { KLST_BASE_TANH_MAXWELL = 0, KLST_BASE_MOTT_SMITH = 1 } klst_base;
 
 /* Pencil description (all nondimensional: T by T_inf, rho by rho_inf, velocity by
@@ -186,8 +186,11 @@ size_t klst_apply_pencil_noalloc_capacity(void);
  * inflow rows replaced by identity rows; shared by g^ and h^) and U V^H is the
  * rank-4-per-point BGK moment coupling.  Computes every K_k^{-1} (batched
  * Gauss-Jordan with partial pivoting), the capacitance C = I - V^H K^{-1} U
- * (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan, one launch per pivot).  precision: KLST_FP64 (all float64) or KLST_MIXED
- * (K_k^{-1} in complex float32, corrected by float64 refinement in the apply).
+ * (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan, one launch per pivot).  precision: KLST_FP64 (all float64),
+ * KLST_MIXED (K_k^{-1} stored in complex float32, each apply corrected by float64 iterative refinement)
+ * or KLST_DF64 (K_k^{-1} stored as double-float pairs, the same bytes as float64, and the block solves
+ * run in double-float arithmetic on the float32 pipes; ~2^-48 accuracy without refinement).
+ * K_k^{-1} and the capacitance are always formed in float64.
  * Errors: KLST_ESINGULAR (zero pivot), KLST_ENOMEM.  Synchronising.
  */
 int klst_factor_shift(klst_pencil p, double sigma_re, double sigma_im, int32_t precision,

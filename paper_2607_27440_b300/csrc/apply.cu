@@ -5,6 +5,7 @@
 // the result is refined in float64: y += T~ (b - (A - sigma B) y).
 #include <algorithm>
 
+#include "df64.cuh"
 #include "factor.cuh"
 
 namespace klst {
@@ -46,8 +47,7 @@ __global__ void k_solve_pass1(int nx, int nxi, const C* __restrict__ KinvT, cons
             const C* Kk = KinvT + (size_t)k * nx * nx + j;
             const C* s0 = sb + (kk * 2 + 0) * NXP;
             const C* s1 = sb + (kk * 2 + 1) * NXP;
-            C zg, zh;
-            zg.x = zg.y = zh.x = zh.y = 0;
+            C zg = czero<C>(), zh = czero<C>();
 #pragma unroll 4
             for (int m = 0; m < nx; ++m) {
                 const C a = Kk[(size_t)m * nx];
@@ -134,8 +134,7 @@ __global__ void k_solve_pass2(int nx, int nxi, const C* __restrict__ KinvT, cons
             const C* Kk = KinvT + (size_t)k * nx * nx + j;
             const C* s0 = sb + (kk * 2 + 0) * NXP;
             const C* s1 = sb + (kk * 2 + 1) * NXP;
-            C zg, zh;
-            zg.x = zg.y = zh.x = zh.y = 0;
+            C zg = czero<C>(), zh = czero<C>();
 #pragma unroll 4
             for (int m = 0; m < nx; ++m) {
                 const C a = Kk[(size_t)m * nx];
@@ -192,19 +191,19 @@ static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y,
     const int ng = f->ngroups, kpg = ((nxi + ng - 1) / ng + KB - 1) / KB * KB;
     dim3 blk(NXP, KB);
     const size_t sm1 = std::max(sizeof(C) * KB * 2 * NXP, sizeof(double2) * 4 * KB * NXP);
-    prof_begin(sizeof(C) == 16 ? "solve_pass1_f64" : "solve_pass1_f32", s);
+    prof_begin(sizeof(C) == 16 ? "solve_pass1_16B" : "solve_pass1_f32", s);
     k_solve_pass1<C><<<dim3(ng, nrhs), blk, sm1, s>>>(nx, nxi, (const C*)f->KinvT, p->w, p->xi_x, b, p->n, mask, ng,
                                                       kpg, f->tpart, done); klst::note_launch();
-    prof_end(sizeof(C) == 16 ? "solve_pass1_f64" : "solve_pass1_f32", s);
+    prof_end(sizeof(C) == 16 ? "solve_pass1_16B" : "solve_pass1_f32", s);
     prof_begin("cap_solve", s);
     k_reduce_groups_ext(f->r, ng, f->tpart, f->t, done, nrhs, s);
     k_cinv_gemv<<<dim3((f->r * 32 + 255) / 256, nrhs), 256, 0, s>>>(f->r, f->Cinv, f->t, f->sv, done); klst::note_launch();
     prof_end("cap_solve", s);
-    prof_begin(sizeof(C) == 16 ? "solve_pass2_f64" : "solve_pass2_f32", s);
+    prof_begin(sizeof(C) == 16 ? "solve_pass2_16B" : "solve_pass2_f32", s);
     const int nb2 = std::min((nxi + KB - 1) / KB, 4 * device_sm_count());
     k_solve_pass2<C><<<dim3(nb2, nrhs), blk, sizeof(C) * KB * 2 * NXP, s>>>(nx, nxi, (const C*)f->KinvT, p->G, p->xi_x,
                                                                            b, p->n, mask, f->sv, y, accumulate, done); klst::note_launch();
-    prof_end(sizeof(C) == 16 ? "solve_pass2_f64" : "solve_pass2_f32", s);
+    prof_end(sizeof(C) == 16 ? "solve_pass2_16B" : "solve_pass2_f32", s);
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
@@ -213,6 +212,7 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
     int rc = factor_reserve(f, nrhs, s);
     if (rc) return rc;
     if (f->precision == KLST_FP64) return woodbury_solve<double2>(f, x, 1, y, 0, nrhs, s, nullptr);
+    if (f->precision == KLST_DF64) return woodbury_solve<float4>(f, x, 1, y, 0, nrhs, s, nullptr);
     klst_pencil p = f->p;
     // y0 = T~ x (float32 blocks), then float64 refinement sweeps on r = B x - (A - sigma B) y
     KLST_CK(cudaMemsetAsync(f->done, 0, sizeof(int) * nrhs, s));

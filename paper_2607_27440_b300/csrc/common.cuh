@@ -77,6 +77,11 @@ __host__ __device__ __forceinline__ void cfma(float2& a, float2 b, float2 c) {
 }
 
 template <typename C> __device__ __forceinline__ C to_c(double2 v);
+template <typename C> __device__ __forceinline__ C czero() {
+    C z;
+    memset(&z, 0, sizeof(C));
+    return z;
+}
 template <> __device__ __forceinline__ double2 to_c<double2>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 to_c<float2>(double2 v) { return mkf((float)v.x, (float)v.y); }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }

@@ -88,4 +88,15 @@ __device__ __forceinline__ cdf cdf_warp_sum(cdf a) {
     return a;
 }
 
+// float4-typed storage overloads, so the block-solve kernels can be instantiated for df64 factors
+__device__ __forceinline__ cdf cdf_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 cdf_pack(cdf a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ void cfma(float4& acc, float4 a, float4 b) {
+    cdf c = cdf_unpack(acc);
+    cdf_fma(c, cdf_unpack(a), cdf_unpack(b));
+    acc = cdf_pack(c);
+}
+template <> __device__ __forceinline__ float4 to_c<float4>(double2 v) { return cdf_pack(cdf_from(v)); }
+__device__ __forceinline__ double2 to_d(float4 v) { return cdf_to(cdf_unpack(v)); }
+
 }  // namespace klst

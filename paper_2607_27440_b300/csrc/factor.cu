@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "df64.cuh"
 #include "factor.cuh"
 
 namespace klst {
@@ -254,6 +255,12 @@ static int launch_cap(klst_factor f, const C* Kinv, double2* Cp, int nsplit, cud
     return KLST_OK;
 }
 
+// complex128 -> double-float pairs of the block inverses (df64 storage, same bytes)
+__global__ void k_split_df(const double2* __restrict__ in, float4* __restrict__ out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += gridDim.x * (size_t)blockDim.x)
+        out[i] = cdf_pack(cdf_from(in[i]));
+}
+
 // complex128 -> complex64 rounding of the block inverses (mixed precision storage)
 __global__ void k_round_c64(const double2* __restrict__ in, float2* __restrict__ out, size_t count) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += gridDim.x * (size_t)blockDim.x) {
@@ -309,7 +316,10 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
                                  klst_factor* out) {
     if (!out) { set_error("out is NULL"); return KLST_EINVAL; }
     *out = nullptr;
-    if (!p || (precision != KLST_FP64 && precision != KLST_MIXED)) { set_error("invalid factor arguments"); return KLST_EINVAL; }
+    if (!p || (precision != KLST_FP64 && precision != KLST_MIXED && precision != KLST_DF64)) {
+        set_error("invalid factor arguments");
+        return KLST_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     klst_factor f = new klst_factor_s();
@@ -323,7 +333,7 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     f->max_refine = 4;
     f->refine_tol = 1e-12;
     const int r = f->r;
-    const size_t esz = precision == KLST_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t esz = precision == KLST_MIXED ? sizeof(float2) : sizeof(double2);
     const int nsplit = std::max(1, std::min(p->nxi, 8));
     double2 *Cp = nullptr, *b0 = nullptr, *b1 = nullptr;
     int* bar = nullptr;
@@ -354,18 +364,21 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     // mixed factor then stores them rounded to complex float32, so the float32 solve carries only
     // the rounding of its operands and not the float32 elimination error.
     double2* K64 = (double2*)f->KinvT;
-    if (precision == KLST_MIXED) {
+    if (precision != KLST_FP64) {
         if ((e = dmalloc((void**)&K64, sizeof(double2) * (size_t)p->nxi * p->nx * p->nx, s)) != cudaSuccess)
             return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     }
-    auto free64 = [&]() { if (precision == KLST_MIXED) dfree(K64, s); };
+    auto free64 = [&]() { if (precision != KLST_FP64) dfree(K64, s); };
     int rc = launch_block_gj<double2>(f, K64, s);
     if (rc) { free64(); return fail(rc); }
     rc = launch_cap<double2>(f, K64, Cp, nsplit, s);
     if (rc) { free64(); return fail(rc); }
-    if (precision == KLST_MIXED) {
+    if (precision != KLST_FP64) {
         const size_t cnt = (size_t)p->nxi * p->nx * p->nx;
-        k_round_c64<<<(int)std::min<size_t>((cnt + 255) / 256, 8192), 256, 0, s>>>(K64, (float2*)f->KinvT, cnt); klst::note_launch();
+        const int nb = (int)std::min<size_t>((cnt + 255) / 256, 8192);
+        if (precision == KLST_MIXED) k_round_c64<<<nb, 256, 0, s>>>(K64, (float2*)f->KinvT, cnt);
+        else k_split_df<<<nb, 256, 0, s>>>(K64, (float4*)f->KinvT, cnt);
+        klst::note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) { free64(); return fail(cuda_fail(e, "round", __FILE__, __LINE__)); }
         free64();
     }

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_schur_house(SchurArgs a) {
         H[idx] = a.S[(size_t)j * a.lds + i];
     }
     for (int i = tid; i < m; i += nt) a.tau[i] = 0.0;
-    if (tid == 0) *a.nconv = 0;  // k_schur_qr sets -1 on failure; k_schur_post reads it
+    if (tid == 0) { *a.nconv = 0; *a.log_count = 0; }  // k_schur_qr sets nconv = -1 on failure
     __syncthreads();
     for (int c = 0; c + 2 < m; ++c) {
         double tail = 0.0;
@@ -308,14 +308,25 @@ __global__ void __launch_bounds__(32) k_schur_q(SchurArgs a) {
         g = tau * g;
         for (int i = c + 1; i < m; ++i) q[i * 32 + t] = q[i * 32 + t] - g * conj(vc[i]);
     }
+    // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in a register
     const int nrot = *a.log_count;
+    int ci = -1;     // column held in cx
+    double2 cx = mk(0, 0);
     for (int k = 0; k < nrot; ++k) {
         const Rot g = a.log[k];
-        double2 x = q[g.i * 32 + t], y = q[(g.i + 1) * 32 + t];
+        double2 x;
+        if (g.i == ci) x = cx;
+        else {
+            if (ci >= 0) q[ci * 32 + t] = cx;
+            x = q[g.i * 32 + t];
+        }
+        double2 y = q[(g.i + 1) * 32 + t];
         rot(x, y, g.c, conj(g.s));
         q[g.i * 32 + t] = x;
-        q[(g.i + 1) * 32 + t] = y;
+        ci = g.i + 1;
+        cx = y;
     }
+    if (ci >= 0) q[ci * 32 + t] = cx;
     if (r < m)
         for (int col = 0; col < m; ++col) a.Q[(size_t)col * m + r] = q[col * 32 + t];
 }
@@ -396,14 +407,28 @@ __global__ void __launch_bounds__(256) k_schur_post(SchurArgs a) {
         a.Ysel[(size_t)i * m + row] = acc;
     }
     __syncthreads();
-    // truncated Krylov-Schur relation: S[0:k,0:k] = T_kk, S[k,0:k] = beta Q[m-1, 0:k]
+    // truncated Krylov-Schur relation: S[0:k,0:k] = T_kk, S[k,0:k] = b = beta Q[m-1, 0:k].
+    // Locking: the leading Schur vectors whose coupling |b_j| already meets the convergence test
+    // get b_j = 0 (an exact deflation up to that tolerance), so the next restart's Householder
+    // reduction skips their columns and the QR sweeps deflate them without iterating.
+    __shared__ int s_lock;
+    if (tid == 0) {
+        int L = 0;
+        for (; L < a.keep; ++L) {
+            const double am = cabs(HH(L, L));
+            const double bj = cabs(beta) * cabs(QQ(m - 1, L));
+            if (!(bj <= a.tol * (a.conv ? am * am : am))) break;
+        }
+        s_lock = L;
+    }
+    __syncthreads();
     const int k = a.keep;
     for (int idx = tid; idx < a.lds * m; idx += nt) {
         const int i = idx % a.lds, j = idx / a.lds;
         double2 val = mk(0, 0);
         if (j < k) {
             if (i < k) val = (i <= j) ? HH(i, j) : mk(0, 0);
-            else if (i == k) val = beta * QQ(m - 1, j);
+            else if (i == k) val = (j < s_lock) ? mk(0, 0) : beta * QQ(m - 1, j);
         }
         a.S[(size_t)j * a.lds + i] = val;
     }
@@ -421,7 +446,8 @@ int launch_schur(const SchurArgs& a, cudaStream_t s) {
     const int m = a.m;
     const size_t packed = sizeof(double2) * (size_t)m * (m + 3) / 2;
     prof_begin("schur_house", s);
-    k_schur_house<<<1, 256, 0, s>>>(a); klst::note_launch();
+    k_schur_house<<<1, 256, 0, s>>>(a);
+    klst::note_launch();
     prof_end("schur_house", s);
     prof_begin("schur_qr", s);
     k_schur_qr<<<1, 256, packed, s>>>(a); klst::note_launch();

@@ -14,7 +14,7 @@ from . import build as _build
 c_int32, c_int64, c_double, c_void_p, c_uint64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64
 
 KLST_OK, KLST_EINVAL, KLST_ENOMEM, KLST_ESINGULAR, KLST_ENOCONV, KLST_EREFINE, KLST_ETIMEOUT, KLST_ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 CONV_REL, CONV_RESID = 0, 1
 ARITH_F64, ARITH_DF64 = 0, 1
 BASES = {"tanh": 0, "mott_smith": 1}

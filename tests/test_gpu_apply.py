@@ -30,7 +30,7 @@ def _oracle(spec, sigma):
     return d, A, B, eig.ShiftInvert(A, B, sigma)
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("spec,sigma", SMALL, ids=lambda v: str(v)[:40])
 def test_apply_matches_dense_lu(klst, spec, sigma, prec):
     """||y_gpu - y_oracle|| / ||y_oracle|| <= max(1e-12, 64 cond(A - sigma B) eps) on three seeded vectors."""
@@ -62,7 +62,7 @@ def test_multi_rhs_equals_single(klst):
         assert np.array_equal(yi, Y[i])
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("which", ["c2", "c3"])
 def test_apply_full_size_residual(klst, which, prec):
     """Full workload sizes: the oracle's matrix-free rows give ||(A - sigma B) y - B x|| / ||B x||."""

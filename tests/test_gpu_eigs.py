@@ -45,8 +45,8 @@ def test_tiny_all_nearest(klst, prec):
     assert np.allclose(np.linalg.norm(V, axis=1), 1.0)
 
 
-@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (0, 1), (1, 1)],
-                         ids=["fp64", "mixed", "fp64-df64basis", "mixed-df64"])
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (0, 1), (1, 1), (2, 1)],
+                         ids=["fp64", "mixed", "fp64-df64basis", "mixed-df64", "df64"])
 def test_c1_against_golden(klst, prec, arith):
     spec, es = wl.c1()
     ref, kap, _ = read_golden("c1_eigs.txt")
@@ -64,7 +64,7 @@ def test_c1_against_golden(klst, prec, arith):
     assert np.all(np.diff(np.abs(om - es.sigma)) >= -1e-12)
 
 
-@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (1, 1)], ids=["fp64", "mixed", "mixed-df64"])
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (1, 1), (2, 1)], ids=["fp64", "mixed", "mixed-df64", "df64"])
 def test_c2_against_golden(klst, prec, arith):
     spec, es = wl.c2()
     ref, kap, _ = read_golden("c2_eigs.txt")
