@@ -6,7 +6,7 @@ purification and explicit residuals (klst_eigs).  Only eigenpairs with explicit 
 ||A q - omega B q|| <= 1e-10 (||q|| = 1) count.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c3|c2|c1] [--precision mixed|fp64]
+                    [--workload c3|c2|c1] [--precision df64|mixed|fp64]
 
 Multi-GPU runs (torchrun) solve independent pencils per rank (replicas; weak scaling).
 """
@@ -34,8 +34,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
+    ap.add_argument("--precision", default="df64", choices=["df64", "mixed", "fp64"],
+                    help="df64: double-float factors and basis; mixed: c64 factors + fp64 refinement; fp64: plain")
+    ap.add_argument("--no-compare", action="store_true", help="skip the runs of the other two paths")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
@@ -112,8 +113,85 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-# FP64 rate: the B300's float64 units (nominal 1.25 TFLOP/s dense; the recipe's figure).
+# Peaks for the arithmetic-bound kernels, from the B300's unit counts (profiling recipe):
+# float64 1.25 TFLOP/s nominal; float32 148 SMs x 128 lanes x 2,032 MHz maximum clock.
 FP64_PEAK_TFLOPS = 1.25
+FP32_LANE_OPS_PEAK_T = 148 * 128 * 2.032e9 / 1e12   # 38.5 T lane instructions/s
+# float32 instructions of one complex double-float multiply-add (4 real df64 FMAs x 15, see df64.cuh)
+DF64_OPS_PER_CMAC = 60
+
+# path name -> (factor precision, Krylov-basis arithmetic)
+PATHS = {
+    "df64": ("DF64", "ARITH_DF64"),   # K^-1 and the Krylov basis in double-float (float32 pipes)
+    "mixed": ("MIXED", "ARITH_F64"),  # complex-float32 K^-1 + float64 refinement, float64 Arnoldi
+    "fp64": ("FP64", "ARITH_F64"),    # everything in float64: the plain FP64 GPU path
+}
+PATH_DTYPE = {
+    "df64": "df64 (double-float: K^-1, block solves and Krylov basis on float32 pipes; fp64 capacitance, Schur, residuals)",
+    "mixed": "c64+f64 (complex fp32 K^-1 and block solves, fp64 refinement, Arnoldi, Schur, residuals)",
+    "fp64": "c128 (fp64 throughout)",
+}
+
+
+def kernel_rooflines(groups, spec, es, info_list, steps, peaks):
+    """Per-group device time (CUDA events on the launching stream, timed region) and, for the
+    groups with an algorithmic cost model, the achieved rate against its bound."""
+    nx, nxi = spec.nx, spec.nxi
+    n = 2 * nx * nxi
+    F = nxi * nx * nx                      # stored K^-1 entries
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    out = {}
+    for name, (ms, calls) in groups.items():
+        e = {"total_ms_per_step": ms / steps, "launch_groups": calls, "avg_ms": ms / max(calls, 1)}
+        avg_s = e["avg_ms"] / 1e3
+        if name.startswith("solve_pass"):
+            vec_bytes = (1 if "pass1" in name else 2) * n * 16
+            if name.endswith("_df64"):
+                ops = 2 * F * DF64_OPS_PER_CMAC
+                e.update(bound="alu", unit="T FP32 lane-ops/s", algorithmic=f"{ops:.4g} FP32 ops/launch "
+                         f"(2 x {F:,} complex MACs x {DF64_OPS_PER_CMAC})", achieved=ops / avg_s / 1e12,
+                         peak=FP32_LANE_OPS_PEAK_T, hbm_gbs=(16 * F + vec_bytes) / avg_s / 1e9)
+            elif name.endswith("_c128"):
+                fl = 2 * F * 8
+                e.update(bound="alu", unit="TFLOP/s (fp64)", algorithmic=f"{fl:.4g} fp64 flops/launch",
+                         achieved=fl / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
+                         hbm_gbs=(16 * F + vec_bytes) / avg_s / 1e9)
+            else:
+                by = 8 * F + vec_bytes
+                e.update(bound="hbm", unit="GB/s", algorithmic=f"{by:.4g} B/launch", achieved=by / avg_s / 1e9,
+                         peak=hbm)
+        elif name in ("orth_pass1", "orth_pass2"):
+            # classical Gram-Schmidt against j+1 basis vectors reads them twice (dots, update)
+            # per pass; the DGKS second pass repeats it when triggered
+            js = []
+            for info in info_list:
+                js += list(range(0, es.ncv))
+                keep = es.keep or (es.nev + (es.ncv - es.nev) // 2)
+                js += list(range(keep, es.ncv)) * info["restarts"]
+            passes = 1.0
+            if name == "orth_pass1":
+                # in the df64 path the group holds both passes
+                nsteps = max(len(js), 1)
+                reo = sum(i.get("reorths", 0) for i in info_list)
+                passes = 1.0 + reo / nsteps if groups.get("orth_pass2") is None else 1.0
+            by = sum(2 * (j + 1) * n * 16 * passes + 3 * n * 16 for j in js)
+            e.update(bound="hbm", unit="GB/s", algorithmic="sum over steps of 2 (j+1) n x 16 B per pass",
+                     achieved=by / (ms / 1e3) / 1e9, peak=hbm)
+        elif name == "rotate":
+            by = (es.ncv * n + (es.keep or es.nev + (es.ncv - es.nev) // 2) * n) * 16
+            e.update(bound="hbm", unit="GB/s", algorithmic=f"{by:.4g} B/launch (read V, write V Q)",
+                     achieved=by / avg_s / 1e9, peak=hbm)
+        if "peak" in e:
+            e["frac"] = e["achieved"] / e["peak"]
+        out[name] = e
+    return out
+
+
+def _jsonable(o):
+    """numpy scalars and arrays in the JSON line"""
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    raise TypeError(f"not JSON serialisable: {type(o).__name__}")
 
 
 def run_ours(args):
@@ -125,7 +203,6 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec = klst.MIXED if args.precision == "mixed" else klst.FP64
     spec, es, sigma = workload(args.workload, rank)
     n = spec.n
     from paper_2607_27440_b300 import workloads as wl
@@ -134,11 +211,12 @@ def run_ours(args):
     v0 = v0_host.to("cuda")
     stream = torch.cuda.current_stream()
 
-    def step(precision, v0_dev, vec_out):
+    def step(path, v0_dev, vec_out):
+        prec, arith = (getattr(klst, a) for a in PATHS[path])
         P = klst.Pencil(spec)
-        F = P.factor(sigma, precision=precision)
+        F = P.factor(sigma, precision=prec)
         om, vec, res, info = F.eigs(es.nev, es.ncv, tol=CONV_TOL, conv=klst.CONV_RESID, max_restarts=es.max_restarts,
-                                    v0=v0_dev, vectors=vec_out, check=False)
+                                    v0=v0_dev, vectors=vec_out, check=False, keep=es.keep, arith=arith)
         good = int(np.sum(res <= RESID_MAX)) if info["status"] in (0, klst.KLST_ENOCONV) else 0
         return good, om, vec, res, info, P, F
 
@@ -150,20 +228,25 @@ def run_ours(args):
 
     # warm-up
     for _ in range(args.warmup):
-        step(prec, v0, False)
+        step(args.precision, v0, False)
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = klst.load().klst_launch_count()
+    klst.prof_reset()
+    klst.prof_enable(True)
     ev0.record(stream)
-    good_total, infos = 0, []
+    good_total, infos, oms = 0, [], []
     for _ in range(args.steps):
-        g, om, vec, res, info, P, F = step(prec, v0, False)
+        g, om, vec, res, info, P, F = step(args.precision, v0, False)
         good_total += g
         infos.append(info)
+        oms.append(om)
     ev1.record(stream)
     barrier()
+    klst.prof_enable(False)
+    groups = klst.prof_read()
     launches = int(klst.load().klst_launch_count() - launches0)
     clocks = sampler.stop()
     dev_ms = ev0.elapsed_time(ev1)
@@ -174,7 +257,7 @@ def run_ours(args):
     h2d = d2h = 0
     for _ in range(0 if args.no_e2e else args.steps):
         v0_dev = v0_pinned.to("cuda", non_blocking=True)
-        g, om, vec, res, info, P, F = step(prec, v0_dev, True)
+        g, om, vec, res, info, P, F = step(args.precision, v0_dev, True)
         vec_host = vec.cpu()
         e2e_good += g
         h2d = v0_pinned.numel() * 16
@@ -192,36 +275,57 @@ def run_ours(args):
         good_total, e2e_good = tsum.tolist()
     else:
         e2e_ms = e2e_s * 1e3
-    compare = None
+    # the other paths on the same pencil, and every path's eigenvalues against the float64 path's
+    compare, om_fp64 = {}, None
     if not args.no_compare and rank == 0:
-        other = klst.FP64 if prec == klst.MIXED else klst.MIXED
-        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        step(other, v0, False)
-        e0_.record(stream)
-        g2, om2, _, res2, info2, _, _ = step(other, v0, False)
-        e1_.record(stream)
-        torch.cuda.synchronize()
-        ms2 = e0_.elapsed_time(e1_)
-        perm = np.array([int(np.argmin(np.abs(om2 - z))) for z in om])
-        compare = {"precision": "fp64" if other == klst.FP64 else "mixed", "eigenpairs_per_s": g2 / (ms2 / 1e3),
-                   "ms_per_step": ms2, "max_rel_eig_diff_vs_this_path": float(np.max(np.abs(om2[perm] - om) / np.abs(om))),
-                   "restarts": info2["restarts"], "applies": info2["applies"]}
+        for other in PATHS:
+            if other == args.precision:
+                continue
+            step(other, v0, False)
+            e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0_.record(stream)
+            g2, om2, _, res2, info2, _, _ = step(other, v0, False)
+            e1_.record(stream)
+            torch.cuda.synchronize()
+            ms2 = e0_.elapsed_time(e1_)
+            compare[other] = {"dtype": PATH_DTYPE[other], "eigenpairs_per_s": g2 / (ms2 / 1e3), "ms_per_step": ms2,
+                              "good_eigenpairs": g2, "restarts": info2["restarts"], "applies": info2["applies"],
+                              "t_factor_ms": info2["t_factor_ms"], "t_eigs_ms": info2["t_eigs_ms"],
+                              "max_resid": info2["max_resid"], "_om": om2}
+            if other == "fp64":
+                om_fp64 = om2
+
+    def eig_err(om):
+        if om_fp64 is None:
+            return None
+        perm = np.array([int(np.argmin(np.abs(om_fp64 - z))) for z in om])
+        return float(np.max(np.abs(om_fp64[perm] - om) / np.abs(om_fp64[perm])))
+
+    for other, c in compare.items():
+        om_other = c.pop("_om")
+        c["max_rel_eig_err_vs_fp64_path"] = eig_err(om_other) if other != "fp64" else 0.0
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
     info = infos[-1]
     value = good_total / (dev_ms / 1e3)
-    # roofline: the orthogonalisation phase (classical Gram-Schmidt + reorthogonalisation, float64)
-    # is float64-ALU bound; algorithmic flops per Arnoldi step j = 4 passes * 8 flops * (j + 1) * n
-    steps_per = []
-    k_keep = min(es.ncv - 1, es.nev + (es.ncv - es.nev) // 2)
-    first = list(range(0, es.ncv))
-    later = list(range(k_keep, es.ncv))
-    js = first + later * info["restarts"]
-    orth_flops = sum(4 * 8 * (j + 1) * n for j in js)
-    orth_tflops = orth_flops / (info["t_orth_ms"] / 1e3) / 1e12 if info["t_orth_ms"] > 0 else 0.0
     peaks, src = measured_peaks()
+    kernels = kernel_rooflines(groups, spec, es, infos, args.steps, peaks)
+    # the roofline object describes the kernel group with the largest share of the timed region
+    # among those with a cost model
+    modelled = {k: v for k, v in kernels.items() if "frac" in v}
+    top = max(modelled, key=lambda k: modelled[k]["total_ms_per_step"]) if modelled else None
+    roof = None
+    if top:
+        t = modelled[top]
+        roof = {"kernel": top, "bound": t["bound"], "achieved": t["achieved"], "peak": t["peak"], "unit": t["unit"],
+                "frac": t["frac"], "traffic": None, "algorithmic": t["algorithmic"],
+                "share_of_step": t["total_ms_per_step"] / (dev_ms / args.steps),
+                "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if t["bound"] == "hbm" and src == "measured"
+                                else "derived from unit counts and the 2,032 MHz maximum clock" if t["bound"] == "alu"
+                                else src)}
+    largest = max(kernels, key=lambda k: kernels[k]["total_ms_per_step"]) if kernels else None
     line = {
         "metric": "eigenpairs/s at 281k unknowns (resid<=1e-10), mixed vs FP64; p99 solve latency",
         "value": value,
@@ -233,33 +337,36 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64+f64 (complex fp32 block inverses, fp64 refinement/Arnoldi)" if prec == klst.MIXED else "c128 (fp64)",
+        "dtype": PATH_DTYPE[args.precision],
         "data": "synthetic (Mott-Smith argon shock base flow, seeded start vector)",
         "config": {"workload": f"{args.workload}: M=4.0 Mott-Smith shock, Nx=128, Nxi=61x18, n=281,088, "
                                f"40 eigenvalues near sigma=0.05+0.2i, ncv 120" if args.workload == "c3" else args.workload,
-                   "n": n, "nev": es.nev, "ncv": es.ncv, "precision": args.precision, "parallelism": f"replicas x{ws}",
-                   "l2": "working set > L2 (factors 144-288 MB, Krylov basis 544 MB)"},
+                   "n": n, "nev": es.nev, "ncv": es.ncv, "keep": es.keep, "path": args.precision,
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "working set > L2 (K^-1 288 MB, Krylov basis 544 MB), no flush needed"},
         "per_step": {"restarts": info["restarts"], "applies": info["applies"], "refine_sweeps": info["refine_sweeps"],
-                     "t_factor_ms": info["t_factor_ms"], "t_apply_ms": info["t_apply_ms"],
+                     "reorths": info.get("reorths"), "t_factor_ms": info["t_factor_ms"],
+                     "t_eigs_ms": info["t_eigs_ms"], "t_apply_ms": info["t_apply_ms"],
                      "t_orth_ms": info["t_orth_ms"], "t_restart_ms": info["t_restart_ms"],
                      "t_schur_ms": info["t_schur_ms"], "max_resid": info["max_resid"],
-                     "good_eigenpairs": good_total / args.steps, "status": info["status"]},
-        "roofline": {"kernel": "orthogonalisation (k_dots + k_update, CGS2 in float64)", "bound": "alu",
-                     "achieved": orth_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": orth_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "nominal B300 float64 rate (1.25 TFLOP/s, profiling recipe); not in MEASURED_PEAKS.json"},
+                     "good_eigenpairs": good_total / args.steps, "status": info["status"],
+                     "eigs_only_eigenpairs_per_s": (good_total / args.steps) / (info["t_eigs_ms"] / 1e3)},
+        "max_rel_eig_err_vs_fp64_path": eig_err(oms[-1]) if args.precision != "fp64" else 0.0,
+        "roofline": roof,
+        "largest_kernel_group": largest,
+        "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": None if args.no_e2e else {"value": e2e_good / (e2e_ms / 1e3), "unit": "eigenpairs/s",
                                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "compare": compare,
+        "compare": compare or None,
         "peaks_source": src,
     }
     if not args.no_batch:
         line["batched"] = batched_sweep(klst, compare=not args.no_compare)
         line["serving"] = serving_run(klst, args.serve_rate, args.serve_window)
     line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(args)
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_jsonable), flush=True)
     if ws > 1:
         dist.destroy_process_group()
 
@@ -272,10 +379,11 @@ def batched_sweep(klst, compare=True):
     out = {"workload": "256 independent Mott-Smith pencils, Mach U[1.2,4], beta U[0,2], Nx in {32,48,64,96}, "
                        "Nxi in {8x6,12x8,16x12,16x16}, sigma = 0.1i(1+U[0,1]), 20 eigenvalues, ncv 40",
            "workers": 16}
-    for name, prec in (("mixed", klst.MIXED), ("fp64", klst.FP64)) if compare else (("mixed", klst.MIXED),):
+    for name in PATHS if compare else ("df64",):
+        prec, arith = (getattr(klst, a) for a in PATHS[name])
         t0 = time.perf_counter()
         om, res, st, infos = klst.batch_eigs(specs, sig, 20, 40, precision=prec, nworkers=16, tol=CONV_TOL,
-                                             conv=klst.CONV_RESID, seed=4)
+                                             conv=klst.CONV_RESID, seed=4, arith=arith)
         dt = time.perf_counter() - t0
         good = int(np.sum(res <= RESID_MAX))
         out[name] = {"eigenpairs_per_s": good / dt, "s": dt, "good_eigenpairs": good,
@@ -293,7 +401,8 @@ def serving_run(klst, rate, window):
     for ta, spec, z in reqs:
         while time.perf_counter() - t0 < ta:
             time.sleep(0.0005)
-        tickets.append(S.submit(spec, z, 20, 40, precision=klst.MIXED, tol=CONV_TOL, conv=klst.CONV_RESID, seed=5))
+        tickets.append(S.submit(spec, z, 20, 40, precision=klst.DF64, tol=CONV_TOL, conv=klst.CONV_RESID, seed=5,
+                                arith=klst.ARITH_DF64))
     lats, good, fails = [], 0, 0
     for t in tickets:
         om, res, info, lat, code = S.poll(t, wait=True)

@@ -115,6 +115,20 @@ typedef struct klst_factor_s* klst_factor;
 /* Number of CUDA kernels this library has launched in the process so far (all threads). */
 unsigned long long klst_launch_count(void);
 
+/*
+ * Per-kernel-group device timing (instrumentation; the paper has no counterpart).
+ * klst_prof_enable(1) makes the library record a pair of CUDA events on the launching stream
+ * around each group of launches it names (for example "solve_pass1_df64", "orth_pass1",
+ * "schur_qr"); klst_prof_enable(0) stops recording.  Totals accumulate across calls until
+ * klst_prof_reset().  klst_prof_entry(i, ...) waits for the recorded events, copies group i's
+ * name (NUL-terminated, truncated to name_cap bytes), total milliseconds and number of timed
+ * groups, and returns the number of groups; an i outside [0, count) only returns the count.
+ * Thread-safe; with recording off the library's launch path is unchanged.
+ */
+void klst_prof_enable(int32_t on);
+void klst_prof_reset(void);
+int32_t klst_prof_entry(int32_t i, char* name, int32_t name_cap, double* total_ms, int64_t* calls);
+
 /* Status text ("KLST_OK", ...) and the calling thread's last error message. */
 const char* klst_status_string(int status);
 const char* klst_last_error(void);

@@ -183,6 +183,11 @@ __global__ void k_refine_check(int nblk, const double* __restrict__ normpart, do
     else if (!last) atomicAdd(sweeps, 1);
 }
 
+template <typename C> static const char* pass_name(int pass);
+template <> const char* pass_name<double2>(int pass) { return pass == 1 ? "solve_pass1_c128" : "solve_pass2_c128"; }
+template <> const char* pass_name<float4>(int pass) { return pass == 1 ? "solve_pass1_df64" : "solve_pass2_df64"; }
+template <> const char* pass_name<float2>(int pass) { return pass == 1 ? "solve_pass1_c64" : "solve_pass2_c64"; }
+
 template <typename C>
 static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
                           cudaStream_t s, const int* done) {
@@ -191,19 +196,19 @@ static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y,
     const int ng = f->ngroups, kpg = ((nxi + ng - 1) / ng + KB - 1) / KB * KB;
     dim3 blk(NXP, KB);
     const size_t sm1 = std::max(sizeof(C) * KB * 2 * NXP, sizeof(double2) * 4 * KB * NXP);
-    prof_begin(sizeof(C) == 16 ? "solve_pass1_16B" : "solve_pass1_f32", s);
+    prof_begin(pass_name<C>(1), s);
     k_solve_pass1<C><<<dim3(ng, nrhs), blk, sm1, s>>>(nx, nxi, (const C*)f->KinvT, p->w, p->xi_x, b, p->n, mask, ng,
                                                       kpg, f->tpart, done); klst::note_launch();
-    prof_end(sizeof(C) == 16 ? "solve_pass1_16B" : "solve_pass1_f32", s);
+    prof_end(pass_name<C>(1), s);
     prof_begin("cap_solve", s);
     k_reduce_groups_ext(f->r, ng, f->tpart, f->t, done, nrhs, s);
     k_cinv_gemv<<<dim3((f->r * 32 + 255) / 256, nrhs), 256, 0, s>>>(f->r, f->Cinv, f->t, f->sv, done); klst::note_launch();
     prof_end("cap_solve", s);
-    prof_begin(sizeof(C) == 16 ? "solve_pass2_16B" : "solve_pass2_f32", s);
+    prof_begin(pass_name<C>(2), s);
     const int nb2 = std::min((nxi + KB - 1) / KB, 4 * device_sm_count());
     k_solve_pass2<C><<<dim3(nb2, nrhs), blk, sizeof(C) * KB * 2 * NXP, s>>>(nx, nxi, (const C*)f->KinvT, p->G, p->xi_x,
                                                                            b, p->n, mask, f->sv, y, accumulate, done); klst::note_launch();
-    prof_end(sizeof(C) == 16 ? "solve_pass2_16B" : "solve_pass2_f32", s);
+    prof_end(pass_name<C>(2), s);
     KLST_CK_LAUNCH();
     return KLST_OK;
 }

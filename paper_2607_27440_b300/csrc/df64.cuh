@@ -88,6 +88,76 @@ __device__ __forceinline__ cdf cdf_warp_sum(cdf a) {
     return a;
 }
 
+// ---------------------------------------------------------------- scalar and complex helpers
+// a * b: TwoProd of the high parts by one FMA, plus the cross terms, renormalised (Fast2Sum)
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+// multiplication by a power of two (exact while no part leaves the float32 range)
+__device__ __forceinline__ df df_scale(df a, float p2) { return {__fmul_rn(a.hi, p2), __fmul_rn(a.lo, p2)}; }
+
+// 1 / sqrt(x) for a normal x > 0.  Seed y0 = float32 reciprocal square root (about 22 correct
+// bits); with r = 1 - x y0^2 (formed in df64; |r| ~ 2^-22) the exact value is
+// y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3 r^2/8 + O(r^3)), so one step of this series (Halley's
+// method) leaves an error of order r^3 ~ 2^-66, below df64 rounding.
+__device__ __forceinline__ df df_rsqrt(df x) {
+    const float y0 = rsqrtf(x.hi);
+    const float q = __fmul_rn(y0, y0);
+    const df yy = {q, __fmaf_rn(y0, y0, -q)};                    // y0^2 exactly
+    const df r = df_sub(df{1.f, 0.f}, df_mul(x, yy));
+    const float h = __fmul_rn(0.5f, y0);
+    const float p = __fmul_rn(h, r.hi);
+    float e = __fmaf_rn(h, r.hi, -p);                            // y0 r / 2 = p + e (high part exact)
+    e = __fmaf_rn(h, r.lo, e);
+    e = __fmaf_rn(__fmul_rn(0.75f, p), r.hi, e);                 // + 3 y0 r^2 / 8
+    return df_add(df{y0, 0.f}, df{p, e});
+}
+
+__device__ __forceinline__ cdf cdf_neg(cdf a) { return {df_neg(a.re), df_neg(a.im)}; }
+__device__ __forceinline__ cdf cdf_conj(cdf a) { return {a.re, df_neg(a.im)}; }
+__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
+    cdf r = {df_mul(a.re, b.re), df_mul(a.re, b.im)};
+    df_fma(r.re, df_neg(a.im), b.im);
+    df_fma(r.im, a.im, b.re);
+    return r;
+}
+__device__ __forceinline__ cdf cdf_rmul(df c, cdf a) { return {df_mul(c, a.re), df_mul(c, a.im)}; }
+__device__ __forceinline__ cdf cdf_scale(cdf a, float p2) { return {df_scale(a.re, p2), df_scale(a.im, p2)}; }
+__device__ __forceinline__ df cdf_abs2(cdf a) {
+    df r = df_mul(a.re, a.re);
+    df_fma(r, a.im, a.im);
+    return r;
+}
+// |re| + |im| of the leading parts (float32), for magnitude tests
+__device__ __forceinline__ float cdf_abs1f(cdf a) { return fabsf(a.re.hi) + fabsf(a.im.hi); }
+
+// plane rotation x' = c x + s y, y' = c y - conj(s) x with real c.  The terms in y are formed
+// first, so a caller that carries x from the previous rotation waits on two df64 FMAs only.
+__device__ __forceinline__ void cdf_rot(cdf& x, cdf& y, df c, cdf s) {
+    cdf t = {df_mul(s.re, y.re), df_mul(s.re, y.im)};
+    df_fma(t.re, df_neg(s.im), y.im);
+    df_fma(t.im, s.im, y.re);
+    cdf u = {df_mul(c, y.re), df_mul(c, y.im)};
+    df_fma(t.re, c, x.re);
+    df_fma(t.im, c, x.im);
+    df_fma(u.re, df_neg(s.re), x.re);
+    df_fma(u.im, df_neg(s.re), x.im);
+    df_fma(u.re, df_neg(s.im), x.im);
+    df_fma(u.im, s.im, x.re);
+    x = t;
+    y = u;
+}
+
+__device__ __forceinline__ float2 df_pack(df a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ df df_unpack(float2 v) { return {v.x, v.y}; }
+
 // float4-typed storage overloads, so the block-solve kernels can be instantiated for df64 factors
 __device__ __forceinline__ cdf cdf_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 __device__ __forceinline__ float4 cdf_pack(cdf a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }

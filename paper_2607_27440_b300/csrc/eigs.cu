@@ -204,9 +204,12 @@ __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ V, i
 // and basis rotations run in df64 arithmetic on the float32 pipes (see df64.cuh).
 
 // part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]; with_self adds column ncols = |w|^2.
-__global__ void k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ w,
-                          int64_t n, int chunk, double2* __restrict__ part, int ldp, int with_self,
-                          const int* __restrict__ gate) {
+// Each warp takes two columns at a time and keeps two accumulators per column (rows lane + 64 u
+// and lane + 32 + 64 u), so four independent loads and multiply-add chains are in flight.
+__global__ void __launch_bounds__(256) k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols,
+                                                 const double2* __restrict__ w, int64_t n, int chunk,
+                                                 double2* __restrict__ part, int ldp, int with_self,
+                                                 const int* __restrict__ gate) {
     if (gate && *gate == 0) return;
     extern __shared__ float4 swf[];
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
@@ -214,12 +217,31 @@ __global__ void k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols, 
     for (int i = threadIdx.x; i < len; i += blockDim.x) cdf_store(&swf[i], cdf_from(w[r0 + i]));
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int col = wid; col < ncols; col += nw) {
-        const float4* vc = V + col * ldv + r0;
-        cdf a = cdf_zero();
-        for (int i = lane; i < len; i += 32) cdf_fma_conj(a, cdf_load(vc + i), cdf_load(swf + i));
-        a = cdf_warp_sum(a);
-        if (lane == 0) part[(size_t)blockIdx.x * ldp + col] = cdf_to(a);
+    for (int col = 2 * wid; col < ncols; col += 2 * nw) {
+        const bool two = col + 1 < ncols;
+        const float4* v0 = V + col * ldv + r0;
+        const float4* v1 = two ? v0 + ldv : v0;
+        cdf a0 = cdf_zero(), a1 = cdf_zero(), b0 = cdf_zero(), b1 = cdf_zero();
+        int i = lane;
+        for (; i + 32 < len; i += 64) {
+            const float4 x0 = v0[i], x1 = v0[i + 32], y0 = v1[i], y1 = v1[i + 32];
+            const cdf w0 = cdf_load(swf + i), w1 = cdf_load(swf + i + 32);
+            cdf_fma_conj(a0, cdf_unpack(x0), w0);
+            cdf_fma_conj(a1, cdf_unpack(x1), w1);
+            cdf_fma_conj(b0, cdf_unpack(y0), w0);
+            cdf_fma_conj(b1, cdf_unpack(y1), w1);
+        }
+        if (i < len) {
+            const cdf w0 = cdf_load(swf + i);
+            cdf_fma_conj(a0, cdf_load(v0 + i), w0);
+            cdf_fma_conj(b0, cdf_load(v1 + i), w0);
+        }
+        a0 = cdf_warp_sum(cdf_add(a0, a1));
+        b0 = cdf_warp_sum(cdf_add(b0, b1));
+        if (lane == 0) {
+            part[(size_t)blockIdx.x * ldp + col] = cdf_to(a0);
+            if (two) part[(size_t)blockIdx.x * ldp + col + 1] = cdf_to(b0);
+        }
     }
     if (with_self && wid == 0) {  // |w|^2 of the chunk in float64
         double s2 = 0.0;
@@ -229,9 +251,11 @@ __global__ void k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols, 
     }
 }
 
-// w -= V h (ncols columns, df64 accumulation); per-block partials of |w|^2
-__global__ void k_update_df(const float4* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ h,
-                            double2* __restrict__ w, int64_t n, double* __restrict__ npart, const int* __restrict__ gate) {
+// w -= V h (ncols columns, df64 accumulation); per-block partials of |w|^2.  Two accumulators
+// (even and odd columns) halve the dependent chain per row and keep two loads in flight.
+__global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V, int64_t ldv, int ncols,
+                                                   const double2* __restrict__ h, double2* __restrict__ w, int64_t n,
+                                                   double* __restrict__ npart, const int* __restrict__ gate) {
     if (gate && *gate == 0) return;
     extern __shared__ float4 shf[];
     for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
@@ -241,9 +265,15 @@ __global__ void k_update_df(const float4* __restrict__ V, int64_t ldv, int ncols
     __syncthreads();
     double nrm = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        cdf acc = cdf_from(w[i]);
-        for (int c = 0; c < ncols; ++c) cdf_fma(acc, cdf_load(V + c * ldv + i), cdf_load(shf + c));
-        const double2 out = cdf_to(acc);
+        cdf acc0 = cdf_from(w[i]), acc1 = cdf_zero();
+        int c = 0;
+        for (; c + 1 < ncols; c += 2) {
+            const float4 x0 = V[c * ldv + i], x1 = V[(c + 1) * ldv + i];
+            cdf_fma(acc0, cdf_unpack(x0), cdf_load(shf + c));
+            cdf_fma(acc1, cdf_unpack(x1), cdf_load(shf + c + 1));
+        }
+        if (c < ncols) cdf_fma(acc0, cdf_load(V + c * ldv + i), cdf_load(shf + c));
+        const double2 out = cdf_to(cdf_add(acc0, acc1));
         w[i] = out;
         nrm += abs2(out);
     }
@@ -362,9 +392,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     const int lds = m + 1;
     const int sms = device_sm_count();
     int chunk = 256;
-    while ((n + chunk - 1) / chunk > 2 * sms && chunk < 2048) chunk *= 2;
+    while ((n + chunk - 1) / chunk > 4 * sms && chunk < 2048) chunk *= 2;
     const int nchunks = (int)((n + chunk - 1) / chunk);
-    const int nblk = std::min<int64_t>((n + 255) / 256, 4 * sms);
+    const int nblk = std::min<int64_t>((n + 255) / 256, 6 * sms);  // 6 resident 256-thread CTAs per SM
     const int ng = pencil_work_groups(p);
     if (o->keep != 0 && (o->keep < nev || o->keep >= m)) {
         set_error("invalid keep=%d (need nev <= keep < ncv)", o->keep);
@@ -507,7 +537,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         SchurArgs a;
         a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
         a.Ysel = W.Ysel; a.mu_sel = W.musel; a.est_sel = W.estsel;
-        a.Vh = W.Vh; a.tau = W.tau; a.log = W.rlog; a.log_cap = log_cap; a.log_count = W.rcount;
+        a.Vh = (float4*)W.Vh; a.tau = W.tau; a.log = W.rlog; a.log_cap = log_cap; a.log_count = W.rcount;
         a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.conv = o->conv; a.st = f->status;
         cudaEventRecord(evs[3 * (m + 1)], s);
         if ((rc = launch_schur(a, s)) != KLST_OK) return fail(rc);

@@ -329,7 +329,11 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     f->sigma = mk(sr, si);
     f->precision = precision;
     f->nx = p->nx; f->nxi = p->nxi; f->r = 4 * p->nx; f->n = p->n;
-    f->ngroups = pencil_work_groups(p);
+    {
+        // block-solve pass 1: one CTA per KB velocity blocks, up to four resident CTAs per SM
+        const int KB = 256 / ((p->nx + 31) & ~31);
+        f->ngroups = std::max(1, std::min((p->nxi + KB - 1) / KB, 4 * device_sm_count()));
+    }
     f->max_refine = 4;
     f->refine_tol = 1e-12;
     const int r = f->r;

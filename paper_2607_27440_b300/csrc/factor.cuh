@@ -33,9 +33,9 @@ struct klst_factor_s {
 };
 
 namespace klst {
-struct Rot {           // rotation of columns (i, i+1): [c s; -conj(s) c] applied from the left to rows
-    double2 s;
-    double c;
+struct Rot {           // rotation [c s; -conj(s) c] of rows/columns (i, i+1), in double-float
+    float4 s;          // complex s: {re.hi, re.lo, im.hi, im.lo}
+    float2 c;          // real c: {hi, lo}
     int i;
     int pad;
 };
@@ -57,7 +57,7 @@ struct SchurArgs {
     double tol;
     int conv;          // 0: est <= tol |mu|, 1: est <= tol |mu|^2
     Status* st;
-    double2* Vh;       // m x m: Householder vectors (column c, rows c+1..m-1)
+    float4* Vh;        // m x m: Householder vectors (column c, rows c+1..m-1), double-float
     double* tau;       // m: Householder scalars (0 = no reflection)
     Rot* log;          // Givens rotations of the QR sweeps and the reordering, in order
     int log_cap;

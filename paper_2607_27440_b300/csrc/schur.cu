@@ -1,5 +1,5 @@
-// Small dense float64 step of the Krylov-Schur restart (Sec. 4.1: restarted Arnoldi with a
-// filter that keeps the wanted Ritz values), on the device:
+// Small dense step of the Krylov-Schur restart (Sec. 4.1: restarted Arnoldi with a filter that
+// keeps the wanted Ritz values), on the device:
 //   S_m = Q T Q^H: Householder reduction to Hessenberg form, then shifted QR with Givens
 //   rotations to the complex Schur form; T is reordered so the Ritz values mu with the largest
 //   |mu| (eigenvalues omega = sigma + 1/mu nearest the shift) lead; Ritz residual estimates
@@ -8,52 +8,13 @@
 // runs the QR sweeps and the reordering on a packed copy of the Hessenberg matrix in shared
 // memory and logs every rotation; k_schur_q rebuilds Q from the reflectors and the rotation log,
 // one thread per row; k_schur_post forms the Ritz estimates, the selection and the truncation.
+#include "df64.cuh"
 #include "factor.cuh"
 
 namespace klst {
 
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 __device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }
-
-// 1/sqrt(x) by Newton-Raphson on y^-2 = x from a float32 seed: each step y <- y (3 - x y^2) / 2
-// doubles the correct bits (24 -> 48 -> full float64).  Only for x well inside the float32 range.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y;
-}
-
-// Givens rotation [c s; -conj(s) c] [f; g] = [r; 0] with real c (the LAPACK zlartg convention).
-// c = |f| / r and s = f conj(g) / (|f| r), r = sqrt(|f|^2 + |g|^2), formed with two reciprocal
-// square roots; magnitudes outside [1e-120, 1e120] take the hypot form below.
-__device__ void givens_ref(double2 f, double2 g, double& c, double2& s);
-__device__ void givens(double2 f, double2 g, double& c, double2& s) {
-    const double af2 = abs2(f), ag2 = abs2(g);
-    if (ag2 == 0.0) { c = 1.0; s = mk(0, 0); return; }
-    const double r2 = af2 + ag2;
-    if (af2 < 1e-240 || r2 > 1e240 || ag2 < 1e-240) { givens_ref(f, g, c, s); return; }
-    const double ir = rsqrt_nr(r2), iaf = rsqrt_nr(af2);
-    c = af2 * iaf * ir;
-    s = (iaf * ir) * (f * conj(g));
-}
-
-__device__ void givens_ref(double2 f, double2 g, double& c, double2& s) {
-    const double af = cabs(f), ag = cabs(g);
-    if (ag == 0.0) { c = 1.0; s = mk(0, 0); return; }
-    if (af == 0.0) { c = 0.0; s = (1.0 / ag) * conj(g); return; }
-    const double nr = hypot(af, ag);
-    c = af / nr;
-    const double2 ph = (1.0 / af) * f;  // f / |f|
-    s = (1.0 / nr) * (ph * conj(g));
-}
-
-// x' = c x + s y ; y' = c y - conj(s) x
-__device__ __forceinline__ void rot(double2& x, double2& y, double c, double2 s) {
-    const double2 t = c * x + s * y;
-    y = c * y - conj(s) * x;
-    x = t;
-}
 
 __device__ double block_sum1(double v, double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -95,7 +56,7 @@ __global__ void __launch_bounds__(256) k_schur_house(SchurArgs a) {
         for (int i = tid; i < len; i += nt) {
             const double2 vi = (i == 0) ? x0 - bet : HH(c + 1 + i, c);
             v[i] = vi;
-            a.Vh[(size_t)c * m + c + 1 + i] = vi;
+            cdf_store(&a.Vh[(size_t)c * m + c + 1 + i], cdf_from(vi));
         }
         __syncthreads();
         const double tau = 1.0 / (alpha * (alpha + ax0));  // 2 / ||v||^2
@@ -125,54 +86,100 @@ __global__ void __launch_bounds__(256) k_schur_house(SchurArgs a) {
 }
 
 // ---------------------------------------------------------------- 2. QR sweeps + reordering
-// Packed upper-Hessenberg storage: column j keeps rows 0..j+1 at offset j(j+3)/2.
+// The sweeps run in double-float (df64) arithmetic on the float32 pipes: a complex rotation costs
+// about 150 float32 instructions against 12 float64 ones, and the B300 issues float64 at about
+// 1/64 of the float32 rate, so both the rotation chains and the serial scans stay off the float64
+// unit.  Packed upper-Hessenberg storage: column j keeps rows 0..j+1 at offset j(j+3)/2.
 __device__ __forceinline__ int pk(int i, int j) { return j * (j + 3) / 2 + i; }
 
+// df64 unit roundoff is 2^-48; a subdiagonal entry below 2^-47 (|h_{l-1,l-1}| + |h_{l,l}|) is
+// set to zero (the float64 form of the test uses the float64 ulp)
+constexpr float kDeflEps = 7.105427357601002e-15f;  // 2^-47
+
+// Givens rotation [c s; -conj(s) c] [f; g] = [r; 0] with real c = |f| / r and
+// s = f conj(g) / (|f| r), r = sqrt(|f|^2 + |g|^2) (the LAPACK zlartg convention), in df64.
+// f and g are first scaled by one power of two (exact) so the squares stay in float32 range.
+__device__ void givens_df(cdf f, cdf g, df& c, cdf& s) {
+    const float mg = fmaxf(fabsf(g.re.hi), fabsf(g.im.hi));
+    const float mf = fmaxf(fabsf(f.re.hi), fabsf(f.im.hi));
+    if (mg == 0.f || mg < 1e-30f * mf) { c = df{1.f, 0.f}; s = cdf_zero(); return; }
+    int e;
+    frexpf(fmaxf(mf, mg), &e);
+    e = max(-120, min(120, e));
+    const float sc = ldexpf(1.f, -e);
+    f = cdf_scale(f, sc);
+    g = cdf_scale(g, sc);
+    const df ag2 = cdf_abs2(g), af2 = cdf_abs2(f);
+    if (af2.hi < 1e-30f) {  // |f| < 1e-15 |g|: c = 0 and s = conj(g) / |g|
+        c = df{0.f, 0.f};
+        s = cdf_rmul(df_rsqrt(ag2), cdf_conj(g));
+        return;
+    }
+    const df ir = df_rsqrt(df_add(af2, ag2)), iaf = df_rsqrt(af2);
+    c = df_mul(df_mul(af2, iaf), ir);
+    s = cdf_rmul(df_mul(iaf, ir), cdf_mul(f, cdf_conj(g)));
+}
+
 __global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
-    extern __shared__ double2 sH[];
-    const int m = a.m, tid = threadIdx.x, nt = blockDim.x;
-    __shared__ double rc[192];
-    __shared__ double2 rs[192];
-    __shared__ double s_c;
-    __shared__ double2 s_s, s_mu;
+    extern __shared__ float4 sT[];
+    const int m = a.m, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ float2 rc[192];
+    __shared__ float4 rs[192];
+    __shared__ float2 s_c;
+    __shared__ float4 s_s, s_mu;
     __shared__ int s_lo, s_q, s_fail, s_cnt;
+#define TT(i, j) sT[pk(i, j)]
+#define LD(i, j) cdf_unpack(sT[pk(i, j)])
     for (int j = 0; j < m; ++j)
-        for (int i = tid; i <= min(j + 1, m - 1); i += nt) sH[pk(i, j)] = a.H[(size_t)j * m + i];
+        for (int i = tid; i <= min(j + 1, m - 1); i += nt) TT(i, j) = cdf_pack(cdf_from(a.H[(size_t)j * m + i]));
     if (tid == 0) { s_fail = 0; s_cnt = 0; }
     __syncthreads();
-#define TT(i, j) sH[pk(i, j)]
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     int hi = m - 1, its = 0, total = 0;
     const int max_total = 30 * m;
     while (hi > 0) {
-        if (tid == 0) {
-            int l = hi;
-            for (; l > 0; --l) {
-                const double sub = cabs1(TT(l, l - 1));
-                double sc = cabs1(TT(l - 1, l - 1)) + cabs1(TT(l, l));
-                if (sc == 0.0) sc = 1.0;
-                if (sub <= 2.220446049250313e-16 * sc || sub < 1e-300) { TT(l, l - 1) = mk(0, 0); break; }
-            }
-            s_lo = l;
-            if (l < hi) {
-                const double2 aa = TT(hi - 1, hi - 1), bb = TT(hi - 1, hi), cc = TT(hi, hi - 1), dd = TT(hi, hi);
-                double2 mu;
-                if (its > 0 && its % 11 == 0) {
-                    mu = dd + mk(0.75 * cabs1(cc), 0.0);  // exceptional shift
-                } else {
-                    // Wilkinson shift: eigenvalue of the trailing 2x2 nearer dd
-                    const double2 hd = 0.5 * (aa - dd);
-                    const double2 disc = hd * hd + bb * cc;
-                    const double r = cabs(disc);
-                    const double sr = sqrt(0.5 * (r + fabs(disc.x)));
-                    double2 sq;
-                    if (sr == 0.0) sq = mk(0, 0);
-                    else if (disc.x >= 0) sq = mk(sr, disc.y / (2.0 * sr));
-                    else sq = mk(fabs(disc.y) / (2.0 * sr), disc.y >= 0 ? sr : -sr);
-                    const double2 m1 = 0.5 * (aa + dd) + sq, m2 = 0.5 * (aa + dd) - sq;
-                    mu = cabs(m1 - dd) < cabs(m2 - dd) ? m1 : m2;
+        if (wid == 0) {
+            // deflation: the largest l in [1, hi] whose subdiagonal entry is negligible (0 if none),
+            // 32 candidates per ballot
+            int l = 0;
+            for (int base = hi; base >= 1; base -= 32) {
+                const int ll = base - lane;
+                bool neg = false;
+                if (ll >= 1) {
+                    const float sub = cdf_abs1f(LD(ll, ll - 1));
+                    float sc = cdf_abs1f(LD(ll - 1, ll - 1)) + cdf_abs1f(LD(ll, ll));
+                    if (sc == 0.f) sc = 1.f;
+                    neg = sub <= kDeflEps * sc;
                 }
-                s_mu = mu;
-                if (s_cnt + (hi - l) > a.log_cap) s_fail = 2;
+                const unsigned b = __ballot_sync(0xffffffffu, neg);
+                if (b) { l = base - (__ffs(b) - 1); break; }
+            }
+            if (lane == 0) {
+                if (l >= 1) TT(l, l - 1) = zero4;
+                s_lo = l;
+                if (l < hi) {
+                    // shift from the trailing 2x2 block, in float64 (once per sweep)
+                    const double2 aa = cdf_to(LD(hi - 1, hi - 1)), bb = cdf_to(LD(hi - 1, hi)),
+                                  cc = cdf_to(LD(hi, hi - 1)), dd = cdf_to(LD(hi, hi));
+                    double2 mu;
+                    if (its > 0 && its % 11 == 0) {
+                        mu = dd + mk(0.75 * cabs1(cc), 0.0);  // exceptional shift
+                    } else {
+                        // Wilkinson shift: eigenvalue of the trailing 2x2 nearer dd
+                        const double2 hd = 0.5 * (aa - dd);
+                        const double2 disc = hd * hd + bb * cc;
+                        const double r = cabs(disc);
+                        const double sr = sqrt(0.5 * (r + fabs(disc.x)));
+                        double2 sq;
+                        if (sr == 0.0) sq = mk(0, 0);
+                        else if (disc.x >= 0) sq = mk(sr, disc.y / (2.0 * sr));
+                        else sq = mk(fabs(disc.y) / (2.0 * sr), disc.y >= 0 ? sr : -sr);
+                        const double2 m1 = 0.5 * (aa + dd) + sq, m2 = 0.5 * (aa + dd) - sq;
+                        mu = cabs(m1 - dd) < cabs(m2 - dd) ? m1 : m2;
+                    }
+                    s_mu = cdf_pack(cdf_from(mu));
+                    if (s_cnt + (hi - l) > a.log_cap) s_fail = 2;
+                }
             }
         }
         __syncthreads();
@@ -180,23 +187,35 @@ __global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
         if (lo == hi) { hi -= 1; its = 0; __syncthreads(); continue; }
         if (s_fail || ++total > max_total) { if (tid == 0) s_fail = s_fail ? s_fail : 1; break; }
         ++its;
-        const double2 mu = s_mu;
-        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = TT(i, i) - mu;
+        const cdf mu = cdf_unpack(s_mu);
+        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = cdf_pack(cdf_sub(LD(i, i), mu));
         __syncthreads();
-        if (tid == 0) givens(TT(lo, lo), TT(lo + 1, lo), rc[lo], rs[lo]);
+        if (tid == 0) {
+            df c;
+            cdf sv;
+            givens_df(LD(lo, lo), LD(lo + 1, lo), c, sv);
+            rc[lo] = df_pack(c);
+            rs[lo] = cdf_pack(sv);
+        }
         __syncthreads();
         // left sweep: rotation i on rows i, i+1 (columns i..m-1); the thread holding column i+1
         // forms rotation i+1 from its freshly rotated diagonal entry
         for (int i = lo; i < hi; ++i) {
-            const double c = rc[i];
-            const double2 s = rs[i];
             const int col = i + tid;
             if (col < m) {
-                double2 x = TT(i, col), y = TT(i + 1, col);
-                rot(x, y, c, s);
-                TT(i, col) = x;
-                TT(i + 1, col) = (col == i) ? mk(0, 0) : y;
-                if (col == i + 1 && i + 1 < hi) givens(y, TT(i + 2, i + 1), rc[i + 1], rs[i + 1]);
+                const df c = df_unpack(rc[i]);
+                const cdf sv = cdf_unpack(rs[i]);
+                cdf x = LD(i, col), y = LD(i + 1, col);
+                cdf_rot(x, y, c, sv);
+                TT(i, col) = cdf_pack(x);
+                TT(i + 1, col) = (col == i) ? zero4 : cdf_pack(y);
+                if (col == i + 1 && i + 1 < hi) {
+                    df c2;
+                    cdf s2;
+                    givens_df(y, LD(i + 2, i + 1), c2, s2);
+                    rc[i + 1] = df_pack(c2);
+                    rs[i + 1] = cdf_pack(s2);
+                }
             }
             __syncthreads();
         }
@@ -204,17 +223,17 @@ __global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
         for (int r = tid; r <= hi; r += nt) {
             const int i0 = max(lo, r - 1);
             if (i0 >= hi) continue;
-            double2 x = TT(r, i0);
+            cdf x = LD(r, i0);
             for (int i = i0; i < hi; ++i) {
-                double2 y = TT(r, i + 1);
-                rot(x, y, rc[i], conj(rs[i]));
-                TT(r, i) = x;
+                cdf y = LD(r, i + 1);
+                cdf_rot(x, y, df_unpack(rc[i]), cdf_conj(cdf_unpack(rs[i])));
+                TT(r, i) = cdf_pack(x);
                 x = y;
             }
-            TT(r, hi) = x;
+            TT(r, hi) = cdf_pack(x);
         }
         __syncthreads();
-        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = TT(i, i) + mu;
+        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = cdf_pack(cdf_add(LD(i, i), mu));
         const int base = s_cnt;
         for (int t = tid; t < hi - lo; t += nt) {
             Rot g;
@@ -230,47 +249,57 @@ __global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
         if (tid == 0) { atomicOr(&a.st->flags, ST_NOCONV_QR); *a.nconv = -1; *a.log_count = 0; }
         return;
     }
-    for (int j = tid; j + 1 < m; j += nt) TT(j + 1, j) = mk(0, 0);
+    for (int j = tid; j + 1 < m; j += nt) TT(j + 1, j) = zero4;
     __syncthreads();
-    // reorder: bring the keep Ritz values of largest |mu| to the front by adjacent swaps
+    // reorder: bring the keep Ritz values of largest |mu| to the front by adjacent swaps; the
+    // maximum is found by warp 0 on |T_ii|^2 in df64 (ties resolve to the lower index)
     for (int p = 0; p < a.keep; ++p) {
-        if (tid == 0) {
+        if (wid == 0) {
+            df bv = df{-1.f, 0.f};
             int q = p;
-            double bv = cabs(TT(p, p));
-            for (int i = p + 1; i < m; ++i) {
-                const double vv = cabs(TT(i, i));
-                if (vv > bv) { bv = vv; q = i; }
+            for (int i = p + lane; i < m; i += 32) {
+                const df v = cdf_abs2(LD(i, i));
+                if (v.hi > bv.hi || (v.hi == bv.hi && v.lo > bv.lo)) { bv = v; q = i; }
             }
-            s_q = q;
-            if (s_cnt + (q - p) > a.log_cap) { s_fail = 2; s_q = p; }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, bv.hi, o), ol = __shfl_xor_sync(0xffffffffu, bv.lo, o);
+                const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+                if (oh > bv.hi || (oh == bv.hi && (ol > bv.lo || (ol == bv.lo && oq < q)))) { bv = df{oh, ol}; q = oq; }
+            }
+            if (lane == 0) {
+                s_q = q;
+                if (s_cnt + (q - p) > a.log_cap) { s_fail = 2; s_q = p; }
+            }
         }
         __syncthreads();
         const int q = s_q;
         for (int i = q - 1; i >= p; --i) {
             if (tid == 0) {
-                double c; double2 s;
-                givens(TT(i, i + 1), TT(i + 1, i + 1) - TT(i, i), c, s);
-                s_c = c; s_s = s;
+                df c;
+                cdf sv;
+                givens_df(LD(i, i + 1), cdf_sub(LD(i + 1, i + 1), LD(i, i)), c, sv);
+                s_c = df_pack(c);
+                s_s = cdf_pack(sv);
                 Rot g;
-                g.s = s; g.c = c; g.i = i; g.pad = 0;
+                g.s = s_s; g.c = s_c; g.i = i; g.pad = 0;
                 a.log[s_cnt] = g;
                 s_cnt = s_cnt + 1;
             }
             __syncthreads();
-            const double c = s_c;
-            const double2 s = s_s, sc = conj(s);
-            const double2 t11 = TT(i, i), t22 = TT(i + 1, i + 1);
+            const df c = df_unpack(s_c);
+            const cdf sv = cdf_unpack(s_s), sc = cdf_conj(sv);
+            const float4 t11 = TT(i, i), t22 = TT(i + 1, i + 1);
             for (int idx = tid; idx < (m - i - 2) + i; idx += nt) {
                 if (idx < m - i - 2) {
                     const int col = i + 2 + idx;
-                    double2 x = TT(i, col), y = TT(i + 1, col);
-                    rot(x, y, c, s);
-                    TT(i, col) = x; TT(i + 1, col) = y;
+                    cdf x = LD(i, col), y = LD(i + 1, col);
+                    cdf_rot(x, y, c, sv);
+                    TT(i, col) = cdf_pack(x); TT(i + 1, col) = cdf_pack(y);
                 } else {
                     const int row = idx - (m - i - 2);
-                    double2 x = TT(row, i), y = TT(row, i + 1);
-                    rot(x, y, c, sc);
-                    TT(row, i) = x; TT(row, i + 1) = y;
+                    cdf x = LD(row, i), y = LD(row, i + 1);
+                    cdf_rot(x, y, c, sc);
+                    TT(row, i) = cdf_pack(x); TT(row, i + 1) = cdf_pack(y);
                 }
             }
             __syncthreads();
@@ -282,53 +311,64 @@ __global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
         if (tid == 0) { atomicOr(&a.st->flags, ST_NOCONV_QR); *a.nconv = -1; *a.log_count = 0; }
         return;
     }
-    // write T (upper triangular) back to global
+    // write T (upper triangular) back to global in float64
     for (int idx = tid; idx < m * m; idx += nt) {
         const int i = idx % m, j = idx / m;
-        a.H[idx] = (i <= j) ? TT(i, j) : mk(0, 0);
+        a.H[idx] = (i <= j) ? cdf_to(LD(i, j)) : mk(0, 0);
     }
     if (tid == 0) *a.log_count = s_cnt;
+#undef LD
 #undef TT
 }
 
 // ---------------------------------------------------------------- 3. Schur vectors
 // Row r of Q = e_r^T H_0 H_1 ... H_{m-3} G_1^H G_2^H ...: the reflectors, then every logged
-// rotation in order.  One thread per row; the row lives in shared memory (column-major over
-// the block's rows, so the 32 threads hit distinct banks).
+// rotation in order, in df64.  One thread per row; the row lives in shared memory (column-major
+// over the block's rows, so the 32 threads hit distinct banks).
 __global__ void __launch_bounds__(32) k_schur_q(SchurArgs a) {
-    extern __shared__ double2 q[];  // [m][32]
+    extern __shared__ float4 q4[];  // [m][32]
     const int m = a.m, t = threadIdx.x, r = blockIdx.x * 32 + t;
-    for (int col = 0; col < m; ++col) q[col * 32 + t] = mk(col == r ? 1.0 : 0.0, 0.0);
+    for (int col = 0; col < m; ++col) q4[col * 32 + t] = make_float4(col == r ? 1.f : 0.f, 0.f, 0.f, 0.f);
     for (int c = 0; c + 2 < m; ++c) {
         const double tau = a.tau[c];
         if (tau == 0.0) continue;
-        const double2* vc = a.Vh + (size_t)c * m;
-        double2 g = mk(0, 0);
-        for (int i = c + 1; i < m; ++i) cfma(g, q[i * 32 + t], vc[i]);
-        g = tau * g;
-        for (int i = c + 1; i < m; ++i) q[i * 32 + t] = q[i * 32 + t] - g * conj(vc[i]);
+        const float4* vc = a.Vh + (size_t)c * m;
+        // g = tau sum_i q_i v_i, two accumulators
+        cdf g0 = cdf_zero(), g1 = cdf_zero();
+        int i = c + 1;
+        for (; i + 1 < m; i += 2) {
+            cdf_fma(g0, cdf_unpack(q4[i * 32 + t]), cdf_unpack(vc[i]));
+            cdf_fma(g1, cdf_unpack(q4[(i + 1) * 32 + t]), cdf_unpack(vc[i + 1]));
+        }
+        if (i < m) cdf_fma(g0, cdf_unpack(q4[i * 32 + t]), cdf_unpack(vc[i]));
+        const cdf g = cdf_neg(cdf_rmul(df_from(tau), cdf_add(g0, g1)));
+        for (i = c + 1; i < m; ++i) {
+            cdf qi = cdf_unpack(q4[i * 32 + t]);
+            cdf_fma(qi, g, cdf_conj(cdf_unpack(vc[i])));
+            q4[i * 32 + t] = cdf_pack(qi);
+        }
     }
-    // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in a register
+    // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in registers
     const int nrot = *a.log_count;
-    int ci = -1;     // column held in cx
-    double2 cx = mk(0, 0);
+    int ci = -1;
+    cdf cx = cdf_zero();
     for (int k = 0; k < nrot; ++k) {
         const Rot g = a.log[k];
-        double2 x;
+        cdf x;
         if (g.i == ci) x = cx;
         else {
-            if (ci >= 0) q[ci * 32 + t] = cx;
-            x = q[g.i * 32 + t];
+            if (ci >= 0) q4[ci * 32 + t] = cdf_pack(cx);
+            x = cdf_unpack(q4[g.i * 32 + t]);
         }
-        double2 y = q[(g.i + 1) * 32 + t];
-        rot(x, y, g.c, conj(g.s));
-        q[g.i * 32 + t] = x;
+        cdf y = cdf_unpack(q4[(g.i + 1) * 32 + t]);
+        cdf_rot(x, y, df_unpack(g.c), cdf_conj(cdf_unpack(g.s)));
+        q4[g.i * 32 + t] = cdf_pack(x);
         ci = g.i + 1;
         cx = y;
     }
-    if (ci >= 0) q[ci * 32 + t] = cx;
+    if (ci >= 0) q4[ci * 32 + t] = cdf_pack(cx);
     if (r < m)
-        for (int col = 0; col < m; ++col) a.Q[(size_t)col * m + r] = q[col * 32 + t];
+        for (int col = 0; col < m; ++col) a.Q[(size_t)col * m + r] = cdf_to(cdf_unpack(q4[col * 32 + t]));
 }
 
 // ---------------------------------------------------------------- 4. Ritz pairs, selection, truncation

@@ -57,6 +57,10 @@ EXPORTS = {
     "klst_status_string": (ctypes.c_char_p, [c_int32]),
     "klst_last_error": (ctypes.c_char_p, []),
     "klst_launch_count": (ctypes.c_ulonglong, []),
+    "klst_prof_enable": (None, [c_int32]),
+    "klst_prof_reset": (None, []),
+    "klst_prof_entry": (c_int32, [c_int32, ctypes.c_char_p, c_int32, ctypes.POINTER(c_double),
+                                  ctypes.POINTER(c_int64)]),
     "klst_build_pencil": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, ctypes.POINTER(c_void_p)]),
     "klst_pencil_destroy": (None, [c_void_p]),
     "klst_pencil_dims": (c_int32, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int32),
@@ -84,6 +88,28 @@ EXPORTS = {
                                     ctypes.POINTER(c_int64)]),
     "klst_server_destroy": (None, [c_void_p]),
 }
+
+
+def prof_enable(on=True):
+    """Record CUDA events around each named kernel group on its launching stream."""
+    load().klst_prof_enable(1 if on else 0)
+
+
+def prof_reset():
+    load().klst_prof_reset()
+
+
+def prof_read():
+    """{group: (total_ms, calls)} accumulated since the last prof_reset (waits for the events)."""
+    lib = load()
+    out = {}
+    count = lib.klst_prof_entry(-1, None, 0, None, None)
+    buf = ctypes.create_string_buffer(64)
+    for i in range(count):
+        ms, calls = c_double(0), c_int64(0)
+        lib.klst_prof_entry(i, buf, 64, ctypes.byref(ms), ctypes.byref(calls))
+        out[buf.value.decode()] = (ms.value, calls.value)
+    return out
 
 
 def lib_path():
