@@ -160,23 +160,25 @@ def kernel_rooflines(groups, spec, es, info_list, steps, peaks):
                 by = 8 * F + vec_bytes
                 e.update(bound="hbm", unit="GB/s", algorithmic=f"{by:.4g} B/launch", achieved=by / avg_s / 1e9,
                          peak=hbm)
-        elif name in ("orth_pass1", "orth_pass2"):
-            # classical Gram-Schmidt against j+1 basis vectors reads them twice (dots, update)
-            # per pass; the DGKS second pass repeats it when triggered
+        elif name.startswith("orth"):
+            # Gram-Schmidt against the j+1 basis vectors of step j: every kernel but the scale
+            # reads them once (the second update only when the DGKS test reorthogonalises)
             js = []
+            keep = es.keep or (es.nev + (es.ncv - es.nev) // 2)
             for info in info_list:
-                js += list(range(0, es.ncv))
-                keep = es.keep or (es.nev + (es.ncv - es.nev) // 2)
-                js += list(range(keep, es.ncv)) * info["restarts"]
-            passes = 1.0
-            if name == "orth_pass1":
-                # in the df64 path the group holds both passes
-                nsteps = max(len(js), 1)
-                reo = sum(i.get("reorths", 0) for i in info_list)
-                passes = 1.0 + reo / nsteps if groups.get("orth_pass2") is None else 1.0
-            by = sum(2 * (j + 1) * n * 16 * passes + 3 * n * 16 for j in js)
-            e.update(bound="hbm", unit="GB/s", algorithmic="sum over steps of 2 (j+1) n x 16 B per pass",
-                     achieved=by / (ms / 1e3) / 1e9, peak=hbm)
+                js += list(range(0, es.ncv)) + list(range(keep, es.ncv)) * info["restarts"]
+            nsteps = max(len(js), 1)
+            reo = min(1.0, sum(i.get("reorths", 0) for i in info_list) / nsteps)
+            if name == "orth_scale":
+                by, what = 3 * n * 16 * nsteps, "3 n x 16 B per step (read w, write the df64 and float64 columns)"
+            else:
+                # reads of V per step: df64 path: dots + update, second dots, gated second update;
+                # float64 path: dots + update per pass, the second pass gated
+                per = {"orth1_df": 2.0, "orth2_dots_df": 1.0, "orth2_update_df": reo,
+                       "orth_pass1": 2.0, "orth_pass2": 2.0 * reo}.get(name, 1.0)
+                by = sum(per * (j + 1) * n * 16 for j in js)
+                what = f"sum over steps of (j+1) n x 16 B x {per:.3g}"
+            e.update(bound="hbm", unit="GB/s", algorithmic=what, achieved=by / (ms / 1e3) / 1e9, peak=hbm)
         elif name == "rotate":
             by = (es.ncv * n + (es.keep or es.nev + (es.ncv - es.nev) // 2) * n) * 16
             e.update(bound="hbm", unit="GB/s", algorithmic=f"{by:.4g} B/launch (read V, write V Q)",

@@ -203,14 +203,15 @@ __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ V, i
 // The Krylov basis is stored as complex df64 (float4) and the Gram-Schmidt projections, updates
 // and basis rotations run in df64 arithmetic on the float32 pipes (see df64.cuh).
 
-// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]; with_self adds column ncols = |w|^2.
-// Each warp takes two columns at a time and keeps two accumulators per column (rows lane + 64 u
-// and lane + 32 + 64 u), so four independent loads and multiply-add chains are in flight.
+// Gram-Schmidt in df64, three kernels per pass: chunked dots with per-chunk partials, a reduction
+// that also takes the DGKS decision, and the update.
+// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i] (df64) and, in column ncols,
+// |w|^2 of the chunk.  Each warp takes two columns at a time and keeps two accumulators per
+// column (rows lane + 64 u and lane + 32 + 64 u), so four independent loads and multiply-add
+// chains are in flight.
 __global__ void __launch_bounds__(256) k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols,
                                                  const double2* __restrict__ w, int64_t n, int chunk,
-                                                 double2* __restrict__ part, int ldp, int with_self,
-                                                 const int* __restrict__ gate) {
-    if (gate && *gate == 0) return;
+                                                 float4* __restrict__ part, int ldp) {
     extern __shared__ float4 swf[];
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
@@ -239,31 +240,28 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4* __restrict__ V, i
         a0 = cdf_warp_sum(cdf_add(a0, a1));
         b0 = cdf_warp_sum(cdf_add(b0, b1));
         if (lane == 0) {
-            part[(size_t)blockIdx.x * ldp + col] = cdf_to(a0);
-            if (two) part[(size_t)blockIdx.x * ldp + col + 1] = cdf_to(b0);
+            part[(size_t)blockIdx.x * ldp + col] = cdf_pack(a0);
+            if (two) part[(size_t)blockIdx.x * ldp + col + 1] = cdf_pack(b0);
         }
     }
-    if (with_self && wid == 0) {  // |w|^2 of the chunk in float64
-        double s2 = 0.0;
-        for (int i = lane; i < len; i += 32) s2 += abs2(w[r0 + i]);
-        s2 = warp_sum(s2);
-        if (lane == 0) part[(size_t)blockIdx.x * ldp + ncols] = mk(s2, 0.0);
+    if (wid == nw - 1) {  // |w|^2 of the chunk
+        df s2 = df{0.f, 0.f};
+        for (int i = lane; i < len; i += 32) s2 = df_add(s2, cdf_abs2(cdf_load(swf + i)));
+        for (int o = 16; o > 0; o >>= 1) s2 = df_add(s2, df_shfl_xor(s2, o));
+        if (lane == 0) part[(size_t)blockIdx.x * ldp + ncols] = make_float4(s2.hi, s2.lo, 0.f, 0.f);
     }
 }
 
-// w -= V h (ncols columns, df64 accumulation); per-block partials of |w|^2.  Two accumulators
-// (even and odd columns) halve the dependent chain per row and keep two loads in flight.
+// w -= V h (ncols columns, df64 accumulation).  Two accumulators (even and odd columns) halve
+// the dependent chain per row and keep two loads in flight.
 __global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V, int64_t ldv, int ncols,
-                                                   const double2* __restrict__ h, double2* __restrict__ w, int64_t n,
-                                                   double* __restrict__ npart, const int* __restrict__ gate) {
-    if (gate && *gate == 0) return;
+                                                   const double2* __restrict__ h, double2* __restrict__ w, int64_t n) {
     extern __shared__ float4 shf[];
     for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
         const double2 hv = h[i];
         cdf_store(&shf[i], cdf_from(mk(-hv.x, -hv.y)));
     }
     __syncthreads();
-    double nrm = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         cdf acc0 = cdf_from(w[i]), acc1 = cdf_zero();
         int c = 0;
@@ -273,20 +271,119 @@ __global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V,
             cdf_fma(acc1, cdf_unpack(x1), cdf_load(shf + c + 1));
         }
         if (c < ncols) cdf_fma(acc0, cdf_load(V + c * ldv + i), cdf_load(shf + c));
-        const double2 out = cdf_to(cdf_add(acc0, acc1));
-        w[i] = out;
-        nrm += abs2(out);
+        w[i] = cdf_to(cdf_add(acc0, acc1));
     }
-    if (npart) {
-        nrm = warp_sum(nrm);
-        __shared__ double red[32];
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+}
+
+// h[c] = sum over CTAs of part[cta][c] for c < nc (one warp per column, df64, fixed order);
+// column nc holds |w|^2: stored in nrm[which].  With second = 1 this is the reorthogonalisation
+// pass: the DGKS test (reorthogonalise when ||w'||^2 < ||w||^2 / 2) sets *gate.  h2 is written
+// whether or not the gate opens; the consumers read it only when it does.
+__global__ void k_orth_reduce_df(const float4* __restrict__ part, int nparts, int nc, int ldp, double2* __restrict__ h,
+                                 double* __restrict__ nrm, int second, int* __restrict__ gate, int* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (col > nc) return;
+    cdf a0 = cdf_zero(), a1 = cdf_zero();
+    int b = lane;
+    for (; b + 32 < nparts; b += 64) {
+        a0 = cdf_add(a0, cdf_unpack(part[(size_t)b * ldp + col]));
+        a1 = cdf_add(a1, cdf_unpack(part[(size_t)(b + 32) * ldp + col]));
+    }
+    if (b < nparts) a0 = cdf_add(a0, cdf_unpack(part[(size_t)b * ldp + col]));
+    const cdf a = cdf_warp_sum(cdf_add(a0, a1));
+    if (lane != 0) return;
+    if (col < nc) {
+        h[col] = cdf_to(a);
+        return;
+    }
+    const double nw2 = df_to(a.re);
+    nrm[second] = nw2;
+    if (second) {
+        const int g = nw2 < 0.5 * nrm[0] ? 1 : 0;
+        *gate = g;
+        if (g) atomicAdd(count, 1);
+    }
+}
+
+// Second projection w'' = w' - V h2 (only when the gate is open), then the last CTA to finish
+// completes Arnoldi column j: S[0..j, j] = h1 (+ h2), S[j+1, j] = beta = ||w||, breakdown test.
+__global__ void __launch_bounds__(256) k_update2_finish_df(const float4* __restrict__ V, int64_t ldv, int nc,
+                                                           const double2* __restrict__ h2, double2* __restrict__ w,
+                                                           int64_t n, double* __restrict__ npart,
+                                                           unsigned* __restrict__ counter, const int* __restrict__ gate,
+                                                           const double2* __restrict__ h1, const double* __restrict__ nrm,
+                                                           int j, double2* __restrict__ S, int lds,
+                                                           double* __restrict__ beta_out, Status* st) {
+    extern __shared__ float4 shf2[];
+    __shared__ double red[32];
+    __shared__ bool last;
+    const int g = *gate;
+    if (g) {
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const double2 hv = h2[i];
+            cdf_store(&shf2[i], cdf_from(mk(-hv.x, -hv.y)));
+        }
+        __syncthreads();
+        double nr = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            cdf acc0 = cdf_from(w[i]), acc1 = cdf_zero();
+            int c = 0;
+            for (; c + 1 < nc; c += 2) {
+                const float4 x0 = V[c * ldv + i], x1 = V[(c + 1) * ldv + i];
+                cdf_fma(acc0, cdf_unpack(x0), cdf_load(shf2 + c));
+                cdf_fma(acc1, cdf_unpack(x1), cdf_load(shf2 + c + 1));
+            }
+            if (c < nc) cdf_fma(acc0, cdf_load(V + c * ldv + i), cdf_load(shf2 + c));
+            const double2 out = cdf_to(cdf_add(acc0, acc1));
+            w[i] = out;
+            nr += abs2(out);
+        }
+        nr = warp_sum(nr);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nr;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0;
             for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
             npart[blockIdx.x] = s;
         }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double beta2 = 0.0;
+    if (g) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(npart + b);
+        s = warp_sum(s);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) beta2 += red[q];
+    } else {
+        beta2 = nrm[1];
+    }
+    double hn = 0.0;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 hv = g ? h1[i] + h2[i] : h1[i];
+        S[(size_t)j * lds + i] = hv;
+        hn += abs2(hv);
+    }
+    hn = warp_sum(hn);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double hs = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) hs += red[q];
+        const double beta = sqrt(beta2);
+        if (!(beta > 1e-13 * sqrt(hs))) atomicOr(&st->flags, ST_BREAKDOWN);
+        S[(size_t)j * lds + j + 1] = mk(beta, 0.0);
+        *beta_out = beta;
+        *counter = 0u;
     }
 }
 
@@ -363,9 +460,12 @@ struct EigsWork {
     double2 *mw = nullptr, *mp = nullptr;
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
+    float4* opart = nullptr;      // df64 Gram-Schmidt: per-chunk partial dots [nchunks][m + 2]
+    double* onrm = nullptr;       // ||w||^2, ||w'||^2
+    unsigned* ocnt = nullptr;     // last-CTA counter of k_update2_finish_df
     std::vector<cudaEvent_t> evs;
     void release(cudaStream_t st) {
-        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, wbuf, vcur, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv};
+        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, wbuf, vcur, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv, opart, onrm, ocnt};
         for (void* p : b) dfree(p, st);
         for (auto& ev : evs) cudaEventDestroy(ev);
         evs.clear();
@@ -467,6 +567,14 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         vcur = W.vcur;
     }
     auto V4 = [&](double2* p0) { return reinterpret_cast<float4*>(p0); };
+    const int ldp = m + 2;
+    if (dfm) {
+        if ((e = dmalloc((void**)&W.opart, sizeof(float4) * (size_t)nchunks * ldp, s)) != cudaSuccess ||
+            (e = dmalloc((void**)&W.onrm, sizeof(double) * 4, s)) != cudaSuccess ||
+            (e = dmalloc((void**)&W.ocnt, sizeof(unsigned) * 4, s)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+        KLST_CK(cudaMemsetAsync(W.ocnt, 0, sizeof(unsigned) * 4, s));
+    }
     // start: v0 (given or seeded), V[:,0] = T v0 / ||T v0|| (range of T: no B-null components)
     double2* v0 = Valt;
     if (o->v0) KLST_CK(cudaMemcpyAsync(v0, o->v0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
@@ -500,23 +608,30 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             ++applies;
             const int nc = j + 1;
             // classical Gram-Schmidt, then a second pass only when the DGKS test asks for it
-            prof_begin("orth_pass1", s);
             if (dfm) {
-                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr); klst::note_launch();
-                k_dots_reduce<<<(nc + 1 + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr); klst::note_launch();
-                k_update_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h, w, n, W.npart, nullptr); klst::note_launch();
-                k_reorth_decide<<<1, 256, 0, s>>>(W.npart, nblk, W.h + nc, W.gate, W.reorth); klst::note_launch();
-                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.dpart, m + 1, 0, W.gate); klst::note_launch();
-                k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0, W.gate); klst::note_launch();
-                k_update_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h + (m + 1), w, n, W.npart2, W.gate); klst::note_launch();
-                k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1, W.gate); klst::note_launch();
-                k_finish_col<<<1, 256, 0, s>>>(W.npart, W.npart2, W.gate, nblk, W.h, j, W.S, lds, W.beta, f->status); klst::note_launch();
+                // df64 basis: dots, reduce, update, dots, reduce (+ DGKS), update (+ column), scale
+                const int nred = (nc + 1 + 7) / 8;
+                prof_begin("orth1_df", s);
+                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.opart, ldp); klst::note_launch();
+                k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h, W.onrm, 0, nullptr, nullptr); klst::note_launch();
+                k_update_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h, w, n); klst::note_launch();
+                prof_end("orth1_df", s);
+                prof_begin("orth2_dots_df", s);
+                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.opart, ldp); klst::note_launch();
+                k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h + (m + 1), W.onrm, 1, W.gate, W.reorth); klst::note_launch();
+                prof_end("orth2_dots_df", s);
+                prof_begin("orth2_update_df", s);
+                k_update2_finish_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h + (m + 1), w, n, W.npart2, W.ocnt, W.gate,
+                                                                W.h, W.onrm, j, W.S, lds, W.beta, f->status); klst::note_launch();
+                prof_end("orth2_update_df", s);
+                prof_begin("orth_scale", s);
                 k_scale_df<<<nblk, 256, 0, s>>>(w, n, W.beta, V4(V) + (int64_t)(j + 1) * n, vcur); klst::note_launch();
-                prof_end("orth_pass1", s);
+                prof_end("orth_scale", s);
                 cudaEventRecord(evs[3 * j + 2], s);
                 KLST_CK_LAUNCH();
                 continue;
             }
+            prof_begin("orth_pass1", s);
             k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr); klst::note_launch();
             k_dots_reduce<<<(nc + 1 + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr); klst::note_launch();
             k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, W.npart, nullptr); klst::note_launch();
