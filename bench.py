@@ -120,6 +120,17 @@ FP32_LANE_OPS_PEAK_T = 148 * 128 * 2.032e9 / 1e12   # 38.5 T lane instructions/s
 # float32 instructions of one complex double-float multiply-add (4 real df64 FMAs x 15, see df64.cuh)
 DF64_OPS_PER_CMAC = 60
 
+# DRAM bytes (read + write) per launch group from one ncu capture of the current kernels at C3
+# (profiles/c3_df64_block_solve_and_gram_schmidt_kernels.md: Arnoldi step j = 100, nc = 101),
+# with the algorithmic bytes of the same launches; an entry must be dropped when its kernels change.
+NCU_TRAFFIC_C3 = {
+    "solve_pass1_df64": (301.4e6 + 5.7e6, 288e6 + 4.5e6, "k_solve_pass1"),
+    "solve_pass2_df64": (301.4e6 + 6.4e6, 288e6 + 9.0e6, "k_solve_pass2"),
+    "orth1_df": (337.3e6 + 4.6e6 + 0.7e6 + 337.3e6 + 4.8e6, 2 * 454e6 + 3 * 4.5e6,
+                 "k_dots_df + k_orth_reduce_df + k_update_df at j = 100"),
+    "orth2_dots_df": (337.3e6 + 4.2e6 + 0.7e6, 454e6 + 4.5e6, "k_dots_df + k_orth_reduce_df at j = 100"),
+}
+
 # path name -> (factor precision, Krylov-basis arithmetic)
 PATHS = {
     "df64": ("DF64", "ARITH_DF64"),   # K^-1 and the Krylov basis in double-float (float32 pipes)
@@ -185,6 +196,9 @@ def kernel_rooflines(groups, spec, es, info_list, steps, peaks):
                      achieved=by / avg_s / 1e9, peak=hbm)
         if "peak" in e:
             e["frac"] = e["achieved"] / e["peak"]
+        if spec.n == 281088 and name in NCU_TRAFFIC_C3:
+            t, alg, what = NCU_TRAFFIC_C3[name]
+            e["ncu_traffic"] = {"bytes": t, "algorithmic_bytes": alg, "ratio": t / alg, "kernels": what}
         out[name] = e
     return out
 
@@ -321,8 +335,12 @@ def run_ours(args):
     roof = None
     if top:
         t = modelled[top]
+        tr = t.get("ncu_traffic")
         roof = {"kernel": top, "bound": t["bound"], "achieved": t["achieved"], "peak": t["peak"], "unit": t["unit"],
-                "frac": t["frac"], "traffic": None, "algorithmic": t["algorithmic"],
+                "frac": t["frac"], "traffic": tr["bytes"] if tr else None,
+                "traffic_note": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {tr['kernels']}; "
+                                 f"{tr['ratio']:.2f} x the algorithmic bytes of the same launches") if tr else None,
+                "algorithmic": t["algorithmic"],
                 "share_of_step": t["total_ms_per_step"] / (dev_ms / args.steps),
                 "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if t["bound"] == "hbm" and src == "measured"
                                 else "derived from unit counts and the 2,032 MHz maximum clock" if t["bound"] == "alu"

@@ -18,10 +18,39 @@ int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t l
                     const int* done, int df_arith);
 int pencil_rows_blocks(klst_pencil p);
 
+// z_g += K_k^{-1}[j, :] s0, z_h += K_k^{-1}[j, :] s1 for thread row j (Kk points at column 0 of row
+// j in the transposed storage, stride nx).  The loads of the next four entries are issued before
+// the multiply-adds of the current four, so eight loads per thread are in flight.
+template <typename C>
+__device__ __forceinline__ void block_gemv2(const C* __restrict__ Kk, int nx, const C* s0, const C* s1, C& zg, C& zh) {
+    C ka[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ka[u] = (u < nx) ? Kk[(size_t)u * nx] : czero<C>();
+    int m = 0;
+    for (; m + 4 <= nx; m += 4) {
+        C kb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) kb[u] = (m + 4 + u < nx) ? Kk[(size_t)(m + 4 + u) * nx] : czero<C>();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            cfma(zg, ka[u], s0[m + u]);
+            cfma(zh, ka[u], s1[m + u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ka[u] = kb[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+        if (m + u < nx) {
+            cfma(zg, ka[u], s0[m + u]);
+            cfma(zh, ka[u], s1[m + u]);
+        }
+}
+
 // Pass 1: for each k in the block's group, z_{c,k} = K_k^{-1} b_{c,k} and accumulate
 // t_a(j) += sum_c w^c_a(j,k) z_{c,k}(j); tpart[(rhs*ngroups + g)*r + a*nx + j].
 template <typename C>
-__global__ void k_solve_pass1(int nx, int nxi, const C* __restrict__ KinvT, const double* __restrict__ w,
+__global__ void __launch_bounds__(256, 4) k_solve_pass1(int nx, int nxi, const C* __restrict__ KinvT, const double* __restrict__ w,
                               const double* __restrict__ xi_x, const double2* __restrict__ b, int64_t ldb, int mask,
                               int ngroups, int kpg, double2* __restrict__ tpart, const int* __restrict__ done) {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -44,16 +73,8 @@ __global__ void k_solve_pass1(int nx, int nxi, const C* __restrict__ KinvT, cons
         }
         __syncthreads();
         if (valid) {
-            const C* Kk = KinvT + (size_t)k * nx * nx + j;
-            const C* s0 = sb + (kk * 2 + 0) * NXP;
-            const C* s1 = sb + (kk * 2 + 1) * NXP;
             C zg = czero<C>(), zh = czero<C>();
-#pragma unroll 4
-            for (int m = 0; m < nx; ++m) {
-                const C a = Kk[(size_t)m * nx];
-                cfma(zg, a, s0[m]);
-                cfma(zh, a, s1[m]);
-            }
+            block_gemv2<C>(KinvT + (size_t)k * nx * nx + j, nx, sb + (kk * 2 + 0) * NXP, sb + (kk * 2 + 1) * NXP, zg, zh);
             const double2 dg = to_d(zg), dh = to_d(zh);
             const double* wk = w + (size_t)k * 8 * nx + j;
 #pragma unroll
@@ -98,7 +119,7 @@ __global__ void k_cinv_gemv(int r, const double2* __restrict__ Cinv, const doubl
 
 // Pass 2: y_{c,k} (+)= K_k^{-1} (b_{c,k} + sum_a G^c_a(.,k) s_a(.)).
 template <typename C>
-__global__ void k_solve_pass2(int nx, int nxi, const C* __restrict__ KinvT, const double* __restrict__ G,
+__global__ void __launch_bounds__(256, 4) k_solve_pass2(int nx, int nxi, const C* __restrict__ KinvT, const double* __restrict__ G,
                               const double* __restrict__ xi_x, const double2* __restrict__ b, int64_t ldb, int mask,
                               const double2* __restrict__ sv, double2* __restrict__ y, int accumulate,
                               const int* __restrict__ done) {
@@ -131,16 +152,8 @@ __global__ void k_solve_pass2(int nx, int nxi, const C* __restrict__ KinvT, cons
         }
         __syncthreads();
         if (valid) {
-            const C* Kk = KinvT + (size_t)k * nx * nx + j;
-            const C* s0 = sb + (kk * 2 + 0) * NXP;
-            const C* s1 = sb + (kk * 2 + 1) * NXP;
             C zg = czero<C>(), zh = czero<C>();
-#pragma unroll 4
-            for (int m = 0; m < nx; ++m) {
-                const C a = Kk[(size_t)m * nx];
-                cfma(zg, a, s0[m]);
-                cfma(zh, a, s1[m]);
-            }
+            block_gemv2<C>(KinvT + (size_t)k * nx * nx + j, nx, sb + (kk * 2 + 0) * NXP, sb + (kk * 2 + 1) * NXP, zg, zh);
             const size_t ig = (size_t)k * nx + j, ih = ((size_t)nxi + k) * nx + j;
             if (accumulate) {
                 yr[ig] = yr[ig] + to_d(zg);

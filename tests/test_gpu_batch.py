@@ -27,22 +27,22 @@ SMALL = [
 NEV, NCV = 6, 20
 
 
-def _alone(klst, spec, sigma, prec, seed):
+def _alone(klst, spec, sigma, prec, seed, arith=0):
     P = klst.Pencil(spec)
     F = P.factor(sigma, precision=prec)
-    om, _, res, info = F.eigs(NEV, NCV, tol=1e-11, conv=klst.CONV_RESID, seed=seed)
+    om, _, res, info = F.eigs(NEV, NCV, tol=1e-11, conv=klst.CONV_RESID, seed=seed, arith=arith)
     return om, res
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-def test_batch_equals_alone_and_oracle(klst, prec):
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (2, 1)], ids=["fp64", "mixed", "df64"])
+def test_batch_equals_alone_and_oracle(klst, prec, arith):
     specs = [s for s, _ in SMALL]
     sig = [z for _, z in SMALL]
     om, res, st, infos = klst.batch_eigs(specs, sig, NEV, NCV, precision=prec, nworkers=4, tol=1e-11,
-                                         conv=klst.CONV_RESID, seed=100)
+                                         conv=klst.CONV_RESID, seed=100, arith=arith)
     assert np.all(st == 0), st
     for i, (spec, z) in enumerate(SMALL):
-        o1, r1 = _alone(klst, spec, z, prec, 100 + i)
+        o1, r1 = _alone(klst, spec, z, prec, 100 + i, arith)
         assert np.array_equal(o1, om[i]) and np.array_equal(r1, res[i]), i
         assert np.max(res[i]) <= 1e-10
     for i in (0, 3, 5):

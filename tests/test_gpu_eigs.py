@@ -64,7 +64,8 @@ def test_c1_against_golden(klst, prec, arith):
     assert np.all(np.diff(np.abs(om - es.sigma)) >= -1e-12)
 
 
-@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (1, 1), (2, 1)], ids=["fp64", "mixed", "mixed-df64", "df64"])
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (0, 1), (1, 1), (2, 1)],
+                         ids=["fp64", "mixed", "fp64-df64basis", "mixed-df64", "df64"])
 def test_c2_against_golden(klst, prec, arith):
     spec, es = wl.c2()
     ref, kap, _ = read_golden("c2_eigs.txt")
@@ -78,6 +79,35 @@ def test_c2_against_golden(klst, prec, arith):
     assert np.max(res) <= 1e-10
     r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
     assert np.max(r) <= 1e-10
+
+
+def test_c3_full_size_checked_by_oracle_operator(klst):
+    """The bench's configuration at full size (n = 281,088; df64 factors and basis, keep 60,
+    KLST_CONV_RESID 2e-11).  No oracle eigensolve fits at this size, so every returned eigenpair is
+    checked with the oracle's own matrix-free float64 A and B (||A q - omega B q|| <= 1e-10,
+    ||q|| = 1), and the eigenvalues are compared with the all-float64 GPU path (1e-9 relative)."""
+    spec, es = wl.c3()
+    v0 = to_dev(wl.start_vector(spec.n, es.seed))
+    P = klst.Pencil(spec)
+    out = {}
+    for prec, arith in ((2, 1), (0, 0)):
+        F = P.factor(es.sigma, precision=prec)
+        om, vec, res, info = F.eigs(es.nev, es.ncv, tol=2e-11, conv=klst.CONV_RESID, keep=es.keep, v0=v0,
+                                    vectors=(prec == 2), arith=arith)
+        assert info["status"] == 0 and len(om) == es.nev
+        out[prec] = (om, vec, res)
+        F.close()
+    om, vec, res = out[2]
+    assert np.max(res) <= 1e-10
+    d = gas.pencil_data(spec.as_dict())
+    V = to_host(vec)
+    r = eig.residuals(spec.as_dict(), d, om, V.T)
+    assert np.max(r) <= 1e-10, np.max(r)
+    # both residuals sit near the float64 floor (~1e-12 here), so they agree in absolute terms only
+    assert np.max(np.abs(r - res)) <= 1e-11
+    om64 = out[0][0]
+    perm = eig.match(om64, om)
+    assert np.max(np.abs(om[perm] - om64) / np.abs(om64)) <= 1e-9
 
 
 def test_no_restarts_reports_noconv(klst):
