@@ -206,42 +206,47 @@ __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ V, i
 // Gram-Schmidt in df64, three kernels per pass: chunked dots with per-chunk partials, a reduction
 // that also takes the DGKS decision, and the update.
 // part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i] (df64) and, in column ncols,
-// |w|^2 of the chunk.  Each warp takes two columns at a time and keeps two accumulators per
-// column (rows lane + 64 u and lane + 32 + 64 u), so four independent loads and multiply-add
-// chains are in flight.
-__global__ void __launch_bounds__(256) k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols,
-                                                 const double2* __restrict__ w, int64_t n, int chunk,
-                                                 float4* __restrict__ part, int ldp) {
+// |w|^2 of the chunk.
+__global__ void __launch_bounds__(256, 4) k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols,
+                                                    const double2* __restrict__ w, int64_t n, int chunk,
+                                                    float4* __restrict__ part, int ldp) {
     extern __shared__ float4 swf[];
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
     for (int i = threadIdx.x; i < len; i += blockDim.x) cdf_store(&swf[i], cdf_from(w[r0 + i]));
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int col = 2 * wid; col < ncols; col += 2 * nw) {
-        const bool two = col + 1 < ncols;
-        const float4* v0 = V + col * ldv + r0;
-        const float4* v1 = two ? v0 + ldv : v0;
-        cdf a0 = cdf_zero(), a1 = cdf_zero(), b0 = cdf_zero(), b1 = cdf_zero();
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // four columns per warp pass, rows lane + 32 u; two rows per iteration: eight loads in flight
+    for (int col = 4 * wid; col < ncols; col += 4 * nw) {
+        const int nq = min(4, ncols - col);
+        const float4* vc = V + col * ldv + r0;
+        cdf a[4] = {cdf_zero(), cdf_zero(), cdf_zero(), cdf_zero()};
         int i = lane;
         for (; i + 32 < len; i += 64) {
-            const float4 x0 = v0[i], x1 = v0[i + 32], y0 = v1[i], y1 = v1[i + 32];
+            float4 x0[4], x1[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                x0[q] = (q < nq) ? vc[q * ldv + i] : z4;
+                x1[q] = (q < nq) ? vc[q * ldv + i + 32] : z4;
+            }
             const cdf w0 = cdf_load(swf + i), w1 = cdf_load(swf + i + 32);
-            cdf_fma_conj(a0, cdf_unpack(x0), w0);
-            cdf_fma_conj(a1, cdf_unpack(x1), w1);
-            cdf_fma_conj(b0, cdf_unpack(y0), w0);
-            cdf_fma_conj(b1, cdf_unpack(y1), w1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cdf_fma_conj(a[q], cdf_unpack(x0[q]), w0);
+                cdf_fma_conj(a[q], cdf_unpack(x1[q]), w1);
+            }
         }
         if (i < len) {
             const cdf w0 = cdf_load(swf + i);
-            cdf_fma_conj(a0, cdf_load(v0 + i), w0);
-            cdf_fma_conj(b0, cdf_load(v1 + i), w0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nq) cdf_fma_conj(a[q], cdf_load(vc + q * ldv + i), w0);
         }
-        a0 = cdf_warp_sum(cdf_add(a0, a1));
-        b0 = cdf_warp_sum(cdf_add(b0, b1));
-        if (lane == 0) {
-            part[(size_t)blockIdx.x * ldp + col] = cdf_pack(a0);
-            if (two) part[(size_t)blockIdx.x * ldp + col + 1] = cdf_pack(b0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const cdf t = cdf_warp_sum(a[q]);
+            if (lane == 0 && q < nq) part[(size_t)blockIdx.x * ldp + col + q] = cdf_pack(t);
         }
     }
     if (wid == nw - 1) {  // |w|^2 of the chunk
@@ -250,6 +255,34 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4* __restrict__ V, i
         for (int o = 16; o > 0; o >>= 1) s2 = df_add(s2, df_shfl_xor(s2, o));
         if (lane == 0) part[(size_t)blockIdx.x * ldp + ncols] = make_float4(s2.hi, s2.lo, 0.f, 0.f);
     }
+}
+
+// acc := w_i + sum_c V[i, c] nh[c] (nh = -h in df64 shared memory) for one row i.  The next four
+// basis entries are loaded before the multiply-adds of the current four (two accumulators, even
+// and odd columns), so eight loads per thread are in flight.
+__device__ __forceinline__ double2 update_row_df(const float4* __restrict__ V, int64_t ldv, int ncols,
+                                                 const float4* nh, double2 wi, int64_t i) {
+    cdf acc0 = cdf_from(wi), acc1 = cdf_zero();
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 xa[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xa[u] = (u < ncols) ? V[u * ldv + i] : z4;
+    int c = 0;
+    for (; c + 4 <= ncols; c += 4) {
+        float4 xb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xb[u] = (c + 4 + u < ncols) ? V[(c + 4 + u) * ldv + i] : z4;
+        cdf_fma(acc0, cdf_unpack(xa[0]), cdf_load(nh + c));
+        cdf_fma(acc1, cdf_unpack(xa[1]), cdf_load(nh + c + 1));
+        cdf_fma(acc0, cdf_unpack(xa[2]), cdf_load(nh + c + 2));
+        cdf_fma(acc1, cdf_unpack(xa[3]), cdf_load(nh + c + 3));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xa[u] = xb[u];
+    }
+    if (c < ncols) cdf_fma(acc0, cdf_unpack(xa[0]), cdf_load(nh + c));
+    if (c + 1 < ncols) cdf_fma(acc1, cdf_unpack(xa[1]), cdf_load(nh + c + 1));
+    if (c + 2 < ncols) cdf_fma(acc0, cdf_unpack(xa[2]), cdf_load(nh + c + 2));
+    return cdf_to(cdf_add(acc0, acc1));
 }
 
 // w -= V h (ncols columns, df64 accumulation).  Two accumulators (even and odd columns) halve
@@ -262,17 +295,8 @@ __global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V,
         cdf_store(&shf[i], cdf_from(mk(-hv.x, -hv.y)));
     }
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        cdf acc0 = cdf_from(w[i]), acc1 = cdf_zero();
-        int c = 0;
-        for (; c + 1 < ncols; c += 2) {
-            const float4 x0 = V[c * ldv + i], x1 = V[(c + 1) * ldv + i];
-            cdf_fma(acc0, cdf_unpack(x0), cdf_load(shf + c));
-            cdf_fma(acc1, cdf_unpack(x1), cdf_load(shf + c + 1));
-        }
-        if (c < ncols) cdf_fma(acc0, cdf_load(V + c * ldv + i), cdf_load(shf + c));
-        w[i] = cdf_to(cdf_add(acc0, acc1));
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = update_row_df(V, ldv, ncols, shf, w[i], i);
 }
 
 // h[c] = sum over CTAs of part[cta][c] for c < nc (one warp per column, df64, fixed order);
@@ -327,15 +351,7 @@ __global__ void __launch_bounds__(256) k_update2_finish_df(const float4* __restr
         __syncthreads();
         double nr = 0.0;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            cdf acc0 = cdf_from(w[i]), acc1 = cdf_zero();
-            int c = 0;
-            for (; c + 1 < nc; c += 2) {
-                const float4 x0 = V[c * ldv + i], x1 = V[(c + 1) * ldv + i];
-                cdf_fma(acc0, cdf_unpack(x0), cdf_load(shf2 + c));
-                cdf_fma(acc1, cdf_unpack(x1), cdf_load(shf2 + c + 1));
-            }
-            if (c < nc) cdf_fma(acc0, cdf_load(V + c * ldv + i), cdf_load(shf2 + c));
-            const double2 out = cdf_to(cdf_add(acc0, acc1));
+            const double2 out = update_row_df(V, ldv, nc, shf2, w[i], i);
             w[i] = out;
             nr += abs2(out);
         }
@@ -495,6 +511,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     while ((n + chunk - 1) / chunk > 4 * sms && chunk < 2048) chunk *= 2;
     const int nchunks = (int)((n + chunk - 1) / chunk);
     const int nblk = std::min<int64_t>((n + 255) / 256, 6 * sms);  // 6 resident 256-thread CTAs per SM
+    const int nupd = std::min<int64_t>((n + 255) / 256, 4 * sms);  // df64 updates: 64 registers, 4 CTAs per SM
     const int ng = pencil_work_groups(p);
     if (o->keep != 0 && (o->keep < nev || o->keep >= m)) {
         set_error("invalid keep=%d (need nev <= keep < ncv)", o->keep);
@@ -614,14 +631,14 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
                 prof_begin("orth1_df", s);
                 k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.opart, ldp); klst::note_launch();
                 k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h, W.onrm, 0, nullptr, nullptr); klst::note_launch();
-                k_update_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h, w, n); klst::note_launch();
+                k_update_df<<<nupd, 256, upd_smem, s>>>(V4(V), n, nc, W.h, w, n); klst::note_launch();
                 prof_end("orth1_df", s);
                 prof_begin("orth2_dots_df", s);
                 k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.opart, ldp); klst::note_launch();
                 k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h + (m + 1), W.onrm, 1, W.gate, W.reorth); klst::note_launch();
                 prof_end("orth2_dots_df", s);
                 prof_begin("orth2_update_df", s);
-                k_update2_finish_df<<<nblk, 256, upd_smem, s>>>(V4(V), n, nc, W.h + (m + 1), w, n, W.npart2, W.ocnt, W.gate,
+                k_update2_finish_df<<<nupd, 256, upd_smem, s>>>(V4(V), n, nc, W.h + (m + 1), w, n, W.npart2, W.ocnt, W.gate,
                                                                 W.h, W.onrm, j, W.S, lds, W.beta, f->status); klst::note_launch();
                 prof_end("orth2_update_df", s);
                 prof_begin("orth_scale", s);
