@@ -4,7 +4,7 @@
 //   rotations to the complex Schur form; T is reordered so the Ritz values mu with the largest
 //   |mu| (eigenvalues omega = sigma + 1/mu nearest the shift) lead; Ritz residual estimates
 //   beta |e_m^T Q y_i|; the truncated Krylov-Schur relation for the next cycle.
-// Four kernels: k_schur_house (one CTA) reduces S and keeps the reflectors; k_schur_qr (one CTA)
+// Four kernels: k_schur_house (one CTA, df64) reduces S and keeps the reflectors; k_schur_qr (one CTA)
 // runs the QR sweeps and the reordering on a packed copy of the Hessenberg matrix in shared
 // memory and logs every rotation; k_schur_q rebuilds Q from the reflectors and the rotation log,
 // one thread per row; k_schur_post forms the Ritz estimates, the selection and the truncation.
@@ -16,72 +16,112 @@ namespace klst {
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 __device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }
 
-__device__ double block_sum1(double v, double* red) {
+
+// ---------------------------------------------------------------- 1. Householder reduction
+// df64 sum over the block (fixed xor tree within warps, then warps in order)
+__device__ df block_sum_df(df v, float2* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
     __syncthreads();
-    if (lane == 0) red[wid] = v;
+    if (lane == 0) red[wid] = df_pack(v);
     __syncthreads();
-    double s = 0;
-    for (int i = 0; i < nw; ++i) s += red[i];
+    df s = df{0.f, 0.f};
+    for (int i = 0; i < nw; ++i) s = df_add(s, df_unpack(red[i]));
     __syncthreads();
     return s;
 }
 
-// ---------------------------------------------------------------- 1. Householder reduction
+// Reduction of S (m x m block of the Krylov-Schur matrix) to upper Hessenberg form with
+// Householder reflectors H_c = I - tau_c v_c v_c^H, in df64: H (global, column-major) holds the
+// matrix as float4 df64 values for the QR kernel, v_c is kept in Vh for the Q rebuild.
 __global__ void __launch_bounds__(256) k_schur_house(SchurArgs a) {
     const int m = a.m, tid = threadIdx.x, nt = blockDim.x;
-    double2* H = a.H;
-    __shared__ double2 v[192];
-    __shared__ double red[8];
+    float4* H = reinterpret_cast<float4*>(a.H);
+    __shared__ float4 v[192];
+    __shared__ float2 red[8];
 #define HH(i, j) H[(size_t)(j) * m + (i)]
+#define HL(i, j) cdf_unpack(H[(size_t)(j) * m + (i)])
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int idx = tid; idx < m * m; idx += nt) {
         const int i = idx % m, j = idx / m;
-        H[idx] = a.S[(size_t)j * a.lds + i];
+        H[idx] = cdf_pack(cdf_from(a.S[(size_t)j * a.lds + i]));
     }
     for (int i = tid; i < m; i += nt) a.tau[i] = 0.0;
     if (tid == 0) { *a.nconv = 0; *a.log_count = 0; }  // k_schur_qr sets nconv = -1 on failure
     __syncthreads();
     for (int c = 0; c + 2 < m; ++c) {
-        double tail = 0.0;
-        for (int i = c + 2 + tid; i < m; i += nt) tail += abs2(HH(i, c));
-        tail = block_sum1(tail, red);
-        if (tail == 0.0) continue;
-        const double2 x0 = HH(c + 1, c);
-        const double alpha = sqrt(tail + abs2(x0));
-        const double ax0 = cabs(x0);
-        const double2 ph = ax0 > 0 ? (1.0 / ax0) * x0 : mk(1, 0);
-        const double2 bet = (-alpha) * ph;  // new subdiagonal entry
+        df tail = df{0.f, 0.f};
+        for (int i = c + 2 + tid; i < m; i += nt) tail = df_add(tail, cdf_abs2(HL(i, c)));
+        tail = block_sum_df(tail, red);
+        if (tail.hi == 0.f) continue;
+        const cdf x0 = HL(c + 1, c);
+        const df ax02 = cdf_abs2(x0);
+        const df s2 = df_add(tail, ax02);
+        if (s2.hi < 1e-28f) {  // every subdiagonal entry below 1e-14: negligible, set to zero
+            __syncthreads();
+            for (int i = c + 2 + tid; i < m; i += nt) HH(i, c) = zero4;
+            __syncthreads();
+            continue;
+        }
+        const df alpha = df_mul(s2, df_rsqrt(s2));  // sqrt(|x|^2)
+        df ax0 = df{0.f, 0.f};
+        cdf ph = cdf{df{1.f, 0.f}, df{0.f, 0.f}};
+        if (ax02.hi > 1e-36f) {
+            const df ri = df_rsqrt(ax02);
+            ax0 = df_mul(ax02, ri);
+            ph = cdf_rmul(ri, x0);  // x0 / |x0|
+        }
+        const cdf bet = cdf_neg(cdf_rmul(alpha, ph));  // new subdiagonal entry
         const int len = m - c - 1;
         for (int i = tid; i < len; i += nt) {
-            const double2 vi = (i == 0) ? x0 - bet : HH(c + 1 + i, c);
-            v[i] = vi;
-            cdf_store(&a.Vh[(size_t)c * m + c + 1 + i], cdf_from(vi));
+            const cdf vi = (i == 0) ? cdf_sub(x0, bet) : HL(c + 1 + i, c);
+            v[i] = cdf_pack(vi);
+            a.Vh[(size_t)c * m + c + 1 + i] = cdf_pack(vi);
         }
         __syncthreads();
-        const double tau = 1.0 / (alpha * (alpha + ax0));  // 2 / ||v||^2
-        if (tid == 0) a.tau[c] = tau;
+        const df rt = df_rsqrt(df_mul(alpha, df_add(alpha, ax0)));
+        const df tau = df_mul(rt, rt);  // 2 / ||v||^2 = 1 / (alpha (alpha + |x0|))
+        if (tid == 0) a.tau[c] = df_to(tau);
         // left: H[c+1:, col] -= tau v (v^H H[c+1:, col]) for col > c
         for (int col = c + 1 + tid; col < m; col += nt) {
-            double2 g = mk(0, 0);
-            for (int i = 0; i < len; ++i) cfma_conj(g, v[i], HH(c + 1 + i, col));
-            g = tau * g;
-            for (int i = 0; i < len; ++i) HH(c + 1 + i, col) = HH(c + 1 + i, col) - v[i] * g;
+            cdf g0 = cdf_zero(), g1 = cdf_zero();
+            int i = 0;
+            for (; i + 1 < len; i += 2) {
+                cdf_fma_conj(g0, cdf_unpack(v[i]), HL(c + 1 + i, col));
+                cdf_fma_conj(g1, cdf_unpack(v[i + 1]), HL(c + 2 + i, col));
+            }
+            if (i < len) cdf_fma_conj(g0, cdf_unpack(v[i]), HL(c + 1 + i, col));
+            const cdf g = cdf_neg(cdf_rmul(tau, cdf_add(g0, g1)));
+            for (i = 0; i < len; ++i) {
+                cdf hv = HL(c + 1 + i, col);
+                cdf_fma(hv, cdf_unpack(v[i]), g);
+                HH(c + 1 + i, col) = cdf_pack(hv);
+            }
         }
         if (tid == 0) {
-            HH(c + 1, c) = bet;
-            for (int i = c + 2; i < m; ++i) HH(i, c) = mk(0, 0);
+            HH(c + 1, c) = cdf_pack(bet);
+            for (int i = c + 2; i < m; ++i) HH(i, c) = zero4;
         }
         __syncthreads();
         // right: row[c+1:] -= tau (row[c+1:] v) v^H for every row of H
         for (int row = tid; row < m; row += nt) {
-            double2 g = mk(0, 0);
-            for (int i = 0; i < len; ++i) cfma(g, HH(row, c + 1 + i), v[i]);
-            g = tau * g;
-            for (int i = 0; i < len; ++i) HH(row, c + 1 + i) = HH(row, c + 1 + i) - g * conj(v[i]);
+            cdf g0 = cdf_zero(), g1 = cdf_zero();
+            int i = 0;
+            for (; i + 1 < len; i += 2) {
+                cdf_fma(g0, HL(row, c + 1 + i), cdf_unpack(v[i]));
+                cdf_fma(g1, HL(row, c + 2 + i), cdf_unpack(v[i + 1]));
+            }
+            if (i < len) cdf_fma(g0, HL(row, c + 1 + i), cdf_unpack(v[i]));
+            const cdf g = cdf_neg(cdf_rmul(tau, cdf_add(g0, g1)));
+            for (i = 0; i < len; ++i) {
+                cdf hv = HL(row, c + 1 + i);
+                cdf_fma(hv, g, cdf_conj(cdf_unpack(v[i])));
+                HH(row, c + 1 + i) = cdf_pack(hv);
+            }
         }
         __syncthreads();
     }
+#undef HL
 #undef HH
 }
 
@@ -131,7 +171,7 @@ __global__ void __launch_bounds__(256) k_schur_qr(SchurArgs a) {
 #define TT(i, j) sT[pk(i, j)]
 #define LD(i, j) cdf_unpack(sT[pk(i, j)])
     for (int j = 0; j < m; ++j)
-        for (int i = tid; i <= min(j + 1, m - 1); i += nt) TT(i, j) = cdf_pack(cdf_from(a.H[(size_t)j * m + i]));
+        for (int i = tid; i <= min(j + 1, m - 1); i += nt) TT(i, j) = reinterpret_cast<const float4*>(a.H)[(size_t)j * m + i];
     if (tid == 0) { s_fail = 0; s_cnt = 0; }
     __syncthreads();
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
