@@ -132,6 +132,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Kernel launches issued by this library (process-wide counter, read by klst_launch_count).
 void note_launch();
+void note_launches(unsigned long long k);
+void set_capturing(bool on);
 
 // Stream-ordered device memory (cudaMallocAsync on the device's default pool, whose release
 // threshold is raised once so freed blocks stay cached): allocations on different streams do

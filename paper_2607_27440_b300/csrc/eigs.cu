@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ V, i
 // |w|^2 of the chunk.
 __global__ void __launch_bounds__(256, 4) k_dots_df(const float4* __restrict__ V, int64_t ldv, int ncols,
                                                     const double2* __restrict__ w, int64_t n, int chunk,
-                                                    float4* __restrict__ part, int ldp) {
+                                                    float4* __restrict__ part, int ldp, const int* __restrict__ jdev) {
+    if (jdev) ncols = *jdev + 1;
     extern __shared__ float4 swf[];
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
@@ -288,7 +289,9 @@ __device__ __forceinline__ double2 update_row_df(const float4* __restrict__ V, i
 // w -= V h (ncols columns, df64 accumulation).  Two accumulators (even and odd columns) halve
 // the dependent chain per row and keep two loads in flight.
 __global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V, int64_t ldv, int ncols,
-                                                   const double2* __restrict__ h, double2* __restrict__ w, int64_t n) {
+                                                   const double2* __restrict__ h, double2* __restrict__ w, int64_t n,
+                                                   const int* __restrict__ jdev) {
+    if (jdev) ncols = *jdev + 1;
     extern __shared__ float4 shf[];
     for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
         const double2 hv = h[i];
@@ -304,7 +307,9 @@ __global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V,
 // pass: the DGKS test (reorthogonalise when ||w'||^2 < ||w||^2 / 2) sets *gate.  h2 is written
 // whether or not the gate opens; the consumers read it only when it does.
 __global__ void k_orth_reduce_df(const float4* __restrict__ part, int nparts, int nc, int ldp, double2* __restrict__ h,
-                                 double* __restrict__ nrm, int second, int* __restrict__ gate, int* __restrict__ count) {
+                                 double* __restrict__ nrm, int second, int* __restrict__ gate, int* __restrict__ count,
+                                 const int* __restrict__ jdev) {
+    if (jdev) nc = *jdev + 1;
     const int lane = threadIdx.x & 31;
     const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (col > nc) return;
@@ -338,7 +343,9 @@ __global__ void __launch_bounds__(256) k_update2_finish_df(const float4* __restr
                                                            unsigned* __restrict__ counter, const int* __restrict__ gate,
                                                            const double2* __restrict__ h1, const double* __restrict__ nrm,
                                                            int j, double2* __restrict__ S, int lds,
-                                                           double* __restrict__ beta_out, Status* st) {
+                                                           double* __restrict__ beta_out, Status* st,
+                                                           const int* __restrict__ jdev) {
+    if (jdev) { j = *jdev; nc = j + 1; }
     extern __shared__ float4 shf2[];
     __shared__ double red[32];
     __shared__ bool last;
@@ -403,9 +410,16 @@ __global__ void __launch_bounds__(256) k_update2_finish_df(const float4* __restr
     }
 }
 
+// step index of a captured Arnoldi step: set before a cycle, advanced after each step
+__global__ void k_set_step(int* jdev, int v) { *jdev = v; }
+__global__ void k_step_advance(int* jdev) { *jdev += 1; }
+
 // basis column = w / scale (df64) and the float64 copy that feeds the next apply
+// (with jdev: vcol is the basis and the column is jdev[0] + 1)
 __global__ void k_scale_df(const double2* __restrict__ w, int64_t n, const double* __restrict__ scale,
-                           float4* __restrict__ vcol, double2* __restrict__ vcopy) {
+                           float4* __restrict__ vcol, double2* __restrict__ vcopy, int64_t ldv,
+                           const int* __restrict__ jdev) {
+    if (jdev) vcol += (int64_t)(*jdev + 1) * ldv;
     const double sc = *scale;
     const double inv = sc > 0 ? 1.0 / sc : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -479,10 +493,16 @@ struct EigsWork {
     float4* opart = nullptr;      // df64 Gram-Schmidt: per-chunk partial dots [nchunks][m + 2]
     double* onrm = nullptr;       // ||w||^2, ||w'||^2
     unsigned* ocnt = nullptr;     // last-CTA counter of k_update2_finish_df
+    int* jdev = nullptr;          // graph mode: device step index
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // graph mode: one captured step per basis buffer
+    double2* gV[2] = {nullptr, nullptr};
+    int gkern[2] = {0, 0};
     std::vector<cudaEvent_t> evs;
     void release(cudaStream_t st) {
-        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, wbuf, vcur, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv, opart, onrm, ocnt};
+        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, wbuf, vcur, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv, opart, onrm, ocnt, jdev};
         for (void* p : b) dfree(p, st);
+        for (auto& ge : gexec)
+            if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
         for (auto& ev : evs) cudaEventDestroy(ev);
         evs.clear();
     }
@@ -588,7 +608,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     if (dfm) {
         if ((e = dmalloc((void**)&W.opart, sizeof(float4) * (size_t)nchunks * ldp, s)) != cudaSuccess ||
             (e = dmalloc((void**)&W.onrm, sizeof(double) * 4, s)) != cudaSuccess ||
-            (e = dmalloc((void**)&W.ocnt, sizeof(unsigned) * 4, s)) != cudaSuccess)
+            (e = dmalloc((void**)&W.ocnt, sizeof(unsigned) * 4, s)) != cudaSuccess ||
+            (e = dmalloc((void**)&W.jdev, sizeof(int) * 4, s)) != cudaSuccess)
             return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
         KLST_CK(cudaMemsetAsync(W.ocnt, 0, sizeof(unsigned) * 4, s));
     }
@@ -602,7 +623,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     ++applies;
     k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(w0, n, n, W.npart); klst::note_launch();
     k_colnorm_fin<<<1, 256, 0, s>>>(W.npart, nblk, 1, W.nrm); klst::note_launch();
-    if (dfm) { k_scale_df<<<nblk, 256, 0, s>>>(wbuf, n, W.nrm, V4(V), vcur); klst::note_launch(); }
+    if (dfm) { k_scale_df<<<nblk, 256, 0, s>>>(wbuf, n, W.nrm, V4(V), vcur, n, nullptr); klst::note_launch(); }
     else { k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm); klst::note_launch(); }
     KLST_CK_LAUNCH();
     // phase timers: event pairs recorded per step and read after each restart synchronisation
@@ -614,9 +635,94 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     int k = 0, restarts = 0, nconv = 0;
     const size_t dots_smem = sizeof(double2) * chunk;
     const size_t upd_smem = sizeof(double2) * (m + 1);
+    // df64 Gram-Schmidt of step j (jd != NULL: the kernels read j from device memory, the grids
+    // are sized for j = m - 1)
+    auto df_orth = [&](double2* Vb, int j, const int* jd) -> int {
+        const int nc = j + 1;
+        const int nred = (nc + 1 + 7) / 8;
+        double2* w = wbuf;
+        prof_begin("orth1_df", s);
+        k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(Vb), n, nc, w, n, chunk, W.opart, ldp, jd); klst::note_launch();
+        k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h, W.onrm, 0, nullptr, nullptr, jd); klst::note_launch();
+        k_update_df<<<nupd, 256, upd_smem, s>>>(V4(Vb), n, nc, W.h, w, n, jd); klst::note_launch();
+        prof_end("orth1_df", s);
+        prof_begin("orth2_dots_df", s);
+        k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(Vb), n, nc, w, n, chunk, W.opart, ldp, jd); klst::note_launch();
+        k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h + (m + 1), W.onrm, 1, W.gate, W.reorth, jd); klst::note_launch();
+        prof_end("orth2_dots_df", s);
+        prof_begin("orth2_update_df", s);
+        k_update2_finish_df<<<nupd, 256, upd_smem, s>>>(V4(Vb), n, nc, W.h + (m + 1), w, n, W.npart2, W.ocnt, W.gate,
+                                                        W.h, W.onrm, j, W.S, lds, W.beta, f->status, jd); klst::note_launch();
+        prof_end("orth2_update_df", s);
+        prof_begin("orth_scale", s);
+        k_scale_df<<<nblk, 256, 0, s>>>(w, n, W.beta, jd ? V4(Vb) : V4(Vb) + (int64_t)(j + 1) * n, vcur, n, jd); klst::note_launch();
+        prof_end("orth_scale", s);
+        KLST_CK_LAUNCH();
+        return KLST_OK;
+    };
+    // Graph mode (df64 basis on a capturable stream): one Arnoldi step (apply, Gram-Schmidt, step
+    // advance) is captured once per basis buffer and launched as a single graph per step, which
+    // removes the host cost of its ~11 kernel launches.  Not used on the legacy default stream, on
+    // a stream that is already capturing, or while kernel-group timing is on.
+    bool use_graph = false;
+    if (dfm && !prof_enabled() && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+        const char* ng = getenv("KLST_NO_GRAPH");
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (!(ng && ng[0] == '1') && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+            use_graph = true;
+        cudaGetLastError();
+    }
+    auto capture_step = [&](double2* Vb, cudaGraphExec_t* ge, int* nkern) -> int {
+        cudaGraph_t g = nullptr;
+        cudaError_t e1 = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        set_capturing(true);
+        int rc2 = apply_T(f, vcur, wbuf, 1, s);
+        if (rc2 == KLST_OK) rc2 = df_orth(Vb, m - 1, W.jdev);
+        if (rc2 == KLST_OK) k_step_advance<<<1, 1, 0, s>>>(W.jdev);
+        set_capturing(false);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (rc2 != KLST_OK || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc2 != KLST_OK ? rc2 : cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        int kern = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+        }
+        e2 = cudaGraphInstantiate(ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) { *ge = nullptr; return cuda_fail(e2, "cudaGraphInstantiate", __FILE__, __LINE__); }
+        *nkern = kern;
+        return KLST_OK;
+    };
     bool converged = false;
     for (;;) {
-        for (int j = k; j < m; ++j) {
+        const int jfirst = k;
+        if (use_graph) {
+            // the whole expansion of this cycle: one graph launch per Arnoldi step
+            int slot = (V == W.gV[0]) ? 0 : (V == W.gV[1]) ? 1 : -1;
+            if (slot < 0) {
+                slot = W.gexec[0] ? 1 : 0;
+                if ((rc = capture_step(V, &W.gexec[slot], &W.gkern[slot])) != KLST_OK) return fail(rc);
+                W.gV[slot] = V;
+            }
+            cudaEventRecord(evs[0], s);
+            k_set_step<<<1, 1, 0, s>>>(W.jdev, k); klst::note_launch();
+            for (int j = k; j < m; ++j) {
+                KLST_CK(cudaGraphLaunch(W.gexec[slot], s));
+                klst::note_launches(W.gkern[slot]);
+            }
+            cudaEventRecord(evs[1], s);
+            applies += m - k;
+        }
+        for (int j = use_graph ? m : k; j < m; ++j) {
             double2* vj = dfm ? vcur : V + (int64_t)j * n;
             double2* w = dfm ? wbuf : V + (int64_t)(j + 1) * n;
             cudaEventRecord(evs[3 * j], s);
@@ -626,26 +732,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             const int nc = j + 1;
             // classical Gram-Schmidt, then a second pass only when the DGKS test asks for it
             if (dfm) {
-                // df64 basis: dots, reduce, update, dots, reduce (+ DGKS), update (+ column), scale
-                const int nred = (nc + 1 + 7) / 8;
-                prof_begin("orth1_df", s);
-                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.opart, ldp); klst::note_launch();
-                k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h, W.onrm, 0, nullptr, nullptr); klst::note_launch();
-                k_update_df<<<nupd, 256, upd_smem, s>>>(V4(V), n, nc, W.h, w, n); klst::note_launch();
-                prof_end("orth1_df", s);
-                prof_begin("orth2_dots_df", s);
-                k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(V), n, nc, w, n, chunk, W.opart, ldp); klst::note_launch();
-                k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h + (m + 1), W.onrm, 1, W.gate, W.reorth); klst::note_launch();
-                prof_end("orth2_dots_df", s);
-                prof_begin("orth2_update_df", s);
-                k_update2_finish_df<<<nupd, 256, upd_smem, s>>>(V4(V), n, nc, W.h + (m + 1), w, n, W.npart2, W.ocnt, W.gate,
-                                                                W.h, W.onrm, j, W.S, lds, W.beta, f->status); klst::note_launch();
-                prof_end("orth2_update_df", s);
-                prof_begin("orth_scale", s);
-                k_scale_df<<<nblk, 256, 0, s>>>(w, n, W.beta, V4(V) + (int64_t)(j + 1) * n, vcur); klst::note_launch();
-                prof_end("orth_scale", s);
+                if ((rc = df_orth(V, j, nullptr)) != KLST_OK) return fail(rc);
                 cudaEventRecord(evs[3 * j + 2], s);
-                KLST_CK_LAUNCH();
                 continue;
             }
             prof_begin("orth_pass1", s);
@@ -665,7 +753,6 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             cudaEventRecord(evs[3 * j + 2], s);
             KLST_CK_LAUNCH();
         }
-        const int jfirst = k;
         SchurArgs a;
         a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
         a.Ysel = W.Ysel; a.mu_sel = W.musel; a.est_sel = W.estsel;
@@ -679,7 +766,12 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         KLST_CK(cudaMemcpyAsync(&hconv, W.nconv, sizeof(int), cudaMemcpyDeviceToHost, s));
         KLST_CK(cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s));
         KLST_CK(cudaStreamSynchronize(s));
-        for (int j = jfirst; j < m; ++j) {
+        if (use_graph) {  // graph mode times the whole expansion (apply + orthogonalisation) as t_orth
+            float a1 = 0;
+            cudaEventElapsedTime(&a1, evs[0], evs[1]);
+            t_orth += a1;
+        }
+        for (int j = use_graph ? m : jfirst; j < m; ++j) {
             float a1 = 0, a2 = 0;
             cudaEventElapsedTime(&a1, evs[3 * j], evs[3 * j + 1]);
             cudaEventElapsedTime(&a2, evs[3 * j + 1], evs[3 * j + 2]);

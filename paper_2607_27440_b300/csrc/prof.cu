@@ -17,7 +17,14 @@
 namespace klst {
 
 static std::atomic<unsigned long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// While a thread captures a CUDA graph its launches are recorded, not run: they are counted when
+// the graph is launched (note_launches with the graph's kernel-node count).
+static thread_local bool t_capturing = false;
+void set_capturing(bool on) { t_capturing = on; }
+void note_launch() {
+    if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void note_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 struct ProfRec {
     std::string name;
