@@ -477,6 +477,19 @@ __global__ void k_randn(double2* x, int64_t n, uint64_t seed) {
     }
 }
 
+// Carves 256-byte-aligned arrays out of one allocation: a first pass (base == NULL) only sums
+// the sizes, a second assigns the pointers.
+struct SlabCarver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    void take(T*& p, size_t cnt) {
+        const size_t bytes = (sizeof(T) * cnt + 255) & ~size_t(255);
+        p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += bytes;
+    }
+};
+
 struct EigsWork {
     double2 *Va = nullptr, *Vb = nullptr, *S = nullptr, *H = nullptr, *Q = nullptr, *Yc = nullptr, *mu = nullptr;
     double2 *Ysel = nullptr, *musel = nullptr, *Vh = nullptr;
@@ -498,12 +511,14 @@ struct EigsWork {
     double2* gV[2] = {nullptr, nullptr};
     int gkern[2] = {0, 0};
     std::vector<cudaEvent_t> evs;
+    void* slab = nullptr;         // one allocation holding every array above except X, Z, R
     void release(cudaStream_t st) {
-        void* b[] = {Va, Vb, S, H, Q, Yc, mu, Ysel, musel, estsel, Vh, tau, rlog, rcount, npart2, gate, reorth, wbuf, vcur, h, dpart, X, Z, R, om, mw, mp, est, npart, beta, nrm, nconv, opart, onrm, ocnt, jdev};
+        void* b[] = {slab, X, Z, R};
         for (void* p : b) dfree(p, st);
         for (auto& ge : gexec)
             if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
-        for (auto& ev : evs) cudaEventDestroy(ev);
+        for (auto& ev : evs)
+            if (ev) cudaEventDestroy(ev);
         evs.clear();
     }
 };
@@ -553,38 +568,56 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         f->arith = prev_arith;
         return code;
     };
-#define EALLOC(ptr, cnt)                                                                     \
-    if ((e = dmalloc((void**)&(ptr), sizeof(*(ptr)) * (size_t)(cnt), s)) != cudaSuccess)      \
-        return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
-    EALLOC(W.Va, n * (m + 1));
-    EALLOC(W.Vb, n * (m + 1));
-    EALLOC(W.S, (size_t)lds * m);
-    EALLOC(W.H, (size_t)m * m);
-    EALLOC(W.Q, (size_t)m * m);
-    EALLOC(W.Yc, (size_t)m * m);
-    EALLOC(W.Ysel, (size_t)m * nev);
-    EALLOC(W.mu, m);
-    EALLOC(W.musel, nev);
-    EALLOC(W.est, m);
-    EALLOC(W.estsel, nev);
-    EALLOC(W.Vh, (size_t)m * m);
-    EALLOC(W.tau, m);
+    // the whole workspace is one stream-ordered allocation: concurrent solves on many host
+    // threads otherwise queue on the allocator for dozens of small arrays each
+    const bool dfm = o->arith == KLST_ARITH_DF64;
+    const int ldp = m + 2;
     const int log_cap = 31 * m * m;
-    EALLOC(W.rlog, log_cap);
-    EALLOC(W.rcount, 4);
-    EALLOC(W.npart2, std::max(nblk, 1));
-    EALLOC(W.gate, 4);
-    EALLOC(W.reorth, 4);
-    EALLOC(W.h, 2 * (m + 1));
-    EALLOC(W.dpart, (size_t)nchunks * (m + 1));
-    EALLOC(W.npart, (size_t)std::max(nblk, 1) * std::max(nev, 1) + 64);
-    EALLOC(W.beta, 4);
-    EALLOC(W.nrm, nev + 4);
-    EALLOC(W.nconv, 4);
-    EALLOC(W.om, nev);
-    EALLOC(W.mw, (size_t)4 * p->nx * nev);
-    EALLOC(W.mp, (size_t)4 * p->nx * ng * nev);
-#undef EALLOC
+    {
+        SlabCarver sc;
+        for (int pass = 0; pass < 2; ++pass) {
+            sc.off = 0;
+            sc.take(W.Va, n * (m + 1));
+            sc.take(W.Vb, n * (m + 1));
+            sc.take(W.S, (size_t)lds * m);
+            sc.take(W.H, (size_t)m * m);
+            sc.take(W.Q, (size_t)m * m);
+            sc.take(W.Yc, (size_t)m * m);
+            sc.take(W.Ysel, (size_t)m * nev);
+            sc.take(W.mu, m);
+            sc.take(W.musel, nev);
+            sc.take(W.est, m);
+            sc.take(W.estsel, nev);
+            sc.take(W.Vh, (size_t)m * m);
+            sc.take(W.tau, m);
+            sc.take(W.rlog, log_cap);
+            sc.take(W.rcount, 4);
+            sc.take(W.npart2, std::max(nblk, 1));
+            sc.take(W.gate, 4);
+            sc.take(W.reorth, 4);
+            sc.take(W.h, 2 * (m + 1));
+            sc.take(W.dpart, (size_t)nchunks * (m + 1));
+            sc.take(W.npart, (size_t)std::max(nblk, 1) * std::max(nev, 1) + 64);
+            sc.take(W.beta, 4);
+            sc.take(W.nrm, nev + 4);
+            sc.take(W.nconv, 4);
+            sc.take(W.om, nev);
+            sc.take(W.mw, (size_t)4 * p->nx * nev);
+            sc.take(W.mp, (size_t)4 * p->nx * ng * nev);
+            if (dfm) {
+                sc.take(W.wbuf, n);
+                sc.take(W.vcur, n);
+                sc.take(W.opart, (size_t)nchunks * ldp);
+                sc.take(W.onrm, 4);
+                sc.take(W.ocnt, 4);
+                sc.take(W.jdev, 4);
+            }
+            if (pass == 0) {
+                if ((e = dmalloc(&W.slab, sc.off, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+                sc.base = static_cast<char*>(W.slab);
+            }
+        }
+    }
     KLST_CK(cudaMemsetAsync(W.S, 0, sizeof(double2) * lds * m, s));
     KLST_CK(cudaMemsetAsync(W.reorth, 0, sizeof(int) * 4, s));
     KLST_CK(cudaMemsetAsync(f->status, 0, sizeof(Status), s));
@@ -594,25 +627,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     double2 *V = W.Va, *Valt = W.Vb;
     // df64 mode: the basis is complex df64 (float4, same bytes); the apply works on float64
     // vectors wbuf (output) and vcur (the newest basis vector in float64)
-    const bool dfm = o->arith == KLST_ARITH_DF64;
-    double2 *wbuf = nullptr, *vcur = nullptr;
-    if (dfm) {
-        if ((e = dmalloc((void**)&W.wbuf, sizeof(double2) * n, s)) != cudaSuccess ||
-            (e = dmalloc((void**)&W.vcur, sizeof(double2) * n, s)) != cudaSuccess)
-            return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
-        wbuf = W.wbuf;
-        vcur = W.vcur;
-    }
+    double2* wbuf = W.wbuf;
+    double2* vcur = W.vcur;
     auto V4 = [&](double2* p0) { return reinterpret_cast<float4*>(p0); };
-    const int ldp = m + 2;
-    if (dfm) {
-        if ((e = dmalloc((void**)&W.opart, sizeof(float4) * (size_t)nchunks * ldp, s)) != cudaSuccess ||
-            (e = dmalloc((void**)&W.onrm, sizeof(double) * 4, s)) != cudaSuccess ||
-            (e = dmalloc((void**)&W.ocnt, sizeof(unsigned) * 4, s)) != cudaSuccess ||
-            (e = dmalloc((void**)&W.jdev, sizeof(int) * 4, s)) != cudaSuccess)
-            return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
-        KLST_CK(cudaMemsetAsync(W.ocnt, 0, sizeof(unsigned) * 4, s));
-    }
+    if (dfm) KLST_CK(cudaMemsetAsync(W.ocnt, 0, sizeof(unsigned) * 4, s));
     // start: v0 (given or seeded), V[:,0] = T v0 / ||T v0|| (range of T: no B-null components)
     double2* v0 = Valt;
     if (o->v0) KLST_CK(cudaMemcpyAsync(v0, o->v0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
@@ -626,10 +644,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     if (dfm) { k_scale_df<<<nblk, 256, 0, s>>>(wbuf, n, W.nrm, V4(V), vcur, n, nullptr); klst::note_launch(); }
     else { k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm); klst::note_launch(); }
     KLST_CK_LAUNCH();
-    // phase timers: event pairs recorded per step and read after each restart synchronisation
+    // phase timers: event pairs recorded per step (eager launches) or per cycle (graph mode) and
+    // read after each restart synchronisation; created below once the mode is known
     W.evs.assign(3 * (m + 1) + 4, nullptr);
-    for (auto& ev : W.evs)
-        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__));
     std::vector<cudaEvent_t>& evs = W.evs;
     double t_apply = 0, t_orth = 0, t_restart = 0, t_schur = 0;
     int k = 0, restarts = 0, nconv = 0;
@@ -702,6 +719,11 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         *nkern = kern;
         return KLST_OK;
     };
+    // graph mode times a whole cycle (events 0, 1); eager mode every step; both time the restart
+    for (int i = 0; i < (int)evs.size(); ++i) {
+        if (use_graph && i > 1 && i < 3 * (m + 1)) continue;
+        if ((e = cudaEventCreate(&evs[i])) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__));
+    }
     bool converged = false;
     for (;;) {
         const int jfirst = k;
