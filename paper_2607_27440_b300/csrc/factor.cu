@@ -5,9 +5,12 @@
 // and C^{-1} by Gauss-Jordan over all SMs, one launch per pivot step.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "df64.cuh"
 #include "factor.cuh"
@@ -218,6 +221,162 @@ __global__ void __launch_bounds__(256) k_gj_step(int r, int p, const double2* __
     }
 }
 
+// The same Gauss-Jordan inverse in one launch of one thread-block cluster of NC CTAs, for
+// r <= 384: CTA q keeps rows [q rpc, (q+1) rpc) in shared memory; per pivot the CTAs exchange
+// their column-maximum candidates and read the pivot row and row p through distributed shared
+// memory, with hardware cluster barriers between the phases (no CTA waits on a flag).  Every
+// entry follows the arithmetic of k_gj_step, so the result is identical; the column interchanges
+// are undone as the rows are written out.
+template <int NC>
+__global__ void __launch_bounds__(256) k_gj_cluster(int r, const double2* __restrict__ Cin, double2* __restrict__ Cout,
+                                                    Status* st) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank(), tid = threadIdx.x, nt = blockDim.x;
+    const int rpc = (r + NC - 1) / NC;
+    const int i0 = q * rpc, i1 = min(r, i0 + rpc), nown = max(0, i1 - i0);
+    extern __shared__ __align__(16) unsigned char gsm[];
+    double2* rows = reinterpret_cast<double2*>(gsm);  // [rpc][r]
+    double2* prow = rows + (size_t)rpc * r;           // [r] pivot row
+    double2* rowp = prow + r;                         // [r] row p (moves to the pivot row's slot)
+    double2* fcol = rowp + r;                         // [rpc] multipliers of the own rows
+    __shared__ double cand_v;
+    __shared__ int cand_i;
+    __shared__ double rv[8];
+    __shared__ int ri[8];
+    __shared__ int s_piv;
+    __shared__ int s_perm[512];
+    for (int idx = tid; idx < nown * r; idx += nt) rows[idx] = Cin[(size_t)i0 * r + idx];
+    __syncthreads();
+    for (int p = 0; p < r; ++p) {
+        // this CTA's candidate: the largest |C(i, p)|^2 over its rows i >= p (lowest index on ties)
+        double best = -1;
+        int bi = r;
+        for (int i = max(p, i0) + tid; i < i1; i += nt) {
+            const double v = abs2(rows[(size_t)(i - i0) * r + p]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = rv[0];
+            int ib = ri[0];
+            for (int w = 1; w < (nt >> 5); ++w)
+                if (rv[w] > b || (rv[w] == b && ri[w] < ib)) { b = rv[w]; ib = ri[w]; }
+            cand_v = b;
+            cand_i = ib;
+        }
+        cl.sync();
+        if (tid == 0) {  // every CTA reduces the NC candidates in the same order
+            double b = -1;
+            int ib = r;
+            for (int k = 0; k < NC; ++k) {
+                const double vk = *cl.map_shared_rank(&cand_v, k);
+                const int ik = *cl.map_shared_rank(&cand_i, k);
+                if (vk > b || (vk == b && ik < ib)) { b = vk; ib = ik; }
+            }
+            if (!(b > 0) && q == 0) atomicOr(&st->flags, ST_SINGULAR);
+            s_piv = ib < r ? ib : p;
+            s_perm[p] = s_piv;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        {
+            const double2* rp = cl.map_shared_rank(rows, piv / rpc) + (size_t)(piv % rpc) * r;
+            const double2* rq = cl.map_shared_rank(rows, p / rpc) + (size_t)(p % rpc) * r;
+            for (int c = tid; c < r; c += nt) { prow[c] = rp[c]; rowp[c] = rq[c]; }
+        }
+        cl.sync();  // every CTA holds its copies before any row changes
+        double2 inv = prow[p];
+        if (!(abs2(inv) > 0)) inv.x = 1;
+        inv = cinv(inv);
+        for (int li = tid; li < nown; li += nt) {
+            const int i = i0 + li;
+            fcol[li] = ((i == piv) ? rowp[p] : rows[(size_t)li * r + p]) * inv;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nown * r; idx += nt) {
+            const int li = idx / r, c = idx % r, i = i0 + li;
+            double2 v;
+            if (i == p) v = (c == p) ? inv : prow[c] * inv;
+            else {
+                const double2 sv = (i == piv) ? rowp[c] : rows[idx];
+                const double2 f = fcol[li];
+                v = (c == p) ? -f : sv - f * prow[c];
+            }
+            rows[idx] = v;
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges: out[:, c] = rows[:, map[c]]
+    __shared__ int colmap[512];
+    if (tid == 0) {
+        for (int c = 0; c < r; ++c) colmap[c] = c;
+        for (int p = r - 1; p >= 0; --p) { const int qq = s_perm[p], t = colmap[p]; colmap[p] = colmap[qq]; colmap[qq] = t; }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nown * r; idx += nt) {
+        const int li = idx / r, c = idx % r;
+        Cout[(size_t)(i0 + li) * r + c] = rows[(size_t)li * r + colmap[c]];
+    }
+    cl.sync();  // no CTA leaves while another may still read its rows
+}
+
+template <int NC>
+static size_t gj_cluster_smem(int r) {
+    const int rpc = (r + NC - 1) / NC;
+    return sizeof(double2) * ((size_t)rpc * r + 2 * (size_t)r + rpc);
+}
+
+// Launches k_gj_cluster<NC> if one cluster of that shape fits on the device; returns false (and
+// launches nothing) otherwise.
+template <int NC>
+static bool launch_gj_cluster(int r, const double2* Cin, double2* Cout, Status* st, cudaStream_t s) {
+    static std::mutex mu;
+    static int ok = -1;
+    const size_t smem = gj_cluster_smem<NC>(r);
+    if (smem > 200 * 1024 || r > 512) return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = NC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(NC, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (ok < 0) {
+            ok = 0;
+            if (cudaFuncSetAttribute(k_gj_cluster<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) == cudaSuccess &&
+                (NC <= 8 || cudaFuncSetAttribute(k_gj_cluster<NC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+                cudaLaunchConfig_t probe = cfg;
+                probe.dynamicSmemBytes = 200 * 1024;
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, k_gj_cluster<NC>, &probe) == cudaSuccess && nclusters > 0)
+                    ok = 1;
+            }
+            cudaGetLastError();
+        }
+    }
+    if (!ok) return false;
+    if (cudaLaunchKernelEx(&cfg, k_gj_cluster<NC>, r, Cin, Cout, st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    klst::note_launch();
+    return true;
+}
+
 // Undo the row interchanges as column interchanges (p, perm[p]) for p = r-1..0, as a gather.
 __global__ void __launch_bounds__(256) k_gj_unpermute(int r, const double2* __restrict__ fin, double2* __restrict__ res,
                                                       const int* __restrict__ perm) {
@@ -388,7 +547,14 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     }
     k_cap_reduce<<<std::min(1024, (r * r + 255) / 256), 256, 0, s>>>(r, nsplit, Cp, b0); klst::note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "cap reduce", __FILE__, __LINE__));
-    {
+    // C^{-1}: one cluster launch when r fits the cluster's shared memory (r <= 384), else one
+    // launch per pivot
+    bool cluster_done = false;
+    if (!getenv("KLST_NO_CLUSTER_GJ")) {
+        if (gj_cluster_smem<8>(r) <= 200 * 1024) cluster_done = launch_gj_cluster<8>(r, b0, f->Cinv, f->status, s);
+        else if (gj_cluster_smem<16>(r) <= 200 * 1024) cluster_done = launch_gj_cluster<16>(r, b0, f->Cinv, f->status, s);
+    }
+    if (!cluster_done) {
         const int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
         const size_t smem = sizeof(double2) * 2 * r;
         int* perm = (int*)bar;
@@ -400,9 +566,11 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
                                                                                         (r & 1) ? b0 : b1, perm); klst::note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "capacitance inverse", __FILE__, __LINE__));
     }
-    double2* res = (r & 1) ? b0 : b1;
-    if ((e = cudaMemcpyAsync(f->Cinv, res, sizeof(double2) * (size_t)r * r, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return fail(cuda_fail(e, "copy Cinv", __FILE__, __LINE__));
+    if (!cluster_done) {
+        double2* res = (r & 1) ? b0 : b1;
+        if ((e = cudaMemcpyAsync(f->Cinv, res, sizeof(double2) * (size_t)r * r, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return fail(cuda_fail(e, "copy Cinv", __FILE__, __LINE__));
+    }
     Status hst;
     if ((e = cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)

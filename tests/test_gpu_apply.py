@@ -88,3 +88,23 @@ def test_exactly_singular_block_is_reported(klst):
     with pytest.raises(klst.KlstError) as ei:
         P.factor(complex(nu[3], 0.0))
     assert ei.value.code == klst.KLST_ESINGULAR
+
+
+@pytest.mark.parametrize("nx", [32, 64, 96], ids=["r128", "r256", "r384"])
+def test_capacitance_inverse_cluster_equals_per_pivot(klst, nx, monkeypatch):
+    """C^{-1} by one thread-block-cluster launch (8 CTAs up to r = 256, 16 at r = 384) follows the
+    per-pivot Gauss-Jordan launches operation for operation: the applies agree bit for bit, and
+    the cluster factorisation launches about r fewer kernels."""
+    spec = wl.tiny(nx=nx, qx=6, qy=4, mach=3.0, beta=0.5)
+    x = to_dev(wl.start_vector(spec.n, 7))
+    P = klst.Pencil(spec)
+    lib = klst.load()
+    c0 = lib.klst_launch_count()
+    y1 = to_host(P.factor(0.1j, precision=0).apply(x))
+    c1 = lib.klst_launch_count()
+    monkeypatch.setenv("KLST_NO_CLUSTER_GJ", "1")
+    y2 = to_host(P.factor(0.1j, precision=0).apply(x))
+    c2 = lib.klst_launch_count()
+    r = 4 * nx
+    assert (c2 - c1) - (c1 - c0) >= r - 2, ((c1 - c0), (c2 - c1))
+    assert np.array_equal(y1, y2)
