@@ -123,12 +123,15 @@ DF64_OPS_PER_CMAC = 60
 # DRAM bytes (read + write) per launch group from one ncu capture of the current kernels at C3
 # (profiles/c3_df64_block_solve_and_gram_schmidt_kernels.md: Arnoldi step j = 100, nc = 101),
 # with the algorithmic bytes of the same launches; an entry must be dropped when its kernels change.
+_V101 = 101 * 281088 * 16  # 101 basis columns
+_W = 281088 * 16           # one n-vector
 NCU_TRAFFIC_C3 = {
-    "solve_pass1_df64": (301.4e6 + 5.7e6, 288e6 + 4.5e6, "k_solve_pass1"),
-    "solve_pass2_df64": (301.4e6 + 6.4e6, 288e6 + 9.0e6, "k_solve_pass2"),
-    "orth1_df": (337.3e6 + 4.6e6 + 0.7e6 + 337.3e6 + 4.8e6, 2 * 454e6 + 3 * 4.5e6,
+    "solve_pass1_df64": (301.4e6 + 5.4e6, 288e6 + _W, "k_solve_pass1"),
+    "solve_pass2_df64": (301.4e6 + 6.2e6, 288e6 + 2 * _W, "k_solve_pass2"),
+    "orth1_df": (458.8e6 + 4.8e6 + 0.96e6 + 458.8e6 + 5.8e6, 2 * _V101 + 3 * _W,
                  "k_dots_df + k_orth_reduce_df + k_update_df at j = 100"),
-    "orth2_dots_df": (337.3e6 + 4.2e6 + 0.7e6, 454e6 + 4.5e6, "k_dots_df + k_orth_reduce_df at j = 100"),
+    "orth2_dots_df": (458.8e6 + 4.2e6 + 0.96e6, _V101 + _W, "k_dots_df + k_orth_reduce_df at j = 100"),
+    "orth2_update_df": (458.8e6 + 6.3e6, _V101 + 2 * _W, "k_update2_finish_df at j = 100"),
 }
 
 # path name -> (factor precision, Krylov-basis arithmetic)
