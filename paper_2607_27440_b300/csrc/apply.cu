@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256, 4) k_solve_pass1(int nx, int nxi, const C
     }
 }
 
-// s = C^{-1} t : one warp per row of the row-major capacitance inverse
+// s = C^{-1} t : one warp per row of the row-major capacitance inverse; four accumulators per
+// lane keep four independent loads and multiply-add chains in flight
 __global__ void k_cinv_gemv(int r, const double2* __restrict__ Cinv, const double2* __restrict__ t,
                             double2* __restrict__ sv, const int* __restrict__ done) {
     const int rhs = blockIdx.y;
@@ -108,8 +109,18 @@ __global__ void k_cinv_gemv(int r, const double2* __restrict__ Cinv, const doubl
     if (warp >= r) return;
     const double2* row = Cinv + (size_t)warp * r;
     const double2* tr = t + (size_t)rhs * r;
-    double2 a = mk(0, 0);
-    for (int l = lane; l < r; l += 32) cfma(a, row[l], tr[l]);
+    double2 a0 = mk(0, 0), a1 = mk(0, 0), a2 = mk(0, 0), a3 = mk(0, 0);
+    int l = lane;
+    for (; l + 96 < r; l += 128) {
+        const double2 x0 = row[l], x1 = row[l + 32], x2 = row[l + 64], x3 = row[l + 96];
+        const double2 y0 = tr[l], y1 = tr[l + 32], y2 = tr[l + 64], y3 = tr[l + 96];
+        cfma(a0, x0, y0);
+        cfma(a1, x1, y1);
+        cfma(a2, x2, y2);
+        cfma(a3, x3, y3);
+    }
+    for (; l < r; l += 32) cfma(a0, row[l], tr[l]);
+    double2 a = (a0 + a1) + (a2 + a3);
     for (int o = 16; o > 0; o >>= 1) {
         a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
         a.y += __shfl_xor_sync(0xffffffffu, a.y, o);

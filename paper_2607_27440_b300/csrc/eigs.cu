@@ -306,22 +306,30 @@ __global__ void __launch_bounds__(256) k_update_df(const float4* __restrict__ V,
 // column nc holds |w|^2: stored in nrm[which].  With second = 1 this is the reorthogonalisation
 // pass: the DGKS test (reorthogonalise when ||w'||^2 < ||w||^2 / 2) sets *gate.  h2 is written
 // whether or not the gate opens; the consumers read it only when it does.
-__global__ void k_orth_reduce_df(const float4* __restrict__ part, int nparts, int nc, int ldp, double2* __restrict__ h,
-                                 double* __restrict__ nrm, int second, int* __restrict__ gate, int* __restrict__ count,
-                                 const int* __restrict__ jdev) {
+__global__ void __launch_bounds__(128) k_orth_reduce_df(const float4* __restrict__ part, int nparts, int nc, int ldp,
+                                                        double2* __restrict__ h, double* __restrict__ nrm, int second,
+                                                        int* __restrict__ gate, int* __restrict__ count,
+                                                        const int* __restrict__ jdev) {
+    // one CTA of 4 warps per column: each thread sums partials tid, tid + 128, ... (two
+    // accumulators), then the warps combine in a fixed order
     if (jdev) nc = *jdev + 1;
-    const int lane = threadIdx.x & 31;
-    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int col = blockIdx.x;
     if (col > nc) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     cdf a0 = cdf_zero(), a1 = cdf_zero();
-    int b = lane;
-    for (; b + 32 < nparts; b += 64) {
-        a0 = cdf_add(a0, cdf_unpack(part[(size_t)b * ldp + col]));
-        a1 = cdf_add(a1, cdf_unpack(part[(size_t)(b + 32) * ldp + col]));
+    int b = tid;
+    for (; b + 128 < nparts; b += 256) {
+        const float4 u = part[(size_t)b * ldp + col], v = part[(size_t)(b + 128) * ldp + col];
+        a0 = cdf_add(a0, cdf_unpack(u));
+        a1 = cdf_add(a1, cdf_unpack(v));
     }
     if (b < nparts) a0 = cdf_add(a0, cdf_unpack(part[(size_t)b * ldp + col]));
-    const cdf a = cdf_warp_sum(cdf_add(a0, a1));
-    if (lane != 0) return;
+    const cdf aw = cdf_warp_sum(cdf_add(a0, a1));
+    __shared__ float4 red[4];
+    if (lane == 0) red[wid] = cdf_pack(aw);
+    __syncthreads();
+    if (tid != 0) return;
+    const cdf a = cdf_add(cdf_add(cdf_add(cdf_unpack(red[0]), cdf_unpack(red[1])), cdf_unpack(red[2])), cdf_unpack(red[3]));
     if (col < nc) {
         h[col] = cdf_to(a);
         return;
@@ -420,8 +428,13 @@ __global__ void k_scale_df(const double2* __restrict__ w, int64_t n, const doubl
                            float4* __restrict__ vcol, double2* __restrict__ vcopy, int64_t ldv,
                            const int* __restrict__ jdev) {
     if (jdev) vcol += (int64_t)(*jdev + 1) * ldv;
-    const double sc = *scale;
-    const double inv = sc > 0 ? 1.0 / sc : 0.0;
+    __shared__ double s_inv;  // one float64 division per CTA, not per thread
+    if (threadIdx.x == 0) {
+        const double sc = *scale;
+        s_inv = sc > 0 ? 1.0 / sc : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_inv;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double2 v = mk(w[i].x * inv, w[i].y * inv);
         cdf_store(vcol + i, cdf_from(v));
@@ -656,16 +669,16 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     // are sized for j = m - 1)
     auto df_orth = [&](double2* Vb, int j, const int* jd) -> int {
         const int nc = j + 1;
-        const int nred = (nc + 1 + 7) / 8;
+        const int nred = nc + 1;  // one CTA per column and one for |w|^2
         double2* w = wbuf;
         prof_begin("orth1_df", s);
         k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(Vb), n, nc, w, n, chunk, W.opart, ldp, jd); klst::note_launch();
-        k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h, W.onrm, 0, nullptr, nullptr, jd); klst::note_launch();
+        k_orth_reduce_df<<<nred, 128, 0, s>>>(W.opart, nchunks, nc, ldp, W.h, W.onrm, 0, nullptr, nullptr, jd); klst::note_launch();
         k_update_df<<<nupd, 256, upd_smem, s>>>(V4(Vb), n, nc, W.h, w, n, jd); klst::note_launch();
         prof_end("orth1_df", s);
         prof_begin("orth2_dots_df", s);
         k_dots_df<<<nchunks, 256, dots_smem, s>>>(V4(Vb), n, nc, w, n, chunk, W.opart, ldp, jd); klst::note_launch();
-        k_orth_reduce_df<<<nred, 256, 0, s>>>(W.opart, nchunks, nc, ldp, W.h + (m + 1), W.onrm, 1, W.gate, W.reorth, jd); klst::note_launch();
+        k_orth_reduce_df<<<nred, 128, 0, s>>>(W.opart, nchunks, nc, ldp, W.h + (m + 1), W.onrm, 1, W.gate, W.reorth, jd); klst::note_launch();
         prof_end("orth2_dots_df", s);
         prof_begin("orth2_update_df", s);
         k_update2_finish_df<<<nupd, 256, upd_smem, s>>>(V4(Vb), n, nc, W.h + (m + 1), w, n, W.npart2, W.ocnt, W.gate,

@@ -42,22 +42,27 @@ __global__ void k_moments_partial(int nx, int nxi, const double* __restrict__ w,
 
 // out[rhs*len + i] = sum_g part[(rhs*ngroups + g)*len + i]: one warp per output, lanes over groups in
 // a fixed stride, then a fixed shuffle tree (deterministic, latency-parallel).
-__global__ void k_reduce_groups(int len, int ngroups, const double2* __restrict__ part, double2* __restrict__ out,
-                                const int* done) {
-    const int rhs = blockIdx.y;
+__global__ void __launch_bounds__(128) k_reduce_groups(int len, int ngroups, const double2* __restrict__ part,
+                                                       double2* __restrict__ out, const int* done) {
+    // one CTA of 4 warps per output: each thread sums groups tid, tid + 128, ... (independent
+    // loads, two accumulators), then the 4 warps combine in a fixed order
+    const int rhs = blockIdx.y, i = blockIdx.x;
     if (done && done[rhs]) return;
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= len) return;
-    double sx = 0.0, sy = 0.0;
-    for (int g = lane; g < ngroups; g += 32) {
-        const double2 v = part[((size_t)rhs * ngroups + g) * len + i];
-        sx += v.x;
-        sy += v.y;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const double2* pr = part + (size_t)rhs * ngroups * len + i;
+    double2 a0 = mk(0, 0), a1 = mk(0, 0);
+    int g = tid;
+    for (; g + 128 < ngroups; g += 256) {
+        const double2 u = pr[(size_t)g * len], v = pr[(size_t)(g + 128) * len];
+        a0 = a0 + u;
+        a1 = a1 + v;
     }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) out[(size_t)rhs * len + i] = mk(sx, sy);
+    if (g < ngroups) a0 = a0 + pr[(size_t)g * len];
+    double sx = warp_sum(a0.x + a1.x), sy = warp_sum(a0.y + a1.y);
+    __shared__ double2 red[4];
+    if (lane == 0) red[wid] = mk(sx, sy);
+    __syncthreads();
+    if (tid == 0) out[(size_t)rhs * len + i] = ((red[0] + red[1]) + red[2]) + red[3];
 }
 
 // Rows of (A - omega B) x (mode 0) or the residual b - (A - sigma B) x (mode 1, b masked by B
@@ -168,7 +173,7 @@ __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __rest
 
 void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,
                          cudaStream_t s) {
-    k_reduce_groups<<<dim3((len + 7) / 8, nrhs), 256, 0, s>>>(len, ngroups, part, out, done); klst::note_launch();
+    k_reduce_groups<<<dim3(len, nrhs), 128, 0, s>>>(len, ngroups, part, out, done); klst::note_launch();
 }
 
 int pencil_work_groups(klst_pencil p) {
@@ -195,7 +200,7 @@ int moments_dev(klst_pencil p, const double2* x, int64_t ldx, int nrhs, double2*
     const int kpg = (p->nxi + ngroups - 1) / ngroups;
     dim3 blk(NXP, KB), grd(ngroups, nrhs);
     k_moments_partial<<<grd, blk, sizeof(double2) * 4 * KB * NXP, s>>>(p->nx, p->nxi, p->w, x, ldx, ngroups, kpg, mpart); klst::note_launch();
-    k_reduce_groups<<<dim3((4 * p->nx + 7) / 8, nrhs), 256, 0, s>>>(4 * p->nx, ngroups, mpart, mwork, done); klst::note_launch();
+    k_reduce_groups<<<dim3(4 * p->nx, nrhs), 128, 0, s>>>(4 * p->nx, ngroups, mpart, mwork, done); klst::note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
 }
