@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
+    ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 latency figures")
     ap.add_argument("--serve-rate", type=float, default=5.0, help="Poisson arrival rate of the serving run (1/s)")
     ap.add_argument("--serve-window", type=float, default=15.0, help="arrival window of the serving run (s)")
     return ap.parse_args()
@@ -105,6 +106,21 @@ def workload(name, rank):
     return spec, es, sigma
 
 
+def combine_ranks(dev_ms, e2e_ms, good, e2e_good, ws, device):
+    """Replicas: the job's time is the slowest rank's (max over ranks), its eigenpairs are every
+    rank's (sum over ranks).  One collective per quantity kind, outside the timed region."""
+    if ws <= 1:
+        return dev_ms, e2e_ms, good, e2e_good
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(good), float(e2e_good)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    (dev_ms, e2e_ms), (good, e2e_good) = tmax.tolist(), tsum.tolist()
+    return dev_ms, e2e_ms, good, e2e_good
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -142,8 +158,8 @@ PATHS = {
     "fp64": ("FP64", "ARITH_F64"),    # everything in float64: the plain FP64 GPU path
 }
 PATH_DTYPE = {
-    "df64": "df64 (double-float: K^-1, block solves and Krylov basis on float32 pipes; fp64 capacitance, Schur, residuals)",
-    "mixed": "c64+f64 (complex fp32 K^-1 and block solves, fp64 refinement, Arnoldi, Schur, residuals)",
+    "df64": "df64 (double-float: K^-1, block solves, Krylov basis and Schur sweeps on float32 pipes; fp64 capacitance, residuals)",
+    "mixed": "c64+f64 (complex fp32 K^-1 and block solves, fp64 refinement, Arnoldi, residuals; df64 Schur sweeps)",
     "fp64": "c128 (fp64 throughout)",
 }
 
@@ -284,17 +300,7 @@ def run_ours(args):
         d2h = vec_host.numel() * 16 + om.nbytes + res.nbytes
     barrier()
     e2e_s = time.perf_counter() - t0
-    # max over ranks
-    times = torch.tensor([dev_ms, e2e_s * 1e3, float(good_total), float(e2e_good)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        tmax = times[:2].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = times[2:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        dev_ms, e2e_ms = tmax.tolist()
-        good_total, e2e_good = tsum.tolist()
-    else:
-        e2e_ms = e2e_s * 1e3
+    dev_ms, e2e_ms, good_total, e2e_good = combine_ranks(dev_ms, e2e_s * 1e3, good_total, e2e_good, ws, "cuda")
     # the other paths on the same pencil, and every path's eigenvalues against the float64 path's
     compare, om_fp64 = {}, None
     if not args.no_compare and rank == 0:
@@ -386,6 +392,11 @@ def run_ours(args):
         "compare": compare or None,
         "peaks_source": src,
     }
+    if not args.no_small:
+        try:
+            line["small_configs"] = small_configs(klst)
+        except Exception as ex:  # the headline line must still print
+            line["small_configs"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_batch:
         line["batched"] = batched_sweep(klst, compare=not args.no_compare)
         line["serving"] = serving_run(klst, args.serve_rate, args.serve_window)
@@ -393,6 +404,54 @@ def run_ours(args):
     print(json.dumps(line, default=_jsonable), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def small_configs(klst, reps=100):
+    """C1 and C2, whose factors fit in L2 and whose solves are latency bound: one df64 solve on a
+    side stream (so each Arnoldi step is one CUDA graph launch), and the mean shift-invert apply
+    time over `reps` applies, both timed with CUDA events on that stream."""
+    import torch
+
+    from paper_2607_27440_b300 import workloads as wl
+    lib = klst.load()
+    st = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(st):
+        for name in ("c1", "c2"):
+            spec, es = getattr(wl, name)()
+            P = klst.Pencil(spec, stream=st)
+            F = P.factor(es.sigma, precision=klst.DF64, stream=st)
+            v0 = torch.from_numpy(wl.start_vector(spec.n, es.seed)).to(torch.complex128).to("cuda")
+            kw = dict(tol=CONV_TOL, conv=klst.CONV_RESID, max_restarts=es.max_restarts, v0=v0, check=False,
+                      keep=es.keep, arith=klst.ARITH_DF64, stream=st)
+            F.eigs(es.nev, es.ncv, **kw)  # warm-up
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0 = lib.klst_launch_count()
+            e0.record(st)
+            om, _, res, info = F.eigs(es.nev, es.ncv, **kw)
+            e1.record(st)
+            st.synchronize()
+            launches = int(lib.klst_launch_count() - c0)
+            ms = e0.elapsed_time(e1)
+            good = int(np.sum(res <= RESID_MAX)) if info["status"] in (0, klst.KLST_ENOCONV) else 0
+            x = v0.clone()
+            for _ in range(3):
+                F.apply(x, stream=st)
+            e0.record(st)
+            for _ in range(reps):
+                F.apply(x, stream=st)
+            e1.record(st)
+            st.synchronize()
+            out[name] = {"n": spec.n, "nev": es.nev, "ncv": es.ncv, "solve_ms": ms,
+                         "eigenpairs_per_s": good / (ms / 1e3), "good_eigenpairs": good,
+                         "restarts": info["restarts"], "applies": info["applies"],
+                         "kernels_per_arnoldi_step": launches / max(info["applies"], 1),
+                         "apply_us": e0.elapsed_time(e1) * 1e3 / reps,
+                         "launch_mode": "one CUDA graph launch per Arnoldi step (side stream)"}
+            F.close()
+            P.close()
+    return out
 
 
 def batched_sweep(klst, compare=True):
