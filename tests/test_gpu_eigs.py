@@ -82,7 +82,7 @@ def test_c2_against_golden(klst, prec, arith):
 
 
 def test_c3_full_size_checked_by_oracle_operator(klst):
-    """The bench's configuration at full size (n = 281,088; df64 factors and basis, keep 60,
+    """The bench's configuration at full size (n = 281,088; df64 factors and basis, keep 70,
     KLST_CONV_RESID 2e-11).  No oracle eigensolve fits at this size, so every returned eigenpair is
     checked with the oracle's own matrix-free float64 A and B (||A q - omega B q|| <= 1e-10,
     ||q|| = 1), and the eigenvalues are compared with the all-float64 GPU path (1e-9 relative)."""
