@@ -102,8 +102,8 @@ typedef struct {
     double t_eigs_ms;     /* wall time of the eigs call */
     double max_resid;     /* max explicit ||A q - omega B q|| over returned pairs, ||q|| = 1 */
     double max_refine_resid; /* worst final relative refinement residual (mixed) */
-    double t_apply_ms;    /* device time in shift-invert applies (CUDA events) */
-    double t_orth_ms;     /* device time in Gram-Schmidt orthogonalisation */
+    double t_apply_ms;    /* device time in shift-invert applies (CUDA events; 0 in graph mode) */
+    double t_orth_ms;     /* device time in Gram-Schmidt (graph mode: applies + Gram-Schmidt) */
     double t_restart_ms;  /* device time in Schur restarts and basis rotations */
     double t_schur_ms;    /* of which the small Schur/reorder step */
     int32_t reorths;      /* Arnoldi steps that needed the second Gram-Schmidt pass (DGKS test) */
@@ -231,9 +231,14 @@ int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol)
 /*
  * klst_eigs -- the nev eigenvalues nearest sigma by Krylov-Schur restarted Arnoldi on T
  * (Sec. 4.1: implicitly restarted Arnoldi with shift-and-invert), with classical
- * Gram-Schmidt in float64 with a second pass when the DGKS test
- * (||w'|| < ||w|| / sqrt 2) asks for it and the small Schur/reorder
- * step in float64 on the device.  Eigenvalues omega = sigma + 1/mu are returned
+ * Gram-Schmidt (a second pass when the DGKS test ||w'|| < ||w|| / sqrt 2 asks for it) in
+ * float64 (opts->arith = KLST_ARITH_F64) or double-float (KLST_ARITH_DF64), and the small
+ * Schur/reorder step on the device (Householder, QR sweeps and Q rebuild in double-float).
+ * With KLST_ARITH_DF64 on a stream other than the legacy default stream, each Arnoldi step is
+ * captured once into a CUDA graph and launched as one graph per step (not when the stream is
+ * already capturing, when klst_prof_enable is on, or with KLST_NO_GRAPH=1 in the environment);
+ * results are the same either way, and info->t_apply_ms is then 0 with the whole expansion in
+ * info->t_orth_ms.  Eigenvalues omega = sigma + 1/mu are returned
  * nearest-first in evals_host (host complex128[nev]); evecs (device complex128,
  * n x nev column-major, may be NULL) receive unit-norm purified eigenvectors
  * q = T x / ||T x||; resid_host (host float64[nev], may be NULL) receives

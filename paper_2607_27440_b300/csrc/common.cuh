@@ -1,5 +1,6 @@
 // Internal helpers shared by the kLST CUDA sources (not part of the public ABI).
 #pragma once
+#include <atomic>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -132,6 +133,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Kernel launches issued by this library (process-wide counter, read by klst_launch_count).
 void note_launch();
+// true the first time it is called for the current device with this flag word (thread-safe); used
+// to set per-device kernel attributes once
+inline bool once_per_device(std::atomic<unsigned long long>& mask) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    const unsigned long long bit = 1ull << dev;
+    return !(mask.fetch_or(bit) & bit);
+}
 void note_launches(unsigned long long k);
 void set_capturing(bool on);
 

@@ -210,11 +210,10 @@ int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t l
                     const int* done, int df_arith) {
     const int NXP = nxp_of(p->nx), KB = 256 / NXP;
     const size_t smem = pencil_rows_smem(p);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_set{0};
+    if (once_per_device(attr_set)) {
         cudaFuncSetAttribute(k_pencil_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_pencil_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
     }
     dim3 blk(NXP, KB), grd(pencil_rows_blocks(p), nrhs);
     if (df_arith)
