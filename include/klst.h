@@ -200,7 +200,10 @@ size_t klst_apply_pencil_noalloc_capacity(void);
  * inflow rows replaced by identity rows; shared by g^ and h^) and U V^H is the
  * rank-4-per-point BGK moment coupling.  Computes every K_k^{-1} (batched
  * Gauss-Jordan with partial pivoting), the capacitance C = I - V^H K^{-1} U
- * (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan, one launch per pivot).  precision: KLST_FP64 (all float64),
+ * (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan with partial pivoting: for 4 Nx <= 384 one launch of one
+ * thread-block cluster holding the matrix in its CTAs' shared memory, otherwise one launch per
+ * pivot; both give the same result).  KLST_NO_CLUSTER_GJ=1 in the environment selects the
+ * per-pivot launches.  precision: KLST_FP64 (all float64),
  * KLST_MIXED (K_k^{-1} stored in complex float32, each apply corrected by float64 iterative refinement)
  * or KLST_DF64 (K_k^{-1} stored as double-float pairs, the same bytes as float64, and the block solves
  * run in double-float arithmetic on the float32 pipes; ~2^-48 accuracy without refinement).
