@@ -27,10 +27,13 @@ int64_t solve_footprint(const klst_pencil_desc& d, int precision, const klst_eig
     const int64_t m = o.ncv, nev = o.nev;
     int64_t b = 0;
     b += 2 * nxi * 8 * nx * 8 + 4 * nx * nx * 8 + 2 * nx * nxi * 8;               // pencil (+ build scratch)
-    b += nxi * nx * nx * 16 + (precision == KLST_MIXED ? nxi * nx * nx * 8 : 0);  // K^{-1} (+ rounded copy)
+    // K^{-1} in float64 while it is formed, plus the stored complex64 (MIXED) or df64 (DF64) copy
+    b += nxi * nx * nx * 16 + (precision == KLST_MIXED ? nxi * nx * nx * 8 : precision == KLST_DF64 ? nxi * nx * nx * 16 : 0);
     b += 11 * r * r * 16;                                                        // capacitance buffers
     b += 2 * n * (m + 1) * 16 + 3 * n * nev * 16;                                // Krylov bases + extraction
     b += (precision == KLST_MIXED ? 2 * n * nev * 16 : 0);                       // refinement work
+    if (o.arith == KLST_ARITH_DF64)                                              // df64 basis: w, v and partial dots
+        b += 2 * n * 16 + ((n + 511) / 512) * (m + 2) * 16;
     b += 31 * m * m * 32 + 8 * m * m * 16;                                       // Schur work and rotation log
     return b + (64 << 20);
 }
