@@ -283,6 +283,13 @@ int klst_batch_eigs(int32_t npencils, const klst_pencil_desc* descs, const doubl
  * info, and the latency from submit to completion in ms, releases the ticket and returns the solve's
  * status; a finished ticket can be polled once.  Thread-safe (internally locked).
  */
+/*
+ * klst_solve_footprint -- device bytes one build + factor + eigs of this request holds at its peak:
+ * the admission size klst_server uses (the paper has no counterpart: a serving service).  Returns the
+ * byte count (> 0), or KLST_EINVAL (< 0) when the request is invalid (the klst_eigs option rules).
+ */
+int64_t klst_solve_footprint(const klst_pencil_desc* desc, int32_t precision, const klst_eigs_opts* opts);
+
 typedef struct klst_server_s* klst_server;
 int klst_server_create(int64_t hbm_budget_bytes, int32_t max_slots, klst_server* out);
 int klst_server_submit(klst_server s, const klst_pencil_desc* desc, double sigma_re, double sigma_im,

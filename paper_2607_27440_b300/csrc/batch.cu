@@ -38,6 +38,20 @@ int64_t solve_footprint(const klst_pencil_desc& d, int precision, const klst_eig
     return b + (64 << 20);
 }
 
+// Request checks shared by the batch and serving entry points: the pencil sizes klst_build_pencil
+// accepts, a known precision and klst_eigs's option rules, so that nothing is sized from a bad value.
+static int validate_request(const klst_pencil_desc& d, int precision, const klst_eigs_opts& o) {
+    if (d.nx < 4 || d.nx > 128 || d.qx < 1 || d.qx > 256 || d.qy < 1 || d.qy > 256) {
+        set_error("invalid pencil sizes nx=%d qx=%d qy=%d", d.nx, d.qx, d.qy);
+        return KLST_EINVAL;
+    }
+    if (precision != KLST_FP64 && precision != KLST_MIXED && precision != KLST_DF64) {
+        set_error("invalid precision %d", precision);
+        return KLST_EINVAL;
+    }
+    return validate_eigs_opts(&o, 2 * (int64_t)d.nx * d.qx * d.qy);
+}
+
 struct SolveResult {
     int status = KLST_OK;
     std::vector<double> evals, resid;
@@ -45,8 +59,8 @@ struct SolveResult {
 };
 
 // Full path for one pencil on stream s.
-static void solve_one(const klst_pencil_desc& d, double2 sigma, int precision, const klst_eigs_opts& o,
-                      cudaStream_t s, SolveResult& out) {
+static void solve_one_impl(const klst_pencil_desc& d, double2 sigma, int precision, const klst_eigs_opts& o,
+                           cudaStream_t s, SolveResult& out) {
     out.evals.assign(2 * o.nev, 0.0);
     out.resid.assign(o.nev, 0.0);
     memset(&out.info, 0, sizeof(out.info));
@@ -61,6 +75,21 @@ static void solve_one(const klst_pencil_desc& d, double2 sigma, int precision, c
     out.status = rc;
     if (rc != KLST_OK && rc != KLST_ENOCONV)  // nothing was computed: no eigenpair may count as valid
         for (auto& r : out.resid) r = INFINITY;
+}
+
+// A host exception (a failed host allocation) becomes the request's status instead of
+// terminating the process with every other request in flight.
+static void solve_one(const klst_pencil_desc& d, double2 sigma, int precision, const klst_eigs_opts& o,
+                      cudaStream_t s, SolveResult& out) {
+    try {
+        solve_one_impl(d, sigma, precision, o, s, out);
+    } catch (...) {
+        cudaStreamSynchronize(s);
+        out.status = KLST_ENOMEM;
+        out.evals.assign(2 * std::max(o.nev, 0), 0.0);
+        out.resid.assign(std::max(o.nev, 0), INFINITY);
+        set_error("host exception during a solve (out of host memory?)");
+    }
 }
 
 }  // namespace klst
@@ -78,6 +107,9 @@ extern "C" int klst_batch_eigs(int32_t npencils, const klst_pencil_desc* descs, 
         set_error("klst_batch_eigs seeds every start vector (opts->v0 must be NULL; pencil i uses seed + i)");
         return KLST_EINVAL;
     }
+    for (int i = 0; i < npencils; ++i)
+        if (int vrc = validate_request(descs[i], precision, *opts)) return vrc;
+    for (int i = 0; i < npencils; ++i) status_host[i] = KLST_ECUDA;  // until a worker runs it
     int dev = 0;
     KLST_CK(cudaGetDevice(&dev));
     const int W = std::max(1, std::min<int>(npencils, nworkers > 0 ? nworkers : 16));
@@ -128,6 +160,8 @@ struct klst_server_s {
         int64_t footprint;
         std::chrono::steady_clock::time_point t_submit, t_start, t_done;
         bool done = false;
+        bool claimed = false;   // a poll is collecting it: no other poll may touch it
+        int passed = 0;         // times a later request was admitted ahead of it
         SolveResult res;
     };
     std::mutex mu;
@@ -136,6 +170,11 @@ struct klst_server_s {
     std::map<uint64_t, Req*> all;            // every request not yet collected
     int64_t budget = 0, in_flight = 0;
     int slots = 0, running = 0;
+    // Backfill is bounded: once the head request has been passed over kMaxPassed times, or has
+    // waited kMaxWaitMs, nothing else is admitted until it fits, so a large request cannot starve
+    // behind a stream of small ones.
+    static constexpr int kMaxPassed = 8;
+    static constexpr double kMaxWaitMs = 2000.0;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::vector<std::thread> workers;
@@ -152,17 +191,27 @@ static void server_worker(klst_server S) {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop) break;
-                // admit the oldest request that fits the remaining HBM budget (backfill past a
-                // head request that has to wait for memory)
-                for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
-                    if (S->in_flight + (*it)->footprint <= S->budget) {
-                        r = *it;
-                        S->queue.erase(it);
-                        break;
+                // admit the oldest request that fits the remaining HBM budget; a later one may
+                // backfill past a head request that has to wait for memory, until the head has
+                // been passed over kMaxPassed times or has waited kMaxWaitMs
+                if (!S->queue.empty()) {
+                    klst_server_s::Req* head = S->queue.front();
+                    const double waited = std::chrono::duration<double, std::milli>(
+                        std::chrono::steady_clock::now() - head->t_submit).count();
+                    const bool may_pass = head->passed < klst_server_s::kMaxPassed && waited < klst_server_s::kMaxWaitMs;
+                    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+                        if (it != S->queue.begin() && !may_pass) break;
+                        if (S->in_flight + (*it)->footprint <= S->budget) {
+                            r = *it;
+                            if (it != S->queue.begin()) head->passed += 1;
+                            S->queue.erase(it);
+                            break;
+                        }
                     }
                 }
                 if (r) break;
-                S->cv.wait(lk);
+                // a waiting head re-evaluates its age periodically even when nothing finishes
+                S->cv.wait_for(lk, std::chrono::milliseconds(50));
             }
             if (!r) break;
             S->in_flight += r->footprint;
@@ -183,6 +232,12 @@ static void server_worker(klst_server S) {
     cudaStreamDestroy(s);
 }
 
+extern "C" int64_t klst_solve_footprint(const klst_pencil_desc* d, int32_t precision, const klst_eigs_opts* o) {
+    if (!d || !o) { set_error("invalid arguments to klst_solve_footprint"); return KLST_EINVAL; }
+    if (int vrc = validate_request(*d, precision, *o)) return vrc;
+    return solve_footprint(*d, precision, *o);
+}
+
 extern "C" int klst_server_create(int64_t hbm_budget_bytes, int32_t max_slots, klst_server* out) {
     if (!out || max_slots < 1 || hbm_budget_bytes <= 0) { set_error("invalid server arguments"); return KLST_EINVAL; }
     klst_server S = new klst_server_s();
@@ -197,6 +252,7 @@ extern "C" int klst_server_create(int64_t hbm_budget_bytes, int32_t max_slots, k
 extern "C" int klst_server_submit(klst_server S, const klst_pencil_desc* d, double sig_re, double sig_im,
                                   int32_t precision, const klst_eigs_opts* o, uint64_t* ticket) {
     if (!S || !d || !o || !ticket || o->v0) { set_error("invalid submit arguments (opts->v0 must be NULL)"); return KLST_EINVAL; }
+    if (int vrc = validate_request(*d, precision, *o)) return vrc;
     auto* r = new klst_server_s::Req();
     r->desc = *d;
     r->sigma = mk(sig_re, sig_im);
@@ -228,7 +284,12 @@ extern "C" int klst_server_poll(klst_server S, uint64_t ticket, int32_t wait, in
     auto it = S->all.find(ticket);
     if (it == S->all.end()) { set_error("unknown or already collected ticket"); return KLST_EINVAL; }
     klst_server_s::Req* r = it->second;
-    if (wait) S->cv_done.wait(lk, [&] { return r->done; });
+    if (r->claimed) { set_error("ticket is being collected by another poll"); return KLST_EINVAL; }
+    if (wait) {
+        // claim the ticket so that a concurrent poll cannot collect (and free) it while this one sleeps
+        r->claimed = true;
+        S->cv_done.wait(lk, [&] { return r->done; });
+    }
     *done = r->done ? 1 : 0;
     if (!r->done) return KLST_OK;
     const int nev = r->opts.nev;

@@ -540,15 +540,37 @@ struct EigsWork {
 
 using namespace klst;
 
-extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_host, void* evecs, double* resid_host,
-                         klst_eigs_info* info, klst_stream stream) {
-    if (!f || !o || !evals_host) { set_error("invalid arguments to klst_eigs"); return KLST_EINVAL; }
+namespace klst {
+// The option rules of klst_eigs, shared with the batch and serving entry points so that a bad
+// request is rejected before any buffer is sized from it.
+int validate_eigs_opts(const klst_eigs_opts* o, int64_t n) {
     const int nev = o->nev, m = o->ncv;
-    if (nev < 1 || m < nev + 2 || m > 160 || (int64_t)m + 1 > f->n || o->max_restarts < 0 || o->max_refine < 0 ||
+    if (nev < 1 || m < nev + 2 || m > 160 || (int64_t)m + 1 > n || o->max_restarts < 0 || o->max_refine < 0 ||
         !(o->tol > 0)) {
         set_error("invalid eigs options nev=%d ncv=%d (need 1 <= nev, nev+2 <= ncv <= min(160, n-1))", nev, m);
         return KLST_EINVAL;
     }
+    if (o->keep != 0 && (o->keep < nev || o->keep >= m)) {
+        set_error("invalid keep=%d (need nev <= keep < ncv)", o->keep);
+        return KLST_EINVAL;
+    }
+    if (o->arith != KLST_ARITH_F64 && o->arith != KLST_ARITH_DF64) {
+        set_error("invalid arith=%d", o->arith);
+        return KLST_EINVAL;
+    }
+    if (o->conv != KLST_CONV_REL && o->conv != KLST_CONV_RESID) {
+        set_error("invalid conv=%d", o->conv);
+        return KLST_EINVAL;
+    }
+    return KLST_OK;
+}
+}  // namespace klst
+
+extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_host, void* evecs, double* resid_host,
+                         klst_eigs_info* info, klst_stream stream) {
+    if (!f || !o || !evals_host) { set_error("invalid arguments to klst_eigs"); return KLST_EINVAL; }
+    const int nev = o->nev, m = o->ncv;
+    if (int vrc = validate_eigs_opts(o, f->n)) return vrc;
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     klst_pencil p = f->p;
@@ -561,10 +583,6 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     const int nblk = std::min<int64_t>((n + 255) / 256, 6 * sms);  // 6 resident 256-thread CTAs per SM
     const int nupd = std::min<int64_t>((n + 255) / 256, 4 * sms);  // df64 updates: 64 registers, 4 CTAs per SM
     const int ng = pencil_work_groups(p);
-    if (o->keep != 0 && (o->keep < nev || o->keep >= m)) {
-        set_error("invalid keep=%d (need nev <= keep < ncv)", o->keep);
-        return KLST_EINVAL;
-    }
     const int keep = o->keep ? o->keep : std::min(m - 1, nev + (m - nev) / 2);
     const int prev_refine = f->max_refine, prev_arith = f->arith;
     const double prev_rtol = f->refine_tol;

@@ -72,6 +72,8 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
 int apply_pencil_dev(klst_pencil p, const double2* x, double2* y, int nrhs, const double2* omega_dev,
                      cudaStream_t s, double2* mwork, double2* mpart, int ngroups);
 int pencil_work_groups(klst_pencil p);
+// klst_eigs's option rules (KLST_EINVAL with a message); n = unknowns of the pencil
+int validate_eigs_opts(const klst_eigs_opts* o, int64_t n);
 void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,
                          cudaStream_t s);
 }  // namespace klst

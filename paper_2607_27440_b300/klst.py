@@ -79,6 +79,7 @@ EXPORTS = {
                             ctypes.POINTER(EigsInfo), c_void_p]),
     "klst_batch_eigs": (c_int32, [c_int32, c_void_p, c_void_p, c_int32, ctypes.POINTER(EigsOpts), c_int32,
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
+    "klst_solve_footprint": (c_int64, [ctypes.POINTER(PencilDesc), c_int32, ctypes.POINTER(EigsOpts)]),
     "klst_server_create": (c_int32, [c_int64, c_int32, ctypes.POINTER(c_void_p)]),
     "klst_server_submit": (c_int32, [c_void_p, ctypes.POINTER(PencilDesc), c_double, c_double, c_int32,
                                      ctypes.POINTER(EigsOpts), ctypes.POINTER(c_uint64)]),
@@ -164,6 +165,32 @@ def _ptr(t):
     return c_void_p(t.data_ptr())
 
 
+def _check_in(x, n, name="x"):
+    """x must be a CUDA complex128 tensor of shape (n,) or (nrhs, n); returns it contiguous."""
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.complex128 or x.device.type != "cuda":
+        raise ValueError(f"{name} must be a complex128 CUDA tensor")
+    if x.dim() not in (1, 2) or x.shape[-1] != n or x.numel() == 0:
+        raise ValueError(f"{name} must have shape (n,) or (nrhs, n) with n = {n}, got {tuple(x.shape)}")
+    return x.contiguous()
+
+
+def _check_out(out, x, name="out"):
+    """A caller-supplied output must match x exactly and not overlap it: the kernels write n * nrhs
+    complex128 values through its pointer."""
+    torch = _torch()
+    if not isinstance(out, torch.Tensor) or out.dtype != torch.complex128:
+        raise ValueError(f"{name} must be a complex128 tensor")
+    if out.device != x.device:
+        raise ValueError(f"{name} is on {out.device}, x on {x.device}")
+    if tuple(out.shape) != tuple(x.shape) or not out.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {tuple(x.shape)}, got {tuple(out.shape)}")
+    nb = x.numel() * 16
+    if out.data_ptr() < x.data_ptr() + nb and x.data_ptr() < out.data_ptr() + nb:
+        raise ValueError(f"{name} may not overlap x")
+    return out
+
+
 class Pencil:
     """Device-resident kLST pencil (klst_build_pencil)."""
 
@@ -207,7 +234,7 @@ class Pencil:
     def apply(self, x, omega=None, stream=None):
         """(A - omega_r B) x_r for x of shape (nrhs, n) (or (n,)), complex128 on the device."""
         torch = _torch()
-        x = x.contiguous()
+        x = _check_in(x, self.n)
         nrhs = 1 if x.dim() == 1 else x.shape[0]
         y = torch.empty_like(x)
         om = None
@@ -223,9 +250,9 @@ class Pencil:
         ``out`` lets a caller that cannot allocate pass its own output buffer.
         """
         torch = _torch()
-        x = x.contiguous()
+        x = _check_in(x, self.n)
         nrhs = 1 if x.dim() == 1 else x.shape[0]
-        y = torch.empty_like(x) if out is None else out
+        y = torch.empty_like(x) if out is None else _check_out(out, x)
         om = None
         if omega is not None:
             om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, dtype=np.complex128), (nrhs,)))
@@ -267,9 +294,9 @@ class Factor:
     def apply(self, x, out=None, stream=None):
         """y = (A - sigma B)^{-1} B x for x of shape (nrhs, n) or (n,), complex128 on the device."""
         torch = _torch()
-        x = x.contiguous()
+        x = _check_in(x, self.pencil.n)
         nrhs = 1 if x.dim() == 1 else x.shape[0]
-        y = torch.empty_like(x) if out is None else out
+        y = torch.empty_like(x) if out is None else _check_out(out, x)
         _check(load().klst_apply_shift_invert(self.handle, _ptr(x), _ptr(y), nrhs, _stream(stream)))
         return y
 
@@ -285,7 +312,9 @@ class Factor:
         res = np.zeros(nev)
         vec = torch.empty((nev, n), dtype=torch.complex128, device="cuda") if vectors else None
         if v0 is not None:
-            v0 = v0.contiguous()
+            v0 = _check_in(v0, n, "v0")
+            if v0.dim() != 1:
+                raise ValueError("v0 must be one vector of length n")
         est = np.zeros(nev)
         opts = EigsOpts(nev=nev, ncv=ncv, max_restarts=max_restarts, max_refine=max_refine, tol=tol,
                         refine_tol=refine_tol, v0=v0.data_ptr() if v0 is not None else None, seed=seed, conv=conv,
@@ -321,10 +350,22 @@ def batch_eigs(specs, sigmas, nev, ncv, precision=FP64, nworkers=0, **kw):
     st = np.zeros(P, dtype=np.int32)
     infos = (EigsInfo * P)()
     opts = _opts(nev, ncv, **kw)
-    lib.klst_batch_eigs(P, ctypes.cast(descs, c_void_p), sig.ctypes.data_as(c_void_p), precision, ctypes.byref(opts),
-                        nworkers, ev.ctypes.data_as(c_void_p), res.ctypes.data_as(c_void_p),
-                        st.ctypes.data_as(c_void_p), ctypes.cast(infos, c_void_p))
+    code = lib.klst_batch_eigs(P, ctypes.cast(descs, c_void_p), sig.ctypes.data_as(c_void_p), precision,
+                               ctypes.byref(opts), nworkers, ev.ctypes.data_as(c_void_p),
+                               res.ctypes.data_as(c_void_p), st.ctypes.data_as(c_void_p), ctypes.cast(infos, c_void_p))
+    if code == KLST_EINVAL:  # rejected before any pencil ran: status_host was not written
+        _check(code)
     return ev[:, 0::2] + 1j * ev[:, 1::2], res, st, [i.as_dict() for i in infos]
+
+
+def solve_footprint(spec, nev, ncv, precision=FP64, **kw):
+    """Device bytes klst_server admits a request by (klst_solve_footprint)."""
+    d = make_desc(spec)
+    o = _opts(nev, ncv, **kw)
+    b = load().klst_solve_footprint(ctypes.byref(d), precision, ctypes.byref(o))
+    if b < 0:
+        _check(int(b))
+    return int(b)
 
 
 class Server:

@@ -88,3 +88,121 @@ def test_sweep_shapes_in_one_batch(klst):
                                          seed=4)
     assert np.all(st == 0), st
     assert np.max(res) <= 1e-10
+
+
+def _pool():
+    """Reset/read helpers for the default stream-ordered pool's used-memory high-water mark (bytes
+    the library had allocated at once, over what was in use when the mark was reset)."""
+    import torch
+    from cuda.bindings import runtime as rt
+    err, pool = rt.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+    assert err == rt.cudaError_t.cudaSuccess
+    hi, cur = rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent
+
+    def get(a):
+        e, v = rt.cudaMemPoolGetAttribute(pool, a)
+        assert e == rt.cudaError_t.cudaSuccess
+        return int(v)
+
+    def reset():
+        torch.cuda.synchronize()
+        (e,) = rt.cudaMemPoolSetAttribute(pool, hi, rt.cuuint64_t(0))
+        assert e == rt.cudaError_t.cudaSuccess
+        return get(cur)
+
+    return reset, lambda: get(hi)
+
+
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (2, 1), (0, 1)], ids=["fp64", "mixed", "df64", "fp64-df64basis"])
+def test_admission_footprint_covers_measured_peak(klst, prec, arith):
+    """klst_solve_footprint (the server's admission size) is at least the device memory one solve
+    actually holds at its peak, measured as the stream-ordered pool's high-water mark."""
+    spec, es = wl.c2()
+    fp = klst.solve_footprint(spec, es.nev, es.ncv, precision=prec, arith=arith)
+    reset, high = _pool()
+    base = reset()
+    om, res, st, infos = klst.batch_eigs([spec], [es.sigma], es.nev, es.ncv, precision=prec, nworkers=1, tol=1e-11,
+                                         conv=klst.CONV_RESID, seed=2, arith=arith)
+    assert st[0] == 0
+    peak = high() - base
+    assert 0 < peak <= fp, (peak, fp)
+
+
+def test_server_admission_under_memory_pressure(klst):
+    """A budget that holds one large request or a few small ones: requests queue, are admitted as
+    memory frees up, a later small request may backfill past a waiting large one, and every result
+    equals the solve alone."""
+    import time
+    small = [(wl.tiny(nx=16, qx=6, qy=4, mach=1.5 + 0.1 * i, beta=0.3), 0.1j) for i in range(6)]
+    large = (wl.tiny(nx=48, qx=12, qy=8, mach=3.0, beta=0.5), 0.1j)
+    f_small = klst.solve_footprint(small[0][0], NEV, NCV)
+    f_large = klst.solve_footprint(large[0], NEV, NCV)
+    budget = max(f_large, 3 * f_small)
+    assert f_large + f_small > budget  # the large request cannot run beside a small one
+    S = klst.Server(hbm_budget_bytes=budget, max_slots=3)
+    reqs = small[:2] + [large] + small[2:]
+    t0 = time.perf_counter()
+    tickets = [S.submit(sp, z, NEV, NCV, tol=1e-11, conv=klst.CONV_RESID, seed=30 + i) for i, (sp, z) in enumerate(reqs)]
+    peak_running, peak_bytes = 0, 0
+    while True:
+        q, r, b = S.stats()
+        peak_running, peak_bytes = max(peak_running, r), max(peak_bytes, b)
+        assert b <= budget
+        if q == 0 and r == 0:
+            break
+        time.sleep(0.002)
+        assert time.perf_counter() - t0 < 300
+    out = [S.poll(t, wait=True) for t in tickets]
+    for i, (sp, z) in enumerate(reqs):
+        om, res, info, lat, code = out[i]
+        assert code == 0
+        o1, r1 = _alone(klst, sp, z, 0, 30 + i)
+        assert np.array_equal(o1, om) and np.array_equal(r1, res), i
+    assert peak_bytes <= budget
+    S.close()
+
+
+def test_server_large_request_is_not_starved(klst):
+    """Backfill is bounded: one large request submitted among many small ones completes before the
+    small requests that arrived after it have all run (it is not passed over indefinitely)."""
+    import time
+    large = (wl.tiny(nx=48, qx=12, qy=8, mach=3.0, beta=0.5), 0.1j)
+    small = wl.tiny(nx=16, qx=6, qy=4, mach=2.0, beta=0.3)
+    f_small = klst.solve_footprint(small, NEV, NCV)
+    f_large = klst.solve_footprint(large[0], NEV, NCV)
+    budget = max(f_large, 2 * f_small)
+    assert f_large + f_small > budget
+    S = klst.Server(hbm_budget_bytes=budget, max_slots=2)
+    sub = {}
+    tickets = []
+    for i in range(3):
+        tickets.append(S.submit(small, 0.1j, NEV, NCV, tol=1e-11, conv=klst.CONV_RESID, seed=i))
+        sub[tickets[-1]] = time.perf_counter()
+    tl = S.submit(large[0], large[1], NEV, NCV, tol=1e-11, conv=klst.CONV_RESID, seed=99)
+    sub[tl] = time.perf_counter()
+    for i in range(3, 30):
+        tickets.append(S.submit(small, 0.1j, NEV, NCV, tol=1e-11, conv=klst.CONV_RESID, seed=i))
+        sub[tickets[-1]] = time.perf_counter()
+    done = {}
+    for t in tickets + [tl]:
+        om, res, info, lat, code = S.poll(t, wait=True)
+        assert code == 0
+        done[t] = sub[t] + lat / 1e3
+    later = [done[t] for t in tickets[3:]]
+    assert done[tl] < max(later), "the large request ran after every small request behind it"
+    S.close()
+
+
+def test_server_and_batch_reject_bad_options(klst):
+    """Options klst_eigs would reject are rejected at submission, before any worker sizes a buffer."""
+    S = klst.Server(hbm_budget_bytes=1 << 30, max_slots=1)
+    for kw in (dict(nev=-3, ncv=20), dict(nev=6, ncv=7), dict(nev=6, ncv=400)):
+        with pytest.raises(klst.KlstError) as ei:
+            S.submit(SMALL[0][0], 0.1j, kw["nev"], kw["ncv"])
+        assert ei.value.code == klst.KLST_EINVAL
+    with pytest.raises(klst.KlstError):
+        S.submit(SMALL[0][0], 0.1j, NEV, NCV, precision=7)
+    S.close()
+    with pytest.raises(klst.KlstError) as ei:
+        klst.batch_eigs([SMALL[0][0]], [0.1j], 6, 6, precision=0)
+    assert ei.value.code == klst.KLST_EINVAL and "invalid eigs options" in str(ei.value)

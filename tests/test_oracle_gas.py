@@ -138,3 +138,64 @@ def test_base_flow_limits():
         assert d["u"][0] == pytest.approx(u2, rel=2e-3)
         assert d["rho"][-1] == pytest.approx(1.0, rel=2e-3)
         assert np.all(d["nu"] > 0)
+
+
+@pytest.mark.parametrize("M", [1.2, 3.0, 4.0])
+def test_nondimensional_viscosity_reproduces_table_knudsen(M):
+    """gas.transport's mu at the free-stream state, put into the mean-free-path definition of Sec. 2.1
+    (l = (16/5) mu / (rho sqrt(2 pi R T)), here in shock-thickness units with rho = T = 1, R = 1/2),
+    is Kn_Delta = l / Delta of Table 1DShockThickness (0.081 / 0.511 / 0.598, printed to 3 decimals).
+    A wrong u_inf factor or Re_Delta in mu would miss the table."""
+    spec = wl.tiny(mach=M).as_dict()
+    u_inf = M * np.sqrt(spec["gamma"] / 2.0)
+    T, P, mu, nu = gas.transport(np.array([1.0]), np.array([u_inf]), np.array([0.0]),
+                                 np.array([0.5 * u_inf ** 2 + 0.75]), spec)
+    assert T[0] == pytest.approx(1.0, rel=1e-15)
+    kn = (16.0 / 5.0) * mu[0] / (1.0 * np.sqrt(2.0 * np.pi * 0.5 * 1.0))
+    assert kn == pytest.approx(gas.SHOCK_TABLE[M][2], abs=0.0015)
+
+
+@pytest.mark.parametrize("M", [1.2, 3.0, 4.0])
+def test_collision_frequency_matches_dimensional_gas(M):
+    """nu = P / mu in the nondimensional units equals the SI collision frequency p / mu(T) with
+    mu(T) = mu_inf (T / T_inf)^s (the power law of Eq. GB1DShockeqn, Table 1DShockConditions), scaled
+    by the time unit Delta / u_ref, at the downstream Rankine-Hugoniot state where T != 1.  This pins
+    P = rho T / 2, the u_inf / Re_Delta factor and the exponent s together (to the table's 3 figures)."""
+    spec = wl.tiny(mach=M).as_dict()
+    g = gas.ARGON
+    rho2, u2, T2 = gas.rankine_hugoniot(M, spec["gamma"])
+    _, _, _, nu = gas.transport(np.array([rho2]), np.array([u2]), np.array([0.0]),
+                                np.array([0.5 * u2 ** 2 + 0.75 * T2]), spec)
+    rho_si = g["P_inf"] / (g["R"] * g["T_inf"]) * rho2
+    T_si = g["T_inf"] * T2
+    mu_si = g["mu_inf"] * (T_si / g["T_inf"]) ** g["s"]
+    nu_si = rho_si * g["R"] * T_si / mu_si
+    Delta = gas.SHOCK_TABLE[M][0]
+    u_ref = np.sqrt(2.0 * g["R"] * g["T_inf"])
+    rel = 0.0005e-3 / Delta + 0.0005 / gas.SHOCK_TABLE[M][1]  # the table's rounding of Delta and Re
+    assert nu[0] == pytest.approx(nu_si * Delta / u_ref, rel=rel)
+
+
+@pytest.mark.parametrize("M", [1.2, 3.0])
+def test_tanh_base_conserves_mass_and_momentum_flux(M):
+    """The tanh local-Maxwellian base flow: at every collocation point the discrete moments of
+    (g_c, h_c) carry the upstream mass flux rho u and momentum flux rho u^2 + P (P = rho T / 2, T from
+    the moments) to quadrature error, and both ends reach the Rankine-Hugoniot temperatures (Sec. 2.1:
+    the shock joins the two Rankine-Hugoniot states).  A wrong base temperature fails pointwise."""
+    spec = wl.tiny(nx=24, qx=48, qy=24, mach=M, base="tanh", noneq=0, width=0.5).as_dict()
+    x, _ = grids.mapped_diff(24, spec["map_L"], spec["map_sinf"])
+    xi_x, xi_y, W = grids.velocity_grid(48, 24)
+    gc, hc = gas.base_flow(spec, x, xi_x, xi_y)
+    rho, u, v, E = gas.moments(gc, hc, W, xi_x, xi_y)
+    T = gas.temperature(u, v, E)
+    r1, u1, T1 = gas.upstream_state(M, spec["gamma"])
+    r2, u2, T2 = gas.rankine_hugoniot(M, spec["gamma"])
+    mass = rho * u
+    mom = rho * u ** 2 + 0.5 * rho * T
+    # the unscaled 48 x 24 Gauss-Hermite rule integrates the hot downstream Maxwellian (T2 = 3.7 at
+    # M = 3) to ~5e-6; a wrong temperature formula is off by O(1), so 1e-4 separates the two
+    tol = 1e-4
+    assert np.max(np.abs(mass / (r1 * u1) - 1.0)) < tol
+    assert np.max(np.abs(mom / (r1 * u1 ** 2 + 0.5 * r1 * T1) - 1.0)) < tol
+    assert T[-1] == pytest.approx(T1, rel=tol)  # x = -s_inf: upstream
+    assert T[0] == pytest.approx(T2, rel=tol)   # x = +s_inf: downstream

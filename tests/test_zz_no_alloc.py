@@ -44,6 +44,66 @@ def test_noalloc_matches_allocating_operator_twice(klst):
     _close(got2, ref2)
 
 
+def _pool_high_minus_current():
+    """(high-water mark - current use) of the device's default stream-ordered pool, after resetting
+    the mark: a call that allocated (and freed) pool memory in between leaves a positive value."""
+    import torch
+    from cuda.bindings import runtime as rt
+    dev = torch.cuda.current_device()
+    err, pool = rt.cudaDeviceGetDefaultMemPool(dev)
+    assert err == rt.cudaError_t.cudaSuccess
+    attr_hi = rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh
+    attr_cur = rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent
+
+    def reset():
+        torch.cuda.synchronize()
+        (e,) = rt.cudaMemPoolSetAttribute(pool, attr_hi, rt.cuuint64_t(0))
+        assert e == rt.cudaError_t.cudaSuccess
+
+    def read():
+        torch.cuda.synchronize()
+        e1, hi = rt.cudaMemPoolGetAttribute(pool, attr_hi)
+        e2, cur = rt.cudaMemPoolGetAttribute(pool, attr_cur)
+        assert e1 == rt.cudaError_t.cudaSuccess and e2 == rt.cudaError_t.cudaSuccess
+        return int(hi) - int(cur)
+
+    return reset, read
+
+
+def test_noalloc_allocates_nothing(klst):
+    """The defining property: after a warm-up call, a call with a caller-owned output raises neither
+    the stream-ordered pool's high-water mark nor PyTorch's allocation count.  The allocating
+    operator, run the same way, does raise the mark (the check can see an allocation)."""
+    import torch
+    spec = wl.c2()[0]
+    P = klst.Pencil(spec)
+    X = to_dev(wl.random_vectors(P.n, 2, 44))
+    out = X.new_empty(X.shape)
+    om = np.array([0.2j, -0.1 + 0.3j])
+    P.apply_noalloc(X, omega=om, out=out)  # warm-up: resolves the scratch address once per device
+    reset, read = _pool_high_minus_current()
+    reset()
+    P.apply(X, omega=om)
+    assert read() > 0
+    reset()
+    n_alloc = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    P.apply_noalloc(X, omega=om, out=out)
+    P.apply_noalloc(X, out=out)
+    assert read() == 0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == n_alloc
+
+
+def test_noalloc_checks_the_output_buffer(klst):
+    import torch
+    spec = wl.c1()[0]
+    P = klst.Pencil(spec)
+    X = to_dev(wl.random_vectors(P.n, 2, 45))
+    for bad in (X.new_empty((1, P.n)), torch.empty(X.shape, dtype=torch.complex64, device="cuda"),
+                X.new_empty((P.n, 2)).t(), X):
+        with pytest.raises(ValueError):
+            P.apply_noalloc(X, out=bad)
+
+
 def test_noalloc_rejects_work_beyond_the_fixed_array(klst):
     lib = klst.load()
     cap = lib.klst_apply_pencil_noalloc_capacity()
