@@ -45,7 +45,7 @@ typedef enum {
     KLST_ESINGULAR = -3,  /* zero pivot: a shifted block or the capacitance matrix is singular */
     KLST_ENOCONV = -4,    /* eigensolver reached max_restarts before nev pairs converged */
     KLST_EREFINE = -5,    /* mixed-precision refinement did not reach its tolerance */
-    KLST_ETIMEOUT = -6,   /* reserved: a bounded device-side wait gave up (no current call waits on the device) */
+    KLST_ETIMEOUT = -6,   /* a bounded device-side wait gave up (the tensor-core GEMM's pipeline waits) */
     KLST_ECUDA = -7       /* a CUDA runtime call failed */
 } klst_status;
 
@@ -129,9 +129,33 @@ void klst_prof_enable(int32_t on);
 void klst_prof_reset(void);
 int32_t klst_prof_entry(int32_t i, char* name, int32_t name_cap, double* total_ms, int64_t* calls);
 
+/*
+ * klst_debug_fail_alloc_after -- test hook (the paper has no counterpart): the n-th next device
+ * allocation the library makes (n = 0: the next one) fails as if the device were out of memory, so
+ * callers can check that every entry point returns KLST_ENOMEM, leaves its out-handle NULL and frees
+ * what it had allocated.  n < 0 switches the hook off (the default).  Process-wide, thread-safe.
+ */
+void klst_debug_fail_alloc_after(int64_t n);
+
 /* Status text ("KLST_OK", ...) and the calling thread's last error message. */
 const char* klst_status_string(int status);
 const char* klst_last_error(void);
+
+/*
+ * klst_gemm_f64_tc -- C = A B in float64 accuracy on the tensor cores (the building block of the
+ * float64 basis rotation of the Krylov-Schur restart, Sec. 4.1; the paper has no counterpart as a
+ * separate call).  A: device float64 M x K column-major (leading dimension lda >= M), B: device
+ * float64 K x N column-major (ldb >= K), C: device float64 M x N column-major (ldc >= M), no
+ * aliasing; 1 <= K <= 256.  Method: each row of A and each column of B is scaled by a power of two
+ * and cut into eight 7-bit integer slices held exactly in bfloat16; the 36 slice products with
+ * s + t <= 9 are accumulated by tcgen05 MMAs in float32 tensor memory, exactly per diagonal s + t,
+ * and combined in float64.  Error: |C - AB|_rc <= ~K 2^-54 max_k |A_rk| max_k |B_kc| (float64-level
+ * relative to the row and column maxima).  Allocates a workspace of ~16 (M + N) K bytes per call.
+ * Errors: KLST_EINVAL, KLST_ENOMEM, KLST_ETIMEOUT (a bounded device wait gave up; C is then
+ * unspecified).  Synchronising.
+ */
+int klst_gemm_f64_tc(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int32_t M,
+                     int32_t N, int32_t K, klst_stream stream);
 
 /*
  * klst_build_pencil -- assemble the structured pencil on the device (Sec. 2.2, 3.1, 3.2).
@@ -232,6 +256,15 @@ int klst_apply_shift_invert(klst_factor f, const void* x, void* y, int32_t nrhs,
 int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol);
 
 /*
+ * klst_factor_check -- waits for stream and reports whether any klst_apply_shift_invert on this MIXED
+ * factor since the last check ended its max_refine refinement sweeps with ||r|| / ||B x|| still above
+ * refine_tol: KLST_EREFINE (the flag is then cleared; the applies' outputs were still written and are
+ * the best iterates reached), else KLST_OK.  klst_eigs reports the same condition for the applies it
+ * makes by returning KLST_EREFINE after filling every output.  Synchronising.
+ */
+int klst_factor_check(klst_factor f, klst_stream stream);
+
+/*
  * klst_eigs -- the nev eigenvalues nearest sigma by Krylov-Schur restarted Arnoldi on T
  * (Sec. 4.1: implicitly restarted Arnoldi with shift-and-invert), with classical
  * Gram-Schmidt (a second pass when the DGKS test ||w'|| < ||w|| / sqrt 2 asks for it) in
@@ -251,7 +284,9 @@ int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol)
  * within 1% of the last returned one (a cluster straddling the nev boundary, whose internal
  * order is not resolved); any separated nearer Ritz value keeps the iteration going.
  * Errors: KLST_ENOCONV (fewer than nev converged; the converged ones are still
- * returned and info->nconv says how many), KLST_EINVAL.  Synchronising.
+ * returned and info->nconv says how many), KLST_EREFINE (MIXED factors: every pair converged but at
+ * least one apply ended its refinement above refine_tol; all outputs are filled and resid_host holds
+ * each pair's explicit residual), KLST_EINVAL.  Synchronising.
  */
 int klst_eigs(klst_factor f, const klst_eigs_opts* opts, double* evals_host, void* evecs,
               double* resid_host, klst_eigs_info* info, klst_stream stream);

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256, 4) k_solve_pass2(int nx, int nxi, const C
 // Refinement bookkeeping: done[rhs] = ||r|| <= tol ||b||; worst residual; sweep counter.
 // One warp per right-hand side sums the per-block norms (fixed order).
 __global__ void k_refine_check(int nblk, const double* __restrict__ normpart, double tol, int* done, double* worst,
-                               int* sweeps, int last) {
+                               int* sweeps, int last, Status* st) {
     const int rhs = blockIdx.x, lane = threadIdx.x;
     if (done[rhs]) return;
     double rr = 0, bb = 0;
@@ -205,6 +205,7 @@ __global__ void k_refine_check(int nblk, const double* __restrict__ normpart, do
     }
     if (ok) done[rhs] = 1;
     else if (!last) atomicAdd(sweeps, 1);
+    else atomicOr(&st->flags, ST_REFINE);  // max_refine sweeps did not reach refine_tol
 }
 
 template <typename C> static const char* pass_name(int pass);
@@ -256,7 +257,8 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
         rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done,
                              f->arith);
         if (rc) return rc;
-        k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last); klst::note_launch();
+        k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last,
+                                            f->status); klst::note_launch();
         prof_end("refine_residual", s);
         KLST_CK_LAUNCH();
         if (last) break;

@@ -73,7 +73,7 @@ static void solve_one_impl(const klst_pencil_desc& d, double2 sigma, int precisi
     if (p) klst_pencil_destroy(p);
     cudaStreamSynchronize(s);
     out.status = rc;
-    if (rc != KLST_OK && rc != KLST_ENOCONV)  // nothing was computed: no eigenpair may count as valid
+    if (rc != KLST_OK && rc != KLST_ENOCONV && rc != KLST_EREFINE)  // nothing computed: no pair may count
         for (auto& r : out.resid) r = INFINITY;
 }
 

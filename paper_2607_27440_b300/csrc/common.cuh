@@ -26,7 +26,9 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 enum : int {
     ST_SINGULAR = 1,   // zero pivot in a block or capacitance inverse
     ST_NOCONV_QR = 4,  // small Schur QR iteration limit
-    ST_BREAKDOWN = 8   // Arnoldi breakdown (invariant subspace)
+    ST_BREAKDOWN = 8,  // Arnoldi breakdown (invariant subspace)
+    ST_REFINE = 16,    // a mixed-precision apply ended its refinement sweeps above refine_tol
+    ST_TIMEOUT = 32    // a bounded device-side wait gave up
 };
 
 // ------------------------------------------------------------------ complex arithmetic
@@ -149,6 +151,8 @@ void set_capturing(bool on);
 // not serialise the device the way cudaMalloc/cudaFree do.
 cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s);
 void dfree(void* ptr, cudaStream_t s);
+// test hook behind klst_debug_fail_alloc_after: the n-th next dmalloc fails (n < 0: off)
+void fail_alloc_after(long long n);
 
 }  // namespace klst
 

@@ -1,7 +1,8 @@
 // Krylov-Schur restarted Arnoldi on T = (A - sigma B)^{-1} B (Sec. 4.1, Eq. parShiftInvert):
-// basis expansion with the shift-invert apply, classical Gram-Schmidt with one
-// reorthogonalisation in float64 (the paper's -bv_orthog_type cgs plus the standard DGKS pass),
-// the float64 Schur restart (schur.cu), basis rotation, purification and explicit residuals.
+// basis expansion with the shift-invert apply, classical Gram-Schmidt applied twice (the paper's
+// -bv_orthog_type cgs plus a reorthogonalisation: orth64.cu for the float64 basis, the df64
+// kernels below for the double-float one), the Schur restart (schur.cu), basis rotation,
+// purification and explicit residuals.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -14,102 +15,6 @@
 
 namespace klst {
 
-
-// part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i]; with_self adds column ncols = |w|^2.
-// gate (optional): skip when *gate == 0 (reorthogonalisation not needed).
-__global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ w,
-                       int64_t n, int chunk, double2* __restrict__ part, int ldp, int with_self,
-                       const int* __restrict__ gate) {
-    if (gate && *gate == 0) return;
-    extern __shared__ double2 sw[];
-    const int64_t r0 = (int64_t)blockIdx.x * chunk;
-    const int len = (int)((n - r0) < chunk ? (n - r0) : chunk);
-    for (int i = threadIdx.x; i < len; i += blockDim.x) sw[i] = w[r0 + i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int col = wid; col < ncols + with_self; col += nw) {
-        const double2* vc = col < ncols ? V + col * ldv + r0 : sw;
-        double2 a = mk(0, 0);
-        for (int i = lane; i < len; i += 32) cfma_conj(a, vc[i], sw[i]);
-        for (int o = 16; o > 0; o >>= 1) {
-            a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-            a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
-        }
-        if (lane == 0) part[(size_t)blockIdx.x * ldp + col] = a;
-    }
-}
-
-// h[col] (+)= sum_chunk part[chunk][col]: one warp per column, fixed lane stride + shuffle tree;
-// with a closed gate, h2 := 0
-__global__ void k_dots_reduce(const double2* __restrict__ part, int nchunks, int ncols, int ldp, double2* h, int add,
-                              const int* __restrict__ gate) {
-    const int lane = threadIdx.x & 31;
-    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (col >= ncols) return;
-    if (gate && *gate == 0) {
-        if (!add && lane == 0) h[col] = mk(0, 0);
-        return;
-    }
-    double sx = 0.0, sy = 0.0;
-    for (int c = lane; c < nchunks; c += 32) {
-        const double2 v = part[(size_t)c * ldp + col];
-        sx += v.x;
-        sy += v.y;
-    }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) h[col] = add ? h[col] + mk(sx, sy) : mk(sx, sy);
-}
-
-// DGKS test (Daniel, Gragg, Kaufman, Stewart): reorthogonalise only when the first projection
-// removed more than half of ||w||^2, i.e. ||w'|| < ||w|| / sqrt(2).
-__global__ void k_reorth_decide(const double* __restrict__ npart, int nblk, const double2* __restrict__ wself,
-                                int* __restrict__ gate, int* __restrict__ count) {
-    __shared__ double red[32];
-    double s = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += npart[b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q];
-        const int g = a < 0.5 * wself->x ? 1 : 0;
-        *gate = g;
-        if (g) atomicAdd(count, 1);
-    }
-}
-
-// w -= V h (ncols columns); optional per-block partial of |w|^2
-__global__ void k_update(const double2* __restrict__ V, int64_t ldv, int ncols, const double2* __restrict__ h,
-                         double2* __restrict__ w, int64_t n, double* __restrict__ npart, const int* __restrict__ gate) {
-    if (gate && *gate == 0) return;
-    extern __shared__ double2 sh[];
-    for (int i = threadIdx.x; i < ncols; i += blockDim.x) sh[i] = h[i];
-    __syncthreads();
-    double nrm = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 acc = w[i];
-        for (int c = 0; c < ncols; ++c) {
-            const double2 v = V[c * ldv + i], hc = sh[c];
-            acc.x -= v.x * hc.x - v.y * hc.y;
-            acc.y -= v.x * hc.y + v.y * hc.x;
-        }
-        w[i] = acc;
-        nrm += abs2(acc);
-    }
-    if (npart) {
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        __shared__ double red[32];
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-            npart[blockIdx.x] = s;
-        }
-    }
-}
 
 // column norm partials: npart[col * nblk + b]
 __global__ void k_colnorm_part(const double2* __restrict__ X, int64_t ldx, int64_t n, double* __restrict__ npart) {
@@ -136,30 +41,6 @@ __global__ void k_colnorm_fin(const double* __restrict__ npart, int nblk, int nc
     for (int b = lane; b < nblk; b += 32) s += npart[(size_t)col * nblk + b];
     s = warp_sum(s);
     if (lane == 0) nrm[col] = sqrt(s);
-}
-
-// Finish the Arnoldi column j: S[0..j, j] = h1 + h2, S[j+1, j] = beta = ||w||; stores beta.
-__global__ void k_finish_col(const double* __restrict__ npart1, const double* __restrict__ npart2,
-                             const int* __restrict__ gate, int nblk, const double2* __restrict__ h, int j,
-                             double2* __restrict__ S, int lds, double* __restrict__ beta_out, Status* st) {
-    __shared__ double red[32];
-    const double* npart = *gate ? npart2 : npart1;
-    double s = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += npart[b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q];
-        const double beta = sqrt(a);
-        double hn = 0;
-        for (int i = 0; i <= j; ++i) hn += abs2(h[i]);
-        if (!(beta > 1e-13 * sqrt(hn))) atomicOr(&st->flags, ST_BREAKDOWN);
-        S[(size_t)j * lds + j + 1] = mk(beta, 0.0);
-        *beta_out = beta;
-    }
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) S[(size_t)j * lds + i] = h[i];
 }
 
 // x *= 1 / scale[col] (column-wise)
@@ -635,13 +516,13 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             sc.take(W.om, nev);
             sc.take(W.mw, (size_t)4 * p->nx * nev);
             sc.take(W.mp, (size_t)4 * p->nx * ng * nev);
+            sc.take(W.wbuf, n);
+            sc.take(W.vcur, n);
+            sc.take(W.jdev, 4);
             if (dfm) {
-                sc.take(W.wbuf, n);
-                sc.take(W.vcur, n);
                 sc.take(W.opart, (size_t)nchunks * ldp);
                 sc.take(W.onrm, 4);
                 sc.take(W.ocnt, 4);
-                sc.take(W.jdev, 4);
             }
             if (pass == 0) {
                 if ((e = dmalloc(&W.slab, sc.off, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
@@ -667,13 +548,12 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     if (o->v0) KLST_CK(cudaMemcpyAsync(v0, o->v0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
     else { k_randn<<<nblk, 256, 0, s>>>(v0, n, o->seed); klst::note_launch(); }
     int applies = 0;
-    double2* w0 = dfm ? wbuf : V;
-    if ((rc = apply_T(f, v0, w0, 1, s)) != KLST_OK) return fail(rc);
+    if ((rc = apply_T(f, v0, wbuf, 1, s)) != KLST_OK) return fail(rc);
     ++applies;
-    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(w0, n, n, W.npart); klst::note_launch();
+    k_colnorm_part<<<dim3(nblk, 1), 256, 0, s>>>(wbuf, n, n, W.npart); klst::note_launch();
     k_colnorm_fin<<<1, 256, 0, s>>>(W.npart, nblk, 1, W.nrm); klst::note_launch();
     if (dfm) { k_scale_df<<<nblk, 256, 0, s>>>(wbuf, n, W.nrm, V4(V), vcur, n, nullptr); klst::note_launch(); }
-    else { k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(V, n, n, W.nrm); klst::note_launch(); }
+    else { k_scale64_ext(wbuf, n, W.nrm, V, vcur, n, nblk, s); }
     KLST_CK_LAUNCH();
     // phase timers: event pairs recorded per step (eager launches) or per cycle (graph mode) and
     // read after each restart synchronisation; created below once the mode is known
@@ -708,12 +588,21 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         KLST_CK_LAUNCH();
         return KLST_OK;
     };
+    // float64 basis: classical Gram-Schmidt twice, first-pass coefficients on the float32 pipes
+    Orth64Args oa;
+    oa.n = n; oa.m = m; oa.w = wbuf; oa.vcur = vcur; oa.chunk = chunk; oa.nchunks = nchunks; oa.ldp = m + 1;
+    oa.part = W.dpart; oa.h1 = W.h; oa.h2 = W.h + (m + 1); oa.nupd = nblk; oa.npart = W.npart2; oa.nscale = nblk;
+    oa.S = W.S; oa.lds = lds; oa.beta = W.beta; oa.st = f->status;
+    auto f64_orth = [&](double2* Vb, int j, const int* jd) -> int {
+        oa.V = Vb;
+        return orth64_step(oa, j, jd, s);
+    };
     // Graph mode (df64 basis on a capturable stream): one Arnoldi step (apply, Gram-Schmidt, step
     // advance) is captured once per basis buffer and launched as a single graph per step, which
     // removes the host cost of its ~11 kernel launches.  Not used on the legacy default stream, on
     // a stream that is already capturing, or while kernel-group timing is on.
     bool use_graph = false;
-    if (dfm && !prof_enabled() && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+    if (!prof_enabled() && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
         const char* ng = getenv("KLST_NO_GRAPH");
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (!(ng && ng[0] == '1') && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
@@ -726,7 +615,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         if (e1 != cudaSuccess) return cuda_fail(e1, "cudaStreamBeginCapture", __FILE__, __LINE__);
         set_capturing(true);
         int rc2 = apply_T(f, vcur, wbuf, 1, s);
-        if (rc2 == KLST_OK) rc2 = df_orth(Vb, m - 1, W.jdev);
+        if (rc2 == KLST_OK) rc2 = dfm ? df_orth(Vb, m - 1, W.jdev) : f64_orth(Vb, m - 1, W.jdev);
         if (rc2 == KLST_OK) k_step_advance<<<1, 1, 0, s>>>(W.jdev);
         set_capturing(false);
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -756,6 +645,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         if ((e = cudaEventCreate(&evs[i])) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__));
     }
     bool converged = false;
+    int f64_steps = 0;  // float64 basis: every step runs both Gram-Schmidt passes
     for (;;) {
         const int jfirst = k;
         if (use_graph) {
@@ -776,43 +666,23 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             applies += m - k;
         }
         for (int j = use_graph ? m : k; j < m; ++j) {
-            double2* vj = dfm ? vcur : V + (int64_t)j * n;
-            double2* w = dfm ? wbuf : V + (int64_t)(j + 1) * n;
             cudaEventRecord(evs[3 * j], s);
-            if ((rc = apply_T(f, vj, w, 1, s)) != KLST_OK) return fail(rc);
+            if ((rc = apply_T(f, vcur, wbuf, 1, s)) != KLST_OK) return fail(rc);
             cudaEventRecord(evs[3 * j + 1], s);
             ++applies;
-            const int nc = j + 1;
-            // classical Gram-Schmidt, then a second pass only when the DGKS test asks for it
-            if (dfm) {
-                if ((rc = df_orth(V, j, nullptr)) != KLST_OK) return fail(rc);
-                cudaEventRecord(evs[3 * j + 2], s);
-                continue;
-            }
-            prof_begin("orth_pass1", s);
-            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 1, nullptr); klst::note_launch();
-            k_dots_reduce<<<(nc + 1 + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc + 1, m + 1, W.h, 0, nullptr); klst::note_launch();
-            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h, w, n, W.npart, nullptr); klst::note_launch();
-            k_reorth_decide<<<1, 256, 0, s>>>(W.npart, nblk, W.h + nc, W.gate, W.reorth); klst::note_launch();
-            prof_end("orth_pass1", s);
-            prof_begin("orth_pass2", s);
-            k_dots<<<nchunks, 256, dots_smem, s>>>(V, n, nc, w, n, chunk, W.dpart, m + 1, 0, W.gate); klst::note_launch();
-            k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.dpart, nchunks, nc, m + 1, W.h + (m + 1), 0, W.gate); klst::note_launch();
-            k_update<<<nblk, 256, upd_smem, s>>>(V, n, nc, W.h + (m + 1), w, n, W.npart2, W.gate); klst::note_launch();
-            k_dots_reduce<<<(nc + 7) / 8, 256, 0, s>>>(W.h + (m + 1), 1, nc, m + 1, W.h, 1, W.gate); klst::note_launch();  // h1 += h2
-            k_finish_col<<<1, 256, 0, s>>>(W.npart, W.npart2, W.gate, nblk, W.h, j, W.S, lds, W.beta, f->status); klst::note_launch();
-            prof_end("orth_pass2", s);
-            k_scale_cols<<<dim3(nblk, 1), 256, 0, s>>>(w, n, n, W.beta); klst::note_launch();
+            // classical Gram-Schmidt twice (df64: the second pass only when the DGKS test asks)
+            if ((rc = dfm ? df_orth(V, j, nullptr) : f64_orth(V, j, nullptr)) != KLST_OK) return fail(rc);
             cudaEventRecord(evs[3 * j + 2], s);
-            KLST_CK_LAUNCH();
         }
+        if (!dfm) f64_steps += m - k;
         SchurArgs a;
         a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
         a.Ysel = W.Ysel; a.mu_sel = W.musel; a.est_sel = W.estsel;
         a.Vh = (float4*)W.Vh; a.tau = W.tau; a.log = W.rlog; a.log_cap = log_cap; a.log_count = W.rcount;
         a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.conv = o->conv; a.st = f->status;
         cudaEventRecord(evs[3 * (m + 1)], s);
-        if ((rc = launch_schur(a, s)) != KLST_OK) return fail(rc);
+        // the small Schur step runs in the basis arithmetic: float64 for the float64 basis
+        if ((rc = dfm ? launch_schur(a, s) : launch_schur64(a, s)) != KLST_OK) return fail(rc);
         cudaEventRecord(evs[3 * (m + 1) + 1], s);
         Status hst;
         int hconv = 0;
@@ -913,6 +783,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     std::vector<double> res(nret);
     double worst = 0;
     int sweeps = 0, reorths = 0;
+    Status fst;
+    KLST_CK(cudaMemcpyAsync(&fst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaMemcpyAsync(res.data(), W.nrm, sizeof(double) * nret, cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaMemcpyAsync(&worst, f->worst, sizeof(double), cudaMemcpyDeviceToHost, s));
     KLST_CK(cudaMemcpyAsync(&sweeps, f->sweeps, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -943,12 +815,17 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         info->t_orth_ms = t_orth;
         info->t_restart_ms = t_restart;
         info->t_schur_ms = t_schur;
-        info->reorths = reorths;
+        info->reorths = dfm ? reorths : f64_steps;
     }
     W.release(s);
     f->max_refine = prev_refine;
     f->refine_tol = prev_rtol;
     f->arith = prev_arith;
     if (!converged) { set_error("only %d of %d eigenpairs converged after %d restarts", nconv, nev, restarts); return KLST_ENOCONV; }
+    if (fst.flags & ST_REFINE) {
+        set_error("mixed-precision refinement missed refine_tol in at least one apply (worst %.3g after %d sweeps); "
+                  "the eigenpairs and their explicit residuals are returned", worst, o->max_refine);
+        return KLST_EREFINE;
+    }
     return KLST_OK;
 }

@@ -598,6 +598,23 @@ extern "C" int klst_factor_info(klst_factor f, double* sr, double* si, int32_t* 
     return KLST_OK;
 }
 
+extern "C" int klst_factor_check(klst_factor f, klst_stream stream) {
+    if (!f) { set_error("factor is NULL"); return KLST_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    Status hst;
+    KLST_CK(cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s));
+    KLST_CK(cudaStreamSynchronize(s));
+    if (hst.flags & ST_REFINE) {
+        const int cleared = hst.flags & ~ST_REFINE;
+        KLST_CK(cudaMemcpyAsync(&f->status->flags, &cleared, sizeof(int), cudaMemcpyHostToDevice, s));
+        KLST_CK(cudaStreamSynchronize(s));
+        set_error("a mixed-precision apply ended its %d refinement sweeps above refine_tol = %g", f->max_refine,
+                  f->refine_tol);
+        return KLST_EREFINE;
+    }
+    return KLST_OK;
+}
+
 extern "C" int klst_factor_set_refine(klst_factor f, int32_t max_refine, double refine_tol) {
     if (!f || max_refine < 0 || !(refine_tol >= 0)) { set_error("invalid refinement settings"); return KLST_EINVAL; }
     f->max_refine = max_refine;

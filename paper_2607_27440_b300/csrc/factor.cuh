@@ -64,7 +64,32 @@ struct SchurArgs {
     int* log_count;
 };
 
-int launch_schur(const SchurArgs& a, cudaStream_t s);
+int launch_schur(const SchurArgs& a, cudaStream_t s);    // double-float sweeps (schur.cu)
+int launch_schur64(const SchurArgs& a, cudaStream_t s);  // float64 sweeps (schur64.cu)
+void launch_schur_post(const SchurArgs& a, cudaStream_t s);
+
+// float64 Gram-Schmidt of one Arnoldi step (orth64.cu)
+struct Orth64Args {
+    double2* V;        // basis, n x (m + 1) column-major (ld n)
+    int64_t n;
+    int m;             // ncv
+    double2* w;        // the vector to orthogonalise (overwritten)
+    double2* vcur;     // receives the new basis vector (input of the next apply)
+    int chunk, nchunks, ldp;
+    double2* part;     // [nchunks][ldp] per-chunk partial coefficients
+    double2 *h1, *h2;  // first- and second-pass coefficients (m + 1 each)
+    int nupd;          // CTAs of the updates (and entries of npart)
+    double* npart;     // [nupd] partial sums of |w''|^2
+    int nscale;        // CTAs of the scaling kernel
+    double2* S;        // Krylov-Schur matrix, (m + 1) x m column-major
+    int lds;
+    double* beta;      // out: ||w''||
+    Status* st;
+};
+int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s);
+// vcol = vcopy = w / *beta (the first basis vector)
+void k_scale64_ext(const double2* w, int64_t n, const double* beta, double2* vcol, double2* vcopy, int64_t ldv,
+                   int nblk, cudaStream_t s);
 int factor_reserve(klst_factor f, int nrhs, cudaStream_t s);
 // y = T x on the factor's stream; x, y complex128 n x nrhs
 int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t s);

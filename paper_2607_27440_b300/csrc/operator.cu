@@ -245,20 +245,20 @@ extern "C" int klst_apply_pencil(klst_pencil p, const void* x, void* y, int32_t 
     const int ng = pencil_work_groups(p);
     double2 *mw = nullptr, *mp = nullptr, *om = nullptr;
     cudaError_t e;
-    if ((e = cudaMallocAsync(&mw, sizeof(double2) * 4 * p->nx * nrhs, s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&mp, sizeof(double2) * 4 * p->nx * (size_t)ng * nrhs, s)) != cudaSuccess ||
-        (e = cudaMallocAsync(&om, sizeof(double2) * nrhs, s)) != cudaSuccess) {
-        if (mw) cudaFreeAsync(mw, s);
-        if (mp) cudaFreeAsync(mp, s);
+    if ((e = dmalloc((void**)&mw, sizeof(double2) * 4 * p->nx * nrhs, s)) != cudaSuccess ||
+        (e = dmalloc((void**)&mp, sizeof(double2) * 4 * p->nx * (size_t)ng * nrhs, s)) != cudaSuccess ||
+        (e = dmalloc((void**)&om, sizeof(double2) * nrhs, s)) != cudaSuccess) {
+        dfree(mw, s);
+        dfree(mp, s);
         return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
     }
     if (omega) e = cudaMemcpyAsync(om, omega, sizeof(double2) * nrhs, cudaMemcpyHostToDevice, s);
     else e = cudaMemsetAsync(om, 0, sizeof(double2) * nrhs, s);
     int rc = e != cudaSuccess ? cuda_fail(e, "copy omega", __FILE__, __LINE__)
                               : apply_pencil_dev(p, (const double2*)x, (double2*)y, nrhs, om, s, mw, mp, ng);
-    cudaFreeAsync(mw, s);
-    cudaFreeAsync(mp, s);
-    cudaFreeAsync(om, s);
+    dfree(mw, s);
+    dfree(mp, s);
+    dfree(om, s);
     if (rc == KLST_OK && omega) KLST_CK(cudaStreamSynchronize(s));  // host omega buffer must outlive the copy
     return rc;
 }

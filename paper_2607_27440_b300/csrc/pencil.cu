@@ -1,5 +1,6 @@
 // Pencil assembly on the device: grids (Sec. 3.1, 3.2), base state, linearisation
 // coefficients (Sec. 2.2, Eq. CompBGKtilde) and the dense export used by tests.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,7 +25,17 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? KLST_ENOMEM : KLST_ECUDA;
 }
 
+// Host-side fault injection for tests: the n-th next device allocation fails as if the device
+// were out of memory (n < 0: off).
+static std::atomic<long long> g_fail_alloc_after{-1};
+
 cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s) {
+    long long v = g_fail_alloc_after.load();
+    while (v >= 0 && !g_fail_alloc_after.compare_exchange_weak(v, v - 1)) {}
+    if (v == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     static bool pool_ready[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -40,6 +51,8 @@ cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
     return cudaMallocAsync(ptr, bytes, s);
 }
+
+void fail_alloc_after(long long n) { g_fail_alloc_after.store(n < 0 ? -1 : n); }
 
 void dfree(void* ptr, cudaStream_t s) {
     if (ptr) cudaFreeAsync(ptr, s);

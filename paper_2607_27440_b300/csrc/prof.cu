@@ -100,6 +100,8 @@ void prof_report(cudaStream_t s) {
 
 using namespace klst;
 
+extern "C" void klst_debug_fail_alloc_after(int64_t n) { klst::fail_alloc_after(n); }
+
 extern "C" unsigned long long klst_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" void klst_prof_enable(int32_t on) { g_prof_api.store(on ? 1 : 0); }

@@ -534,11 +534,15 @@ int launch_schur(const SchurArgs& a, cudaStream_t s) {
     prof_begin("schur_q", s);
     k_schur_q<<<(m + 31) / 32, 32, sizeof(double2) * 32 * m, s>>>(a); klst::note_launch();
     prof_end("schur_q", s);
+    launch_schur_post(a, s);
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+
+void launch_schur_post(const SchurArgs& a, cudaStream_t s) {
     prof_begin("schur_post", s);
     k_schur_post<<<1, 256, 0, s>>>(a); klst::note_launch();
     prof_end("schur_post", s);
-    KLST_CK_LAUNCH();
-    return KLST_OK;
 }
 
 }  // namespace klst

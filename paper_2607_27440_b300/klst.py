@@ -75,11 +75,15 @@ EXPORTS = {
     "klst_factor_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "klst_apply_shift_invert": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "klst_factor_set_refine": (c_int32, [c_void_p, c_int32, c_double]),
+    "klst_factor_check": (c_int32, [c_void_p, c_void_p]),
+    "klst_debug_fail_alloc_after": (None, [c_int64]),
     "klst_eigs": (c_int32, [c_void_p, ctypes.POINTER(EigsOpts), c_void_p, c_void_p, c_void_p,
                             ctypes.POINTER(EigsInfo), c_void_p]),
     "klst_batch_eigs": (c_int32, [c_int32, c_void_p, c_void_p, c_int32, ctypes.POINTER(EigsOpts), c_int32,
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "klst_solve_footprint": (c_int64, [ctypes.POINTER(PencilDesc), c_int32, ctypes.POINTER(EigsOpts)]),
+    "klst_gemm_f64_tc": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int32,
+                                   c_void_p]),
     "klst_server_create": (c_int32, [c_int64, c_int32, ctypes.POINTER(c_void_p)]),
     "klst_server_submit": (c_int32, [c_void_p, ctypes.POINTER(PencilDesc), c_double, c_double, c_int32,
                                      ctypes.POINTER(EigsOpts), ctypes.POINTER(c_uint64)]),
@@ -291,6 +295,10 @@ class Factor:
     def set_refine(self, max_refine, refine_tol):
         _check(load().klst_factor_set_refine(self.handle, max_refine, refine_tol))
 
+    def check(self, stream=None):
+        """klst_factor_check: KLST_EREFINE if an apply since the last check missed refine_tol, else KLST_OK."""
+        return load().klst_factor_check(self.handle, _stream(stream))
+
     def apply(self, x, out=None, stream=None):
         """y = (A - sigma B)^{-1} B x for x of shape (nrhs, n) or (n,), complex128 on the device."""
         torch = _torch()
@@ -356,6 +364,28 @@ def batch_eigs(specs, sigmas, nev, ncv, precision=FP64, nworkers=0, **kw):
     if code == KLST_EINVAL:  # rejected before any pencil ran: status_host was not written
         _check(code)
     return ev[:, 0::2] + 1j * ev[:, 1::2], res, st, [i.as_dict() for i in infos]
+
+
+def gemm_f64_tc(A, B, stream=None):
+    """C = A @ B (float64 CUDA tensors, 2-D) through klst_gemm_f64_tc (float64 accuracy on tensor cores)."""
+    torch = _torch()
+    for t, nm in ((A, "A"), (B, "B")):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.device.type != "cuda" or t.dim() != 2:
+            raise ValueError(f"{nm} must be a 2-D float64 CUDA tensor")
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    At = A.t().contiguous()  # column-major M x K: the transpose's row-major storage
+    Bt = B.t().contiguous()
+    C = torch.empty((N, M), dtype=torch.float64, device=A.device)  # column-major M x N
+    _check(load().klst_gemm_f64_tc(_ptr(At), M, _ptr(Bt), K, _ptr(C), M, M, N, K, _stream(stream)))
+    return C.t()
+
+
+def fail_alloc_after(n):
+    """klst_debug_fail_alloc_after: the n-th next device allocation of the library fails (n < 0: off)."""
+    load().klst_debug_fail_alloc_after(int(n))
 
 
 def solve_footprint(spec, nev, ncv, precision=FP64, **kw):

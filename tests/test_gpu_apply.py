@@ -108,3 +108,111 @@ def test_capacitance_inverse_cluster_equals_per_pivot(klst, nx, monkeypatch):
     r = 4 * nx
     assert (c2 - c1) - (c1 - c0) >= r - 2, ((c1 - c0), (c2 - c1))
     assert np.array_equal(y1, y2)
+
+
+def test_refinement_shortfall_reports_erefine(klst):
+    """MIXED factors: an apply whose refinement cannot reach refine_tol within max_refine sweeps raises
+    the factor's flag; klst_factor_check reports KLST_EREFINE once and clears it, and klst_eigs returns
+    KLST_EREFINE with every output filled.  A reachable tolerance reports KLST_OK."""
+    spec, sigma = SMALL[2]
+    P = klst.Pencil(spec)
+    F = P.factor(sigma, precision=klst.MIXED)
+    X = to_dev(wl.random_vectors(P.n, 2, 5))
+    F.set_refine(6, 1e-11)
+    F.apply(X)
+    assert F.check() == klst.KLST_OK
+    F.set_refine(1, 1e-30)  # unreachable: one sweep cannot bring ||r|| / ||B x|| to 1e-30
+    Y = to_host(F.apply(X))
+    assert np.all(np.isfinite(Y))
+    assert F.check() == klst.KLST_EREFINE
+    assert F.check() == klst.KLST_OK  # the flag was cleared
+    om, vec, res, info = F.eigs(6, 20, tol=1e-8, max_refine=2, refine_tol=1e-30, seed=3, check=False)
+    assert info["status"] == klst.KLST_EREFINE
+    assert info["nconv"] == 6 and np.all(np.isfinite(om)) and np.all(np.isfinite(res))
+    assert info["max_refine_resid"] > 1e-30
+
+
+def _pool_used():
+    import torch
+    from cuda.bindings import runtime as rt
+    torch.cuda.synchronize()
+    err, pool = rt.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+    e, v = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+    return int(v)
+
+
+def test_injected_allocation_failure_returns_enomem(klst):
+    """Host-injected device allocation failure at every allocation of build + factor + eigs in turn:
+    each failing call returns KLST_ENOMEM with no handle, frees what it had taken (the pool's in-use
+    bytes return to the baseline), and the next full solve gives the same eigenvalues as before."""
+    spec, sigma = wl.tiny(nx=12, qx=6, qy=4, mach=3.0, beta=0.5), 0.1j
+    for prec in (klst.FP64, klst.MIXED):
+        ref = klst.Pencil(spec).factor(sigma, precision=prec).eigs(6, 20, tol=1e-11, seed=9)[0]
+        base = _pool_used()
+        ok_at = None
+        for n in range(200):
+            klst.fail_alloc_after(n)
+            try:
+                P = klst.Pencil(spec)
+                F = P.factor(sigma, precision=prec)
+                om = F.eigs(6, 20, tol=1e-11, seed=9)[0]
+            except klst.KlstError as e:
+                assert e.code == klst.KLST_ENOMEM, (n, e)
+                assert "out of memory" in str(e) or "cudaMalloc" in str(e), str(e)
+                continue
+            finally:
+                klst.fail_alloc_after(-1)
+                import gc
+                gc.collect()
+            ok_at = n
+            assert np.array_equal(om, ref)
+            del F, P
+            break
+        assert ok_at is not None and ok_at >= 10, ok_at  # the solve makes at least ten allocations
+        import gc
+        gc.collect()
+        assert _pool_used() == base
+
+
+# Nx = 128 with a small velocity grid: the full-size tile path (the block Gauss-Jordan of a 128 x 128
+# block leaves shared memory and works in global memory, and r = 4 Nx = 512 takes the per-pivot
+# capacitance inverse) at sizes the dense oracle still factors in seconds.
+NX128 = [
+    (wl.tiny(nx=128, qx=4, qy=2, mach=3.0, beta=1.0), 0.05 + 0.2j),
+    (wl.tiny(nx=128, qx=6, qy=4, mach=4.0, beta=0.6), 0.1j),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "mixed", "df64"])
+@pytest.mark.parametrize("spec,sigma", NX128, ids=["128x4x2", "128x6x4"])
+def test_apply_nx128_matches_dense_lu(klst, spec, sigma, prec):
+    """Element by element against the oracle's dense LU solve of A - sigma B at Nx = 128."""
+    d, A, B, si = _oracle(spec, sigma)
+    X = wl.random_vectors(A.shape[0], 2, 23)
+    ref = np.stack([si.apply(x) for x in X])
+    cond = cond1(A - sigma * B, si.lu)
+    tol = max(1e-12, 64 * cond * 2.220446049250313e-16)
+    P = klst.Pencil(spec)
+    F = P.factor(sigma, precision=prec)
+    if prec == 1:
+        F.set_refine(6, 1e-15)
+    Y = to_host(F.apply(to_dev(X)))
+    err = np.abs(Y - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert np.all(err <= tol), (err, tol, cond)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "mixed", "df64"])
+def test_apply_c3_paper_shape_residual(klst, prec):
+    """The paper's own 281,088-unknown shape (Nx = 61, 48 x 48): the oracle's matrix-free rows give
+    ||(A - sigma B) y - B x|| / ||B x|| at the float64 level."""
+    spec, es = wl.c3_paper_shape()
+    d = gas.pencil_data(spec.as_dict())
+    P = klst.Pencil(spec)
+    F = P.factor(es.sigma, precision=prec)
+    x = wl.start_vector(P.n, 22)
+    y = to_host(F.apply(to_dev(x)))
+    r = pencil.apply_A(spec.as_dict(), d, y) - es.sigma * pencil.apply_B(d, y) - pencil.apply_B(d, x)
+    rel = np.linalg.norm(r) / np.linalg.norm(pencil.apply_B(d, x))
+    normA = np.abs(d["Dx"]).sum(axis=1).max() * np.abs(d["xi_x"]).max() + np.abs(d["nu"]).max() + abs(es.sigma)
+    bound = 1e3 * 2.220446049250313e-16 * normA * np.linalg.norm(y) / np.linalg.norm(pencil.apply_B(d, x))
+    assert rel <= max(bound, 1e-12), (rel, bound)

@@ -54,8 +54,10 @@ def test_c1_against_golden(klst, prec, arith):
     A, B = pencil.assemble_dense(spec.as_dict(), d)
     P = klst.Pencil(spec)
     F = P.factor(es.sigma, precision=prec)
+    # MIXED factors with the df64 residual (arith 1) refine to the double-float floor (~1e-12)
+    rtol = 1e-11 if (prec, arith) == (1, 1) else 1e-12
     om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)), vectors=True,
-                                arith=arith)
+                                arith=arith, refine_tol=rtol)
     _check_against(om, ref, kap, pencil_norm2_est(d, spec.beta))
     assert np.max(res) <= 1e-10
     r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
@@ -73,8 +75,9 @@ def test_c2_against_golden(klst, prec, arith):
     normA = pencil_norm2_est(d, spec.beta)
     P = klst.Pencil(spec)
     F = P.factor(es.sigma, precision=prec)
+    rtol = 1e-11 if (prec, arith) == (1, 1) else 1e-12
     om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)), vectors=True,
-                                arith=arith)
+                                arith=arith, refine_tol=rtol)
     _check_against(om, ref, kap, normA)
     assert np.max(res) <= 1e-10
     r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
@@ -127,3 +130,38 @@ def test_invalid_options_rejected(klst):
     with pytest.raises(klst.KlstError) as ei:
         F.eigs(20, 21)
     assert ei.value.code == klst.KLST_EINVAL
+
+
+@pytest.mark.parametrize("prec,arith", [(0, 0), (1, 0), (2, 1)], ids=["fp64", "mixed", "df64"])
+def test_nx128_against_interior_oracle(klst, prec, arith):
+    """Nx = 128 (the full-size block and capacitance paths), 4 x 2 velocity nodes (n = 2,048): the
+    12 eigenvalues nearest sigma against the oracle's interior standard problem at 1e-8."""
+    spec = wl.tiny(nx=128, qx=4, qy=2, mach=3.0, beta=1.0)
+    sigma = 0.05 + 0.2j
+    d = gas.pencil_data(spec.as_dict())
+    A, B = pencil.assemble_dense(spec.as_dict(), d)
+    lam, X, kap = eig.interior(A, pencil.boundary_rows(d))
+    idx = eig.nearest(lam, sigma, 12)
+    P = klst.Pencil(spec)
+    F = P.factor(sigma, precision=prec)
+    om, vec, res, info = F.eigs(12, 40, tol=1e-13, v0=to_dev(wl.start_vector(P.n, 4)), vectors=True, arith=arith)
+    _check_against(om, lam[idx], kap[idx], pencil_norm2_est(d, spec.beta))
+    assert np.max(res) <= 1e-10
+    r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
+    assert np.max(r) <= 1e-10
+
+
+def test_c3_paper_shape_checked_by_oracle_operator(klst):
+    """The paper's own 281,088-unknown shape (Nx = 61, 48 x 48, M = 4): 40 eigenpairs, each checked
+    with the oracle's matrix-free float64 A and B (||A q - omega B q|| <= 1e-10, ||q|| = 1)."""
+    spec, es = wl.c3_paper_shape()
+    P = klst.Pencil(spec)
+    F = P.factor(es.sigma, precision=0)
+    om, vec, res, info = F.eigs(es.nev, es.ncv, tol=2e-11, conv=klst.CONV_RESID, keep=70,
+                                v0=to_dev(wl.start_vector(spec.n, es.seed)), vectors=True)
+    assert info["status"] == 0 and len(om) == es.nev
+    assert np.max(res) <= 1e-10
+    d = gas.pencil_data(spec.as_dict())
+    r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
+    assert np.max(r) <= 1e-10, np.max(r)
+    assert np.max(np.abs(r - res)) <= 1e-11

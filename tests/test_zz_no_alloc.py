@@ -49,6 +49,7 @@ def _pool_high_minus_current():
     the mark: a call that allocated (and freed) pool memory in between leaves a positive value."""
     import torch
     from cuda.bindings import runtime as rt
+    from cuda.bindings.driver import cuuint64_t as _cuuint64
     dev = torch.cuda.current_device()
     err, pool = rt.cudaDeviceGetDefaultMemPool(dev)
     assert err == rt.cudaError_t.cudaSuccess
@@ -57,7 +58,7 @@ def _pool_high_minus_current():
 
     def reset():
         torch.cuda.synchronize()
-        (e,) = rt.cudaMemPoolSetAttribute(pool, attr_hi, rt.cuuint64_t(0))
+        (e,) = rt.cudaMemPoolSetAttribute(pool, attr_hi, _cuuint64(0))
         assert e == rt.cudaError_t.cudaSuccess
 
     def read():
