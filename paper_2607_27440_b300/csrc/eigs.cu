@@ -394,6 +394,7 @@ struct EigsWork {
     int *gate = nullptr, *reorth = nullptr;
     double2 *h = nullptr, *dpart = nullptr, *X = nullptr, *Z = nullptr, *R = nullptr, *om = nullptr;
     double2 *wbuf = nullptr, *vcur = nullptr;
+    char* ozws = nullptr;         // float64 basis: workspace of the tensor-core rotation
     double2 *mw = nullptr, *mp = nullptr;
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
@@ -483,6 +484,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     // the whole workspace is one stream-ordered allocation: concurrent solves on many host
     // threads otherwise queue on the allocator for dozens of small arrays each
     const bool dfm = o->arith == KLST_ARITH_DF64;
+    // float64 basis: the basis rotations run as float64-accurate tensor-core GEMMs (2 ncv <= 256;
+    // KLST_NO_TC=1 selects the float64 CUDA-core rotation)
+    const char* notc = getenv("KLST_NO_TC");
+    const bool use_tc = !dfm && 2 * m <= 256 && n <= 0x7FFFFFFF && !(notc && notc[0] == '1');
     const int ldp = m + 2;
     const int log_cap = 31 * m * m;
     {
@@ -524,6 +529,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
                 sc.take(W.onrm, 4);
                 sc.take(W.ocnt, 4);
             }
+            if (use_tc) sc.take(W.ozws, oz_workspace_bytes((int)n, 2 * std::max(keep, nev), 2 * m));
             if (pass == 0) {
                 if ((e = dmalloc(&W.slab, sc.off, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
                 sc.base = static_cast<char*>(W.slab);
@@ -709,6 +715,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         }
         if (hconv < 0 || (hst.flags & ST_NOCONV_QR)) { set_error("small Schur QR iteration did not converge"); return fail(KLST_ENOCONV); }
         if (hst.flags & ST_BREAKDOWN) { set_error("Arnoldi breakdown (invariant subspace found)"); return fail(KLST_ENOCONV); }
+        if (hst.flags & ST_TIMEOUT) { set_error("tensor-core rotation: a bounded device wait gave up"); return fail(KLST_ETIMEOUT); }
         nconv = hconv;
         if (nconv >= nev) { converged = true; break; }
         if (restarts >= o->max_restarts) break;
@@ -717,9 +724,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             cudaEventRecord(evs[3 * (m + 1) + 2], s);
             dim3 grd(std::max(1, nblk / std::max(1, (keep + 7) / 8)), (keep + 7) / 8);
             prof_begin("rotate", s);
-            if (dfm) k_rotate_df<float4><<<grd, 256, sizeof(double2) * m * 8, s>>>(V4(V), n, m, W.Q, m, keep, V4(Valt), n, n);
-            else k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n);
-            klst::note_launch();
+            if (dfm) { k_rotate_df<float4><<<grd, 256, sizeof(double2) * m * 8, s>>>(V4(V), n, m, W.Q, m, keep, V4(Valt), n, n); klst::note_launch(); }
+            else if (use_tc) { if ((rc = oz_rotate(V, n, m, W.Q, keep, Valt, W.ozws, f->status, s)) != KLST_OK) return fail(rc); }
+            else { k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Q, m, keep, Valt, n, n); klst::note_launch(); }
             prof_end("rotate", s);
             KLST_CK_LAUNCH();
             KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
@@ -756,9 +763,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     {
         dim3 grd(std::max(1, nblk / std::max(1, (nret + 7) / 8)), (nret + 7) / 8);
-        if (dfm) k_rotate_df<double2><<<grd, 256, sizeof(double2) * m * 8, s>>>(V4(V), n, m, W.Ysel, m, nret, X, n, n);
-        else k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n);
-        klst::note_launch();
+        if (dfm) { k_rotate_df<double2><<<grd, 256, sizeof(double2) * m * 8, s>>>(V4(V), n, m, W.Ysel, m, nret, X, n, n); klst::note_launch(); }
+        else if (use_tc) { if ((rc = oz_rotate(V, n, m, W.Ysel, nret, X, W.ozws, f->status, s)) != KLST_OK) return fail(rc); }
+        else { k_rotate<<<grd, 256, sizeof(double2) * m * 8, s>>>(V, n, m, W.Ysel, m, nret, X, n, n); klst::note_launch(); }
         KLST_CK_LAUNCH();
     }
     if ((rc = apply_T(f, X, Z, nret, s)) != KLST_OK) return fail(rc);
@@ -822,6 +829,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     f->refine_tol = prev_rtol;
     f->arith = prev_arith;
     if (!converged) { set_error("only %d of %d eigenpairs converged after %d restarts", nconv, nev, restarts); return KLST_ENOCONV; }
+    if (fst.flags & ST_TIMEOUT) {
+        set_error("tensor-core rotation: a bounded device wait gave up");
+        return KLST_ETIMEOUT;
+    }
     if (fst.flags & ST_REFINE) {
         set_error("mixed-precision refinement missed refine_tol in at least one apply (worst %.3g after %d sweeps); "
                   "the eigenpairs and their explicit residuals are returned", worst, o->max_refine);

@@ -68,6 +68,12 @@ int launch_schur(const SchurArgs& a, cudaStream_t s);    // double-float sweeps 
 int launch_schur64(const SchurArgs& a, cudaStream_t s);  // float64 sweeps (schur64.cu)
 void launch_schur_post(const SchurArgs& a, cudaStream_t s);
 
+// float64-accurate GEMMs on the tensor cores (ozaki.cu)
+size_t oz_workspace_bytes(int M, int N, int K);
+// V'[:, 0:keep] = V[:, 0:m] Q[:, 0:keep]: complex, column-major (ld n for V, V'; m for Q); 2 m <= 256
+int oz_rotate(const double2* V, int64_t n, int m, const double2* Q, int keep, double2* Vout, void* ws, Status* st,
+              cudaStream_t s);
+
 // float64 Gram-Schmidt of one Arnoldi step (orth64.cu)
 struct Orth64Args {
     double2* V;        // basis, n x (m + 1) column-major (ld n)

@@ -19,35 +19,53 @@ static_assert(sizeof(Rot64) == sizeof(Rot), "the rotation log is shared by both 
 
 __device__ __forceinline__ double cabs1_64(double2 a) { return fabs(a.x) + fabs(a.y); }
 
-// x' = c x + s y, y' = c y - conj(s) x (real c)
+// x' = c x + s y, y' = c y - conj(s) x (real c).  The terms without x are formed first, so a
+// caller that carries y' into the next rotation as its x waits on two float64 operations only.
 __device__ __forceinline__ void crot64(double2& x, double2& y, double c, double2 s) {
-    const double2 tx = make_double2(fma(c, x.x, s.x * y.x - s.y * y.y), fma(c, x.y, s.x * y.y + s.y * y.x));
-    const double2 ty = make_double2(fma(c, y.x, -(s.x * x.x + s.y * x.y)), fma(c, y.y, -(s.x * x.y - s.y * x.x)));
+    const double2 sy = make_double2(fma(s.x, y.x, -s.y * y.y), fma(s.x, y.y, s.y * y.x));
+    const double2 cy = make_double2(c * y.x, c * y.y);
+    const double2 tx = make_double2(fma(c, x.x, sy.x), fma(c, x.y, sy.y));
+    const double2 ty = make_double2(fma(-s.x, x.x, fma(-s.y, x.y, cy.x)), fma(-s.x, x.y, fma(s.y, x.x, cy.y)));
     x = tx;
     y = ty;
 }
 
+// 1 / sqrt(x) for a normal x > 0 to float64 accuracy with four dependent float64 operations: x is
+// scaled by an even power of two into [1, 4) (integer operations on its bits), the float32
+// reciprocal square root gives y0 with |1 - x y0^2| = e ~ 2^-22, and the exact value
+// y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3 e^2/8 + O(e^3)) is taken to second order (error ~2^-66).
+// The float32 value and the float64 it feeds are built from bits, off the float64 pipe.
+__device__ __forceinline__ double rsqrt64(double x) {
+    const long long b = __double_as_longlong(x);
+    const int k = ((int)((b >> 52) & 0x7FF) - 1023) >> 1;                 // x = xm 4^k, xm in [1, 4)
+    const double xm = __longlong_as_double(b - ((long long)(2 * k) << 52));
+    const long long bm = __double_as_longlong(xm);
+    const float xf = __uint_as_float((unsigned)(((bm >> 52) - 1023 + 127) << 23) | (unsigned)((bm >> 29) & 0x7FFFFF));
+    const unsigned yb = __float_as_uint(rsqrtf(xf));
+    const double y0 = __longlong_as_double(((long long)(((yb >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                           ((long long)(yb & 0x7FFFFF) << 29));
+    const double e = fma(-(xm * y0), y0, 1.0);
+    const double y = fma(y0 * e, fma(0.375, e, 0.5), y0);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));  // y 2^-k
+}
+
 // [c s; -conj(s) c] [f; g] = [r; 0] with real c = |f| / r, s = f conj(g) / (|f| r),
-// r = sqrt(|f|^2 + |g|^2) (the LAPACK zlartg convention).  f and g are first scaled by one power of
-// two (exact) so the squares stay far from the float64 limits.
+// r = sqrt(|f|^2 + |g|^2) (the LAPACK zlartg convention), from two independent reciprocal square
+// roots (no float64 division or square root on the dependent chain).  The entries of the
+// Krylov-Schur matrix are far inside the float64 range, so no scaling is needed; an |f|^2 or |g|^2
+// below 1e-290 is treated as zero.
 __device__ void givens64(double2 f, double2 g, double& c, double2& s) {
-    const double mg = fmax(fabs(g.x), fabs(g.y)), mf = fmax(fabs(f.x), fabs(f.y));
-    if (mg == 0.0 || mg < 1e-300 * mf) { c = 1.0; s = make_double2(0.0, 0.0); return; }
-    int e;
-    frexp(fmax(mf, mg), &e);
-    const double sc = ldexp(1.0, -e);
-    f = make_double2(f.x * sc, f.y * sc);
-    g = make_double2(g.x * sc, g.y * sc);
     const double ag2 = abs2(g), af2 = abs2(f);
-    if (af2 < 1e-200) {  // |f| negligible next to |g|: c = 0, s = conj(g) / |g|
-        const double ig = 1.0 / sqrt(ag2);
+    if (!(ag2 > 1e-290)) { c = 1.0; s = make_double2(0.0, 0.0); return; }
+    if (!(af2 > 1e-290)) {  // |f| negligible: c = 0, s = conj(g) / |g|
+        const double ig = rsqrt64(ag2);
         c = 0.0;
         s = make_double2(g.x * ig, -g.y * ig);
         return;
     }
-    const double r = sqrt(af2 + ag2), af = sqrt(af2);
-    c = af / r;
-    const double q = 1.0 / (af * r);
+    const double ir = rsqrt64(af2 + ag2), iaf = rsqrt64(af2);
+    c = (af2 * iaf) * ir;
+    const double q = iaf * ir;
     s = make_double2((f.x * g.x + f.y * g.y) * q, (f.y * g.x - f.x * g.y) * q);
 }
 

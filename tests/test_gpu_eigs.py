@@ -165,3 +165,22 @@ def test_c3_paper_shape_checked_by_oracle_operator(klst):
     r = eig.residuals(spec.as_dict(), d, om, to_host(vec).T)
     assert np.max(r) <= 1e-10, np.max(r)
     assert np.max(np.abs(r - res)) <= 1e-11
+
+
+def test_tensor_core_rotation_matches_cuda_core_rotation(klst, monkeypatch):
+    """The float64 basis rotations through the tensor-core GEMM (default) and through the float64
+    CUDA-core kernel (KLST_NO_TC=1) give the same eigenpairs to float64 rounding (C2, 40 pairs)."""
+    spec, es = wl.c2()
+    P = klst.Pencil(spec)
+    v0 = to_dev(wl.start_vector(P.n, es.seed))
+    out = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("KLST_NO_TC", env)
+        F = P.factor(es.sigma, precision=0)
+        om, vec, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=v0, vectors=False)
+        out.append((om, res, info))
+    (o1, r1, i1), (o2, r2, i2) = out
+    assert i1["restarts"] == i2["restarts"] and i1["applies"] == i2["applies"]
+    perm = eig.match(o2, o1)
+    assert np.max(np.abs(o1[perm] - o2) / np.abs(o2)) <= 1e-11
+    assert np.max(r1) <= 1e-10 and np.max(r2) <= 1e-10
