@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 latency figures")
-    ap.add_argument("--serve-rate", type=float, default=5.0, help="Poisson arrival rate of the serving run (1/s)")
-    ap.add_argument("--serve-window", type=float, default=15.0, help="arrival window of the serving run (s)")
+    ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
+                    help="Poisson arrival rates of the serving runs (1/s), comma-separated")
+    ap.add_argument("--serve-window", type=float, default=6.0, help="arrival window of each serving run (s)")
     return ap.parse_args()
 
 
@@ -167,6 +168,9 @@ PATH_DTYPE = {
             "Householder/QR Schur step, residuals; first-pass Gram-Schmidt coefficients on float32 pipes, completed by "
             "the float64 second pass)",
 }
+# per-path solver settings: MIXED refines every apply at most twice (two sweeps reach ||r|| / ||Bx||
+# <= 1e-12 at C3; a miss is reported as KLST_EREFINE and the pairs still face the residual check)
+PATH_OPTS = {"mixed": {"max_refine": 2, "refine_tol": 1e-12}, "fp64": {}, "df64": {}}
 # statuses whose eigenpairs are returned (each still counts only with explicit residual <= 1e-10)
 RETURNED = (0, -4, -5)  # KLST_OK, KLST_ENOCONV, KLST_EREFINE
 
@@ -300,7 +304,8 @@ def run_ours(args):
         P = klst.Pencil(spec)
         F = P.factor(sigma, precision=prec)
         om, vec, res, info = F.eigs(es.nev, es.ncv, tol=CONV_TOL, conv=klst.CONV_RESID, max_restarts=es.max_restarts,
-                                    v0=v0_dev, vectors=vec_out, check=False, keep=es.keep, arith=arith)
+                                    v0=v0_dev, vectors=vec_out, check=False, keep=es.keep, arith=arith,
+                                    **PATH_OPTS[path])
         good = int(np.sum(res <= RESID_MAX)) if info["status"] in RETURNED else 0
         return good, om, vec, res, info, P, F
 
@@ -448,12 +453,16 @@ def run_ours(args):
     }
     if not args.no_small:
         try:
-            line["small_configs"] = small_configs(klst)
+            line["small_configs"] = small_configs(klst, args.precision)
         except Exception as ex:  # the headline line must still print
             line["small_configs"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_batch:
         line["batched"] = batched_sweep(klst, compare=not args.no_compare)
-        line["serving"] = serving_run(klst, args.serve_rate, args.serve_window)
+        rates = [float(r) for r in args.serve_rates.split(",") if r]
+        runs = [serving_run(klst, r, args.serve_window, args.precision) for r in rates]
+        line["serving"] = {"path": args.precision, "window_s": args.serve_window,
+                           "workload": runs[0]["workload"] if runs else None,
+                           "per_rate": [{k: v for k, v in r.items() if k != "workload"} for r in runs]}
     if args.no_cpu:
         line["cpu_baseline"] = None
     else:
@@ -465,10 +474,10 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def small_configs(klst, reps=100):
-    """C1 and C2, whose factors fit in L2 and whose solves are latency bound: one df64 solve on a
-    side stream (so each Arnoldi step is one CUDA graph launch), and the mean shift-invert apply
-    time over `reps` applies, both timed with CUDA events on that stream."""
+def small_configs(klst, path="fp64", reps=100):
+    """C1 and C2, whose factors fit in L2 and whose solves are latency bound: one solve of the given
+    path on a side stream (so each Arnoldi step is one CUDA graph launch), and the mean shift-invert
+    apply time over `reps` applies, both timed with CUDA events on that stream."""
     import torch
 
     from paper_2607_27440_b300 import workloads as wl
@@ -478,11 +487,12 @@ def small_configs(klst, reps=100):
     with torch.cuda.stream(st):
         for name in ("c1", "c2"):
             spec, es = getattr(wl, name)()
+            prec, arith = (getattr(klst, a) for a in PATHS[path])
             P = klst.Pencil(spec, stream=st)
-            F = P.factor(es.sigma, precision=klst.DF64, stream=st)
+            F = P.factor(es.sigma, precision=prec, stream=st)
             v0 = torch.from_numpy(wl.start_vector(spec.n, es.seed)).to(torch.complex128).to("cuda")
             kw = dict(tol=CONV_TOL, conv=klst.CONV_RESID, max_restarts=es.max_restarts, v0=v0, check=False,
-                      keep=es.keep, arith=klst.ARITH_DF64, stream=st)
+                      keep=es.keep, arith=arith, stream=st, **PATH_OPTS[path])
             F.eigs(es.nev, es.ncv, **kw)  # warm-up
             st.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -507,7 +517,7 @@ def small_configs(klst, reps=100):
                          "restarts": info["restarts"], "applies": info["applies"],
                          "kernels_per_arnoldi_step": launches / max(info["applies"], 1),
                          "apply_us": e0.elapsed_time(e1) * 1e3 / reps,
-                         "launch_mode": "one CUDA graph launch per Arnoldi step (side stream)"}
+                         "path": path, "launch_mode": "one CUDA graph launch per Arnoldi step (side stream)"}
             F.close()
             P.close()
     return out
@@ -521,11 +531,11 @@ def batched_sweep(klst, compare=True):
     out = {"workload": "256 independent Mott-Smith pencils, Mach U[1.2,4], beta U[0,2], Nx in {32,48,64,96}, "
                        "Nxi in {8x6,12x8,16x12,16x16}, sigma = 0.1i(1+U[0,1]), 20 eigenvalues, ncv 40",
            "workers": 16}
-    for name in PATHS if compare else ("df64",):
+    for name in PATHS if compare else ("fp64",):
         prec, arith = (getattr(klst, a) for a in PATHS[name])
         t0 = time.perf_counter()
         om, res, st, infos = klst.batch_eigs(specs, sig, 20, 40, precision=prec, nworkers=16, tol=CONV_TOL,
-                                             conv=klst.CONV_RESID, seed=4, arith=arith)
+                                             conv=klst.CONV_RESID, seed=4, arith=arith, **PATH_OPTS[name])
         dt = time.perf_counter() - t0
         good = int(np.sum(res <= RESID_MAX))
         out[name] = {"eigenpairs_per_s": good / dt, "s": dt, "good_eigenpairs": good,
@@ -533,9 +543,10 @@ def batched_sweep(klst, compare=True):
     return out
 
 
-def serving_run(klst, rate, window):
+def serving_run(klst, rate, window, path="fp64"):
     """Poisson arrivals of mixed-size requests (n log-uniform in [1,536, 281,088]); latency submit -> done."""
     from paper_2607_27440_b300 import workloads as wl
+    prec, arith = (getattr(klst, a) for a in PATHS[path])
     reqs = wl.serving_requests(rate, window, seed=5)
     S = klst.Server(hbm_budget_bytes=200 << 30, max_slots=8)
     t0 = time.perf_counter()
@@ -543,8 +554,8 @@ def serving_run(klst, rate, window):
     for ta, spec, z in reqs:
         while time.perf_counter() - t0 < ta:
             time.sleep(0.0005)
-        tickets.append(S.submit(spec, z, 20, 40, precision=klst.DF64, tol=CONV_TOL, conv=klst.CONV_RESID, seed=5,
-                                arith=klst.ARITH_DF64))
+        tickets.append(S.submit(spec, z, 20, 40, precision=prec, tol=CONV_TOL, conv=klst.CONV_RESID, seed=5,
+                                arith=arith, **PATH_OPTS[path]))
     lats, good, fails = [], 0, 0
     for t in tickets:
         om, res, info, lat, code = S.poll(t, wait=True)
@@ -561,26 +572,48 @@ def serving_run(klst, rate, window):
             "workload": "M in {1.2,3,4}, n log-uniform [1,536, 281,088], sigma U[0,0.2]+iU[0,0.3], 20 eigenpairs"}
 
 
+def cpu_verify_main(path):
+    """Child process of cpu_baseline_c3: oracle assembly + matrix-free residuals of the stored pairs."""
+    from oracle import eig, gas
+    from paper_2607_27440_b300 import workloads as wl
+    z = np.load(path)
+    spec, _ = wl.c3()
+    t0 = time.perf_counter()
+    d = gas.pencil_data(spec.as_dict())
+    r = eig.residuals(spec.as_dict(), d, z["om"], z["X"])
+    dt = time.perf_counter() - t0
+    print(json.dumps({"s": dt, "verified": int(np.sum(r <= RESID_MAX)), "max_resid": float(np.max(r))}), flush=True)
+
+
 def cpu_baseline_c3(spec, om, vec_host):
     """The oracle at the bench's own workload (n = 281,088): no oracle eigensolve exists at this size
     (the dense A alone would be 1.26 TB, and a sparse LU fills to the paper's terabyte problem), so the
     oracle's share of the job is assembly of the pencil tables plus the matrix-free float64
-    verification ||A q - omega B q|| of the GPU's eigenpairs.  Timed with every host core and with one
-    thread (BLAS threads capped by threadpoolctl); value = verified eigenpairs per second."""
-    from threadpoolctl import threadpool_limits
-
-    from oracle import eig, gas
+    verification ||A q - omega B q|| of the GPU's eigenpairs.  Timed in child processes with every
+    host core and with one thread (BLAS and OpenMP threads set through the environment before numpy
+    loads); value = verified eigenpairs per second."""
+    import subprocess
+    import tempfile
     cores = len(os.sched_getaffinity(0))
-    X = vec_host.numpy().T  # n x nev
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, om=om, X=vec_host.numpy().T)
     out = {}
-    for label, nthreads in (("all_cores", cores), ("one_thread", 1)):
-        with threadpool_limits(limits=nthreads):
-            t0 = time.perf_counter()
-            d = gas.pencil_data(spec.as_dict())
-            r = eig.residuals(spec.as_dict(), d, om, X)
-            dt = time.perf_counter() - t0
-        out[label] = {"s": dt, "threads": nthreads, "eigenpairs_per_s": len(om) / dt,
-                      "verified": int(np.sum(r <= RESID_MAX)), "max_resid": float(np.max(r))}
+    try:
+        for label, nthreads in (("all_cores", cores), ("one_thread", 1)):
+            env = dict(os.environ)
+            for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                env[k] = str(nthreads)
+            res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-verify", path], env=env,
+                                 capture_output=True, text=True, timeout=900)
+            line = [l for l in res.stdout.splitlines() if l.startswith("{")]
+            if res.returncode != 0 or not line:
+                raise RuntimeError(f"oracle verification failed: {res.stderr[-500:]}")
+            rec = json.loads(line[-1])
+            out[label] = {"s": rec["s"], "threads": nthreads, "eigenpairs_per_s": len(om) / rec["s"],
+                          "verified": rec["verified"], "max_resid": rec["max_resid"]}
+    finally:
+        os.remove(path)
     a = out["all_cores"]
     return {"value": a["eigenpairs_per_s"], "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
             "sample": (f"oracle at n=281,088 (C3): assembly of the pencil tables + matrix-free float64 residual "
@@ -643,6 +676,9 @@ def run_reference(args):
 
 
 if __name__ == "__main__":
+    if len(sys.argv) == 3 and sys.argv[1] == "--cpu-verify":
+        cpu_verify_main(sys.argv[2])
+        sys.exit(0)
     a = parse()
     if a.impl == "reference":
         run_reference(a)

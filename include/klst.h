@@ -106,7 +106,10 @@ typedef struct {
     double t_orth_ms;     /* device time in Gram-Schmidt (graph mode: applies + Gram-Schmidt) */
     double t_restart_ms;  /* device time in Schur restarts and basis rotations */
     double t_schur_ms;    /* of which the small Schur/reorder step */
-    int32_t reorths;      /* Arnoldi steps that needed the second Gram-Schmidt pass (DGKS test) */
+    int32_t reorths;      /* Arnoldi steps that ran the second Gram-Schmidt pass (float64 basis: every step) */
+    int32_t schur_sweeps; /* shifted QR sweeps of the small Schur step, summed over restarts (float64 basis) */
+    int32_t schur_swaps;  /* adjacent swaps of the reordering, summed over restarts (float64 basis) */
+    int64_t schur_rotations; /* Givens rotations logged by the Schur step, summed over restarts */
 } klst_eigs_info;
 
 typedef struct klst_pencil_s* klst_pencil;
@@ -216,6 +219,26 @@ int klst_apply_pencil(klst_pencil p, const void* x, void* y, int32_t nrhs, const
 int klst_apply_pencil_noalloc(klst_pencil p, const void* x, void* y, int32_t nrhs, const double* omega,
                               klst_stream stream);
 size_t klst_apply_pencil_noalloc_capacity(void);
+
+/*
+ * klst_base_noneq -- the base flow's translational non-equilibrium measure (Sec. 5, Eq. L2norm):
+ * eneq_host[j] = sqrt( sum_k W_k (g_c(x_j, xi_k) - g_c^e(x_j, xi_k))^2 ) for the nx collocation points,
+ * with g_c the base reduced distribution, g_c^e its discrete local equilibrium and W_k the full-line
+ * Gauss-Hermite product weights (0 for an EQ base).  eneq_host: host float64[nx].  Synchronising.
+ */
+int klst_base_noneq(klst_pencil p, double* eneq_host);
+
+/*
+ * klst_eigvec_macro -- macroscopic perturbations of nvec vectors q (device complex128, n x nvec
+ * column-major, e.g. the evecs of klst_eigs): macro_host (host complex128 [nvec][4][nx]) receives
+ * (rho^, u^, v^, E^)(x_j), the perturbation moments of Sec. 2.2 (rho^ = sum W g^, u^ = sum W (xi_x - u)
+ * g^ / rho, v^ = sum W xi_y g^ / rho, E^ = [sum W (|xi|^2 - 2E) g^ + sum W h^] / (2 rho)), and umax_host
+ * (host float64[nvec], may be NULL) max_j |U^| with |U^| = sqrt(|u^|^2 + |v^|^2) (Eq. Unormpert), the
+ * normalisation the paper applies to velocity eigenvectors.  Errors: KLST_EINVAL, KLST_ENOMEM.
+ * Synchronising.
+ */
+int klst_eigvec_macro(klst_pencil p, const void* q, int32_t nvec, double* macro_host, double* umax_host,
+                      klst_stream stream);
 
 /*
  * klst_factor_shift -- factor A - sigma B for the shift-and-invert transform

@@ -21,26 +21,33 @@ int pencil_rows_blocks(klst_pencil p);
 // z_g += K_k^{-1}[j, :] s0, z_h += K_k^{-1}[j, :] s1 for thread row j (Kk points at column 0 of row
 // j in the transposed storage, stride nx).  The loads of the next four entries are issued before
 // the multiply-adds of the current four, so eight loads per thread are in flight.
+// D entries per group: the next group's D loads are issued before the current group's
+// multiply-adds, so 2 D loads per thread are in flight.  The 8-byte complex64 entries use D = 8
+// (the HBM-bound float32 solves need more bytes in flight per thread), the 16-byte ones D = 4.
+template <typename C> struct GemvDepth { static constexpr int D = 4; };
+template <> struct GemvDepth<float2> { static constexpr int D = 8; };
+
 template <typename C>
 __device__ __forceinline__ void block_gemv2(const C* __restrict__ Kk, int nx, const C* s0, const C* s1, C& zg, C& zh) {
-    C ka[4];
+    constexpr int D = GemvDepth<C>::D;
+    C ka[D];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) ka[u] = (u < nx) ? Kk[(size_t)u * nx] : czero<C>();
+    for (int u = 0; u < D; ++u) ka[u] = (u < nx) ? Kk[(size_t)u * nx] : czero<C>();
     int m = 0;
-    for (; m + 4 <= nx; m += 4) {
-        C kb[4];
+    for (; m + D <= nx; m += D) {
+        C kb[D];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) kb[u] = (m + 4 + u < nx) ? Kk[(size_t)(m + 4 + u) * nx] : czero<C>();
+        for (int u = 0; u < D; ++u) kb[u] = (m + D + u < nx) ? Kk[(size_t)(m + D + u) * nx] : czero<C>();
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < D; ++u) {
             cfma(zg, ka[u], s0[m + u]);
             cfma(zh, ka[u], s1[m + u]);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ka[u] = kb[u];
+        for (int u = 0; u < D; ++u) ka[u] = kb[u];
     }
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
+    for (int u = 0; u < D - 1; ++u)
         if (m + u < nx) {
             cfma(zg, ka[u], s0[m + u]);
             cfma(zh, ka[u], s1[m + u]);
@@ -252,10 +259,23 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
     for (int it = 0; it <= f->max_refine; ++it) {
         const int last = it == f->max_refine;
         prof_begin("refine_residual", s);
+        prof_begin("refine_moments", s);
         rc = moments_dev(p, y, p->n, nrhs, f->t, f->tpart, f->ngroups, s, f->done);
+        prof_end("refine_moments", s);
         if (rc) return rc;
-        rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done,
-                             f->arith);
+        if (f->tc_resid && !f->arith) {
+            prof_begin("refine_dx_tc", s);
+            rc = oz_dx_apply(p->dx_oz, p->nx, p->nxi, y, p->n, nrhs, f->zwork, f->ozws, f->status, s, f->done);
+            prof_end("refine_dx_tc", s);
+            if (rc) return rc;
+            prof_begin("refine_rows", s);
+            rc = pencil_rows_z_dev(p, f->t, f->zwork, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s,
+                                   f->done);
+            prof_end("refine_rows", s);
+        } else {
+            rc = pencil_rows_dev(p, f->t, y, p->n, nrhs, f->sigma_dev, 1, x, 1, f->rwork, f->normpart, s, f->done,
+                                 f->arith);
+        }
         if (rc) return rc;
         k_refine_check<<<nrhs, 32, 0, s>>>(nblk, f->normpart, f->refine_tol, f->done, f->worst, f->sweeps, last,
                                             f->status); klst::note_launch();

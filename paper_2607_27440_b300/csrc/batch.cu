@@ -31,7 +31,8 @@ int64_t solve_footprint(const klst_pencil_desc& d, int precision, const klst_eig
     b += nxi * nx * nx * 16 + (precision == KLST_MIXED ? nxi * nx * nx * 8 : precision == KLST_DF64 ? nxi * nx * nx * 16 : 0);
     b += 11 * r * r * 16;                                                        // capacitance buffers
     b += 2 * n * (m + 1) * 16 + 3 * n * nev * 16;                                // Krylov bases + extraction
-    b += (precision == KLST_MIXED ? 2 * n * nev * 16 : 0);                       // refinement work
+    b += (precision == KLST_MIXED ? 3 * n * nev * 16 + (int64_t)oz_dx_ws_bytes((int)nx, (int)nxi, (int)nev) : 0);  // refinement work
+    b += (int64_t)oz_dx_bytes((int)nx);                                           // D_x slices
     if (o.arith == KLST_ARITH_DF64)                                              // df64 basis: w, v and partial dots
         b += 2 * n * 16 + ((n + 511) / 512) * (m + 2) * 16;
     b += 31 * m * m * 32 + 8 * m * m * 16;                                       // Schur work and rotation log

@@ -113,6 +113,8 @@ struct klst_pencil_s {
     double* macro;  // [4*nx] rho, u, E, T of the base state
     double* G;      // [((k*2 + c)*4 + a)*nx + j] coupling coefficients (zero on inflow rows)
     double* w;      // [((k*2 + c)*4 + a)*nx + j] moment functionals
+    void* dx_oz;    // D_x cut into the tensor-core GEMM's integer slices (A operand) and row exponents
+    double* eneq;   // [nx] non-equilibrium measure of the base flow (Eq. L2norm)
     klst::Status* status;
     int64_t footprint;
     cudaStream_t stream;  // stream of the last call (the handle's memory is released on it)

@@ -538,6 +538,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     KLST_CK(cudaMemsetAsync(W.S, 0, sizeof(double2) * lds * m, s));
     KLST_CK(cudaMemsetAsync(W.reorth, 0, sizeof(int) * 4, s));
+    KLST_CK(cudaMemsetAsync(W.rcount, 0, sizeof(int) * 4, s));
     KLST_CK(cudaMemsetAsync(f->status, 0, sizeof(Status), s));
     KLST_CK(cudaMemsetAsync(f->worst, 0, sizeof(double), s));
     KLST_CK(cudaMemsetAsync(f->sweeps, 0, sizeof(int), s));
@@ -652,6 +653,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     }
     bool converged = false;
     int f64_steps = 0;  // float64 basis: every step runs both Gram-Schmidt passes
+    int64_t schur_rot = 0;
+    int schur_sweeps = 0, schur_swaps = 0;
     for (;;) {
         const int jfirst = k;
         if (use_graph) {
@@ -691,8 +694,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         if ((rc = dfm ? launch_schur(a, s) : launch_schur64(a, s)) != KLST_OK) return fail(rc);
         cudaEventRecord(evs[3 * (m + 1) + 1], s);
         Status hst;
-        int hconv = 0;
+        int hconv = 0, hcnt[4] = {0, 0, 0, 0};
         KLST_CK(cudaMemcpyAsync(&hconv, W.nconv, sizeof(int), cudaMemcpyDeviceToHost, s));
+        KLST_CK(cudaMemcpyAsync(hcnt, W.rcount, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
         KLST_CK(cudaMemcpyAsync(&hst, f->status, sizeof(Status), cudaMemcpyDeviceToHost, s));
         KLST_CK(cudaStreamSynchronize(s));
         if (use_graph) {  // graph mode times the whole expansion (apply + orthogonalisation) as t_orth
@@ -713,6 +717,8 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             t_restart += a3;
             t_schur += a3;
         }
+        schur_rot += hcnt[0];
+        if (!dfm) { schur_sweeps += hcnt[1]; schur_swaps += hcnt[2]; }
         if (hconv < 0 || (hst.flags & ST_NOCONV_QR)) { set_error("small Schur QR iteration did not converge"); return fail(KLST_ENOCONV); }
         if (hst.flags & ST_BREAKDOWN) { set_error("Arnoldi breakdown (invariant subspace found)"); return fail(KLST_ENOCONV); }
         if (hst.flags & ST_TIMEOUT) { set_error("tensor-core rotation: a bounded device wait gave up"); return fail(KLST_ETIMEOUT); }
@@ -823,6 +829,9 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         info->t_restart_ms = t_restart;
         info->t_schur_ms = t_schur;
         info->reorths = dfm ? reorths : f64_steps;
+        info->schur_sweeps = schur_sweeps;
+        info->schur_swaps = schur_swaps;
+        info->schur_rotations = schur_rot;
     }
     W.release(s);
     f->max_refine = prev_refine;

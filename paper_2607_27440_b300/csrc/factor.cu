@@ -432,6 +432,9 @@ int factor_reserve(klst_factor f, int nrhs, cudaStream_t s) {
     f->stream = s;
     if (nrhs <= f->nrhs_cap) return KLST_OK;
     dfree(f->tpart, s); dfree(f->t, s); dfree(f->sv, s); dfree(f->bwork, s); dfree(f->rwork, s);
+    dfree(f->zwork, s); dfree(f->ozws, s);
+    f->zwork = nullptr;
+    f->ozws = nullptr;
     dfree(f->normpart, s); dfree(f->done, s); dfree(f->sigma_dev, s);
     f->sigma_dev = nullptr;
     f->tpart = f->t = f->sv = f->bwork = f->rwork = nullptr;
@@ -445,6 +448,10 @@ int factor_reserve(klst_factor f, int nrhs, cudaStream_t s) {
     if (f->precision == KLST_MIXED) {
         KLST_CK(dmalloc((void**)&f->bwork, sizeof(double2) * nrhs * n, s));
         KLST_CK(dmalloc((void**)&f->rwork, sizeof(double2) * nrhs * n, s));
+        if (f->tc_resid) {
+            KLST_CK(dmalloc((void**)&f->zwork, sizeof(double2) * nrhs * n, s));
+            KLST_CK(dmalloc(&f->ozws, oz_dx_ws_bytes(f->nx, f->nxi, nrhs), s));
+        }
     }
     KLST_CK(dmalloc((void**)&f->normpart, sizeof(double) * nrhs * 2 * 4096, s));
     KLST_CK(dmalloc((void**)&f->done, sizeof(int) * nrhs, s));
@@ -465,8 +472,8 @@ using namespace klst;
 extern "C" void klst_factor_destroy(klst_factor f) {
     if (!f) return;
     cudaStream_t s = f->stream;
-    void* bufs[] = {f->KinvT, f->Cinv, f->tpart, f->t, f->sv, f->bwork, f->rwork, f->normpart, f->done,
-                    f->sigma_dev, f->worst, f->sweeps, f->status};
+    void* bufs[] = {f->KinvT, f->Cinv, f->tpart, f->t, f->sv, f->bwork, f->rwork, f->zwork, f->ozws, f->normpart,
+                    f->done, f->sigma_dev, f->worst, f->sweeps, f->status};
     for (void* b : bufs) dfree(b, s);
     delete f;
 }
@@ -495,6 +502,12 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     }
     f->max_refine = 4;
     f->refine_tol = 1e-12;
+    {
+        // the float64 refinement residual forms its D_x products as float64-accurate tensor-core
+        // GEMMs (KLST_NO_TC=1: the float64 CUDA-core rows)
+        const char* notc = getenv("KLST_NO_TC");
+        f->tc_resid = (precision == KLST_MIXED && p->dx_oz && !(notc && notc[0] == '1')) ? 1 : 0;
+    }
     const int r = f->r;
     const size_t esz = precision == KLST_MIXED ? sizeof(float2) : sizeof(double2);
     const int nsplit = std::max(1, std::min(p->nxi, 8));

@@ -18,6 +18,9 @@ struct klst_factor_s {
     double2* sv;       // [nrhs][r]
     double2* bwork;    // [nrhs][n] masked right-hand side B x (mixed)
     double2* rwork;    // [nrhs][n] refinement residual
+    double2* zwork;    // [nrhs][n] D_x products of the refinement residual (tensor-core path)
+    void* ozws;        // tensor-core D_x product workspace (integer slices of the iterate)
+    int tc_resid;      // 1: the float64 refinement residual forms its D_x products on the tensor cores
     double* normpart;  // [nrhs][nblk][2]
     int* done;         // [nrhs] refinement converged flags
     double2* sigma_dev;// [nrhs] the shift replicated per right-hand side
@@ -74,6 +77,14 @@ size_t oz_workspace_bytes(int M, int N, int K);
 int oz_rotate(const double2* V, int64_t n, int m, const double2* Q, int keep, double2* Vout, void* ws, Status* st,
               cudaStream_t s);
 
+// D_x products of the pencil operator on the tensor cores: D_x slices once per pencil (oz_dx_bytes,
+// oz_split_dx), then z = blockwise D_x x for nrhs vectors (workspace oz_dx_ws_bytes)
+size_t oz_dx_bytes(int nx);
+int oz_split_dx(const double* Dx, int nx, void* buf, cudaStream_t s);
+size_t oz_dx_ws_bytes(int nx, int nxi, int nrhs);
+int oz_dx_apply(const void* dxbuf, int nx, int nxi, const double2* x, int64_t ldx, int nrhs, double2* z, void* ws,
+                Status* st, cudaStream_t s, const int* done = nullptr);  // done[rhs] != 0: skip that vector
+
 // float64 Gram-Schmidt of one Arnoldi step (orth64.cu)
 struct Orth64Args {
     double2* V;        // basis, n x (m + 1) column-major (ld n)
@@ -103,6 +114,9 @@ int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t 
 int apply_pencil_dev(klst_pencil p, const double2* x, double2* y, int nrhs, const double2* omega_dev,
                      cudaStream_t s, double2* mwork, double2* mpart, int ngroups);
 int pencil_work_groups(klst_pencil p);
+int pencil_rows_z_dev(klst_pencil p, const double2* m, const double2* z, const double2* x, int64_t ldx, int nrhs,
+                      const double2* omega, int mode, const double2* b, int mask_b, double2* y, double* normpart,
+                      cudaStream_t s, const int* done);
 // klst_eigs's option rules (KLST_EINVAL with a message); n = unknowns of the pencil
 int validate_eigs_opts(const klst_eigs_opts* o, int64_t n);
 void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,

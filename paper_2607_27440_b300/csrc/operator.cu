@@ -171,6 +171,81 @@ __global__ void k_pencil_rows(int nx, int nxi, double beta, const double* __rest
     }
 }
 
+// The same rows as k_pencil_rows with the D_x products z (one per velocity block and component,
+// layout of x) already formed, one entry per thread: the diagonal, the moment coupling, the inflow
+// rows and the residual and norm bookkeeping, all float64.
+__global__ void __launch_bounds__(256) k_pencil_rows_z(int nx, int nxi, double beta, const double* __restrict__ xi_x,
+                                                       const double* __restrict__ xi_y, const double* __restrict__ nu,
+                                                       const double* __restrict__ G, const double2* __restrict__ m,
+                                                       const double2* __restrict__ z, const double2* __restrict__ x,
+                                                       int64_t ldx, const double2* __restrict__ omega, int mode,
+                                                       const double2* __restrict__ b, int mask_b,
+                                                       double2* __restrict__ y, double* __restrict__ normpart,
+                                                       const int* __restrict__ done) {
+    const int rhs = blockIdx.y;
+    if (done && done[rhs]) return;
+    const int64_t n = 2 * (int64_t)nxi * nx, per = (int64_t)nxi * nx;
+    const double2* xr = x + rhs * ldx;
+    const double2* zr = z + rhs * ldx;
+    const double2* br = b ? b + rhs * ldx : nullptr;
+    double2* yr = y + rhs * ldx;
+    const double2 om = omega ? omega[rhs] : mk(0, 0);
+    const double2* mr = m + (size_t)rhs * 4 * nx;
+    double nrm_y = 0.0, nrm_b = 0.0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / per);
+        const int64_t rem = idx - c * per;
+        const int k = (int)(rem / nx), j = (int)(rem - (int64_t)k * nx);
+        const double xix = xi_x[k];
+        const bool bc = is_bc(j, nx, xix);
+        const double2 xv = xr[idx];
+        double2 val;
+        if (bc) {
+            val = xv;
+        } else {
+            const double2 diag = mk(nu[j] - om.x, beta * xi_y[k] - om.y);
+            val = xix * zr[idx] + diag * xv;
+            const double* Gk = G + ((size_t)k * 2 + c) * 4 * nx + j;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) val = val - Gk[a * nx] * mr[a * nx + j];
+        }
+        if (mode == 1) {
+            double2 bv = br[idx];
+            if (mask_b && bc) bv = mk(0, 0);
+            val = bv - val;
+            nrm_b += abs2(bv);
+        }
+        nrm_y += abs2(val);
+        yr[idx] = val;
+    }
+    if (normpart) {
+        __shared__ double red[2][8];
+        nrm_y = warp_sum(nrm_y);
+        nrm_b = warp_sum(nrm_b);
+        if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = nrm_y; red[1][threadIdx.x >> 5] = nrm_b; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a0 = 0, a1 = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a0 += red[0][q]; a1 += red[1][q]; }
+            normpart[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 0] = a0;
+            normpart[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 1] = a1;
+        }
+    }
+}
+
+int pencil_rows_blocks(klst_pencil p);
+
+int pencil_rows_z_dev(klst_pencil p, const double2* m, const double2* z, const double2* x, int64_t ldx, int nrhs,
+                      const double2* omega, int mode, const double2* b, int mask_b, double2* y, double* normpart,
+                      cudaStream_t s, const int* done) {
+    dim3 grd(pencil_rows_blocks(p), nrhs);
+    k_pencil_rows_z<<<grd, 256, 0, s>>>(p->nx, p->nxi, p->desc.beta, p->xi_x, p->xi_y, p->nu, p->G, m, z, x, ldx, omega,
+                                        mode, b, mask_b, y, normpart, done);
+    note_launch();
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+
 void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,
                          cudaStream_t s) {
     k_reduce_groups<<<dim3(len, nrhs), 128, 0, s>>>(len, ngroups, part, out, done); klst::note_launch();

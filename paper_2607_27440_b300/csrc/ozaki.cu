@@ -35,6 +35,7 @@ namespace klst {
 constexpr int OZ_S = 8;        // slices per operand
 constexpr int OZ_NT = 32;      // output columns per CTA (8 diagonal blocks x 32 = 256 TMEM columns)
 constexpr int OZ_KMAX = 256;   // exactness bound of the float32 accumulation (see above)
+constexpr size_t kOzSmemCap = 200 * 1024;  // dynamic shared memory the GEMM may use
 
 // ------------------------------------------------------------------ splitting
 // biased float64 exponent of x (0 for zero and subnormals)
@@ -106,62 +107,77 @@ struct SrcRotCols {     // columns of [[Qr, Qi], [-Qi, Qr]] (2m x 2 keep) for a 
     }
 };
 
-// One thread per A row: exponent, then every k-chunk's eight digits as eight 16-byte rows.
-template <class Src>
-__global__ void __launch_bounds__(128) k_oz_split_a(Src src, int R, int Kp, unsigned short* __restrict__ out,
-                                                    int* __restrict__ ea) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int mtile = r >> 7, rr = r & 127;
-    if (mtile >= (R + 127) / 128) return;
+struct SrcPencilCols {  // Z = D_x Y: column col = rhs * 4 nxi + 2 p + reim of Y is component reim of block p of x_rhs
+    const double* y;     // complex, interleaved; x_rhs starts at rhs * ldy complex entries
+    int64_t ldy;
+    int nx, nxi, N;
+    __device__ double operator()(int col, int kk) const {
+        if (col >= N || kk >= nx) return 0.0;
+        const int per = 4 * nxi, rhs = col / per, cc = col - rhs * per;
+        return y[((int64_t)rhs * ldy + (int64_t)(cc >> 1) * nx + kk) * 2 + (cc & 1)];
+    }
+};
+
+// Slice writer shared by both operands: one warp per row of the operand (a row of A, or a column
+// of B); lane q handles k-chunk q (eight consecutive k), so Kp <= 256 fits one warp.  The warp
+// first takes the row's largest exponent (shuffle max), then every lane writes its chunk's eight
+// digits of each slice as one 16-byte store.  dst(s, kc) gives the chunk's 8-element destination.
+template <class Src, class Out>
+__device__ __forceinline__ void oz_split_row(const Src& src, int r, int Kp, Out out, int* e_out) {
+    const int lane = threadIdx.x & 31, nkc = Kp / 8;
+    double v[8];
     int Emax = 0;
-    for (int k = 0; k < Kp; ++k) Emax = max(Emax, dexp(src(r, k)));
-    const int e = Emax - 1022;
-    ea[r] = e;
-    const int nkc = Kp / 8;
-    for (int kc = 0; kc < nkc; ++kc) {
-        int dig[8][OZ_S];
+    if (lane < nkc) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) oz_digits(oz_fixed(src(r, kc * 8 + q), e), dig[q]);
-#pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
-            uint4 v;
-            v.x = bf16_of_int(dig[0][s]) | ((unsigned)bf16_of_int(dig[1][s]) << 16);
-            v.y = bf16_of_int(dig[2][s]) | ((unsigned)bf16_of_int(dig[3][s]) << 16);
-            v.z = bf16_of_int(dig[4][s]) | ((unsigned)bf16_of_int(dig[5][s]) << 16);
-            v.w = bf16_of_int(dig[6][s]) | ((unsigned)bf16_of_int(dig[7][s]) << 16);
-            const size_t off = ((((size_t)mtile * OZ_S + s) * nkc + kc) * 128 + rr) * 8;
-            *reinterpret_cast<uint4*>(out + off) = v;
+        for (int q = 0; q < 8; ++q) {
+            v[q] = src(r, lane * 8 + q);
+            Emax = max(Emax, dexp(v[q]));
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Emax = max(Emax, __shfl_xor_sync(0xffffffffu, Emax, o));
+    const int e = Emax - 1022;
+    if (lane == 0) *e_out = e;
+    if (lane >= nkc) return;
+    int dig[8][OZ_S];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) oz_digits(oz_fixed(v[q], e), dig[q]);
+#pragma unroll
+    for (int sl = 0; sl < OZ_S; ++sl) {
+        uint4 w;
+        w.x = bf16_of_int(dig[0][sl]) | ((unsigned)bf16_of_int(dig[1][sl]) << 16);
+        w.y = bf16_of_int(dig[2][sl]) | ((unsigned)bf16_of_int(dig[3][sl]) << 16);
+        w.z = bf16_of_int(dig[4][sl]) | ((unsigned)bf16_of_int(dig[5][sl]) << 16);
+        w.w = bf16_of_int(dig[6][sl]) | ((unsigned)bf16_of_int(dig[7][sl]) << 16);
+        *reinterpret_cast<uint4*>(out(sl, lane)) = w;
     }
 }
 
-// One thread per B column c (a row of B^T): exponent and the stacked slice layout of its N-tile.
+// A operand: rows padded to whole 128-row tiles (zero rows beyond R); four warps per CTA
+template <class Src>
+__global__ void __launch_bounds__(128) k_oz_split_a(Src src, int R, int Kp, unsigned short* __restrict__ out,
+                                                    int* __restrict__ ea, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int r = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int mtile = r >> 7, rr = r & 127;
+    if (mtile >= (R + 127) / 128) return;
+    const int nkc = Kp / 8;
+    auto dst = [&](int sl, int kc) { return out + ((((size_t)mtile * OZ_S + sl) * nkc + kc) * 128 + rr) * 8; };
+    oz_split_row(src, r, Kp, dst, ea + r);
+}
+
+// B operand: one warp per column c (a row of B^T) into the stacked slice layout of its N-tile.
+// skip (optional): per column group of cols_per_flag columns, a flag that marks the group done.
 template <class Src>
 __global__ void __launch_bounds__(128) k_oz_split_b(Src src, int N, int Kp, unsigned short* __restrict__ out,
-                                                    int* __restrict__ eb) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+                                                    int* __restrict__ eb, const int* __restrict__ skip, int cols_per_flag) {
+    const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int ntile = c / OZ_NT, cc = c % OZ_NT;
     if (ntile >= (N + OZ_NT - 1) / OZ_NT) return;
-    int Emax = 0;
-    for (int k = 0; k < Kp; ++k) Emax = max(Emax, dexp(src(c, k)));
-    const int e = Emax - 1022;
-    eb[c] = e;
+    if (skip && c < N && skip[c / cols_per_flag]) return;
     const int nkc = Kp / 8;
-    for (int kc = 0; kc < nkc; ++kc) {
-        int dig[8][OZ_S];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) oz_digits(oz_fixed(src(c, kc * 8 + q), e), dig[q]);
-#pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
-            uint4 v;
-            v.x = bf16_of_int(dig[0][s]) | ((unsigned)bf16_of_int(dig[1][s]) << 16);
-            v.y = bf16_of_int(dig[2][s]) | ((unsigned)bf16_of_int(dig[3][s]) << 16);
-            v.z = bf16_of_int(dig[4][s]) | ((unsigned)bf16_of_int(dig[5][s]) << 16);
-            v.w = bf16_of_int(dig[6][s]) | ((unsigned)bf16_of_int(dig[7][s]) << 16);
-            const size_t off = ((((size_t)ntile * nkc + kc) * OZ_S + s) * OZ_NT + cc) * 8;
-            *reinterpret_cast<uint4*>(out + off) = v;
-        }
-    }
+    auto dst = [&](int sl, int kc) { return out + ((((size_t)ntile * nkc + kc) * OZ_S + sl) * OZ_NT + cc) * 8; };
+    oz_split_row(src, c, Kp, dst, eb + c);
 }
 
 // 2^(-7 d) exactly, from its exponent bits
@@ -238,17 +254,45 @@ struct DstBasis {       // column c < keep -> Re V'[r, c], c >= keep -> Im V'[r,
     }
 };
 
+struct DstPencilCols {  // C[j, col] -> z_rhs[p nx + j] component reim, the layout of the input vectors
+    double* z;
+    int64_t ldz;
+    int nx, nxi, N;
+    __device__ void operator()(int r, int col, double v) const {
+        if (r >= nx || col >= N) return;
+        const int per = 4 * nxi, rhs = col / per, cc = col - rhs * per;
+        z[((int64_t)rhs * ldz + (int64_t)(cc >> 1) * nx + r) * 2 + (cc & 1)] = v;
+    }
+};
+
 // One CTA = one 128-row M tile x OZ_NT output columns; four warps.  Thread 0 loads (bulk copies)
 // and issues the MMAs; every warp then drains its 32 TMEM lanes.  smem: the N-tile's stacked B
 // slices (K x OZ_NT x 16 B) and one A slice (K x 256 B).  Waits are bounded: on a timeout the CTA
 // sets ST_TIMEOUT in *st, skips the remaining work, frees its TMEM and returns.
+// x 2^e by integer operations on the exponent field (x a normal float64 or 0; results below the
+// normal range become 0)
+__device__ __forceinline__ double scale2(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0.0;
+    const int En = E + e;
+    if (En <= 0) return 0.0;
+    return __longlong_as_double(b + ((long long)e << 52));
+}
+
 template <class Dst>
 __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __restrict__ As,
                                                     const unsigned short* __restrict__ Bs,
                                                     const int* __restrict__ ea, const int* __restrict__ eb, int Kp,
-                                                    Dst dst, Status* st) {
+                                                    Dst dst, Status* st, const int* __restrict__ skip, int cols_per_flag,
+                                                    int N) {
+    {
+        // every column of this tile belongs to finished work: nothing to do (before any allocation)
+        const int c0 = blockIdx.x * OZ_NT, c1 = min(N, c0 + OZ_NT) - 1;
+        if (skip && skip[c0 / cols_per_flag] && skip[c1 / cols_per_flag]) return;
+    }
     extern __shared__ __align__(128) unsigned char oz_smem[];
-    __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+    __shared__ __align__(8) uint64_t bar_ld, bar_ld2, bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int ntile = blockIdx.x, mtile = blockIdx.y;
@@ -257,10 +301,14 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __rest
     const uint32_t bytesB = (uint32_t)Kp * OZ_NT * 16;   // nkc x OZ_S x OZ_NT x 16 B
     const uint32_t bytesA = (uint32_t)Kp * 256;          // nkc x 128 x 16 B
     unsigned char* sB = oz_smem;
-    unsigned char* sA = oz_smem + bytesB;
+    unsigned char* sA0 = oz_smem + bytesB;
+    // two A buffers when they fit (the next slice loads while the current one multiplies)
+    const bool dbuf = (size_t)bytesB + 2 * (size_t)bytesA <= kOzSmemCap;
+    unsigned char* sA1 = dbuf ? sA0 + bytesA : sA0;
     constexpr uint32_t kCols = 256;                      // 8 diagonal blocks x OZ_NT
     if (tid == 0) {
         mbar_init(&bar_ld, 1);
+        mbar_init(&bar_ld2, 1);
         mbar_init(&bar_mma, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -275,36 +323,52 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __rest
     const uint32_t tbase = tmem_base;
     if (tid == 0) {
         const unsigned short* gB = Bs + (size_t)ntile * nkc * OZ_S * OZ_NT * 8;
-        uint32_t ph_ld = 0, ph_mma = 0;
+        auto gA = [&](int s) { return As + (((size_t)mtile * OZ_S + s) * nkc) * 128 * 8; };
+        // slice s is loaded into buffer s & 1 on barrier bar[s & 1]; with one buffer both are the same
+        uint64_t* bars[2] = {&bar_ld, dbuf ? &bar_ld2 : &bar_ld};
+        unsigned char* bufs[2] = {sA0, sA1};
+        uint32_t ph[2] = {0, 0}, ph_mma = 0;
         bool ok = true;
+        mbar_expect_tx(bars[0], bytesA + bytesB);
+        bulk_g2s(bufs[0], gA(0), bytesA, bars[0]);
+        bulk_g2s(sB, gB, bytesB, bars[0]);
+        if (dbuf) {
+            mbar_expect_tx(bars[1], bytesA);
+            bulk_g2s(bufs[1], gA(1), bytesA, bars[1]);
+        }
         for (int s = 0; s < OZ_S && ok; ++s) {
-            const unsigned short* gA = As + (((size_t)mtile * OZ_S + s) * nkc) * 128 * 8;
-            mbar_expect_tx(&bar_ld, bytesA + (s == 0 ? bytesB : 0));
-            bulk_g2s(sA, gA, bytesA, &bar_ld);
-            if (s == 0) bulk_g2s(sB, gB, bytesB, &bar_ld);
-            ok = mbar_wait(&bar_ld, ph_ld);
-            ph_ld ^= 1;
+            const int b = dbuf ? (s & 1) : 0;
+            ok = mbar_wait(bars[b], ph[b]);
+            ph[b] ^= 1;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // a_s x [b_1 .. b_{8-s}] (N = (8 - s) x OZ_NT) into diagonal blocks s+1 .. 8 (0-based d-2)
             const int nst = OZ_S - s;
             const uint32_t idesc = idesc_bf16(128, nst * OZ_NT);
             const uint32_t dcol = tbase + (uint32_t)(s * OZ_NT);
-            const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+            const uint32_t aBase = smem_u32(bufs[b]), bBase = smem_u32(sB);
             for (int kk = 0; kk < Kp / 16; ++kk) {
                 const uint64_t ad = sdesc(aBase + kk * 2 * 2048, 2048, 128);
                 const uint64_t bd = sdesc(bBase + kk * 2 * (OZ_S * OZ_NT * 16), OZ_S * OZ_NT * 16, 128);
                 mma_bf16(dcol, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
             }
             mma_commit(&bar_mma);
+            // the buffer is reused only after the MMAs reading it have completed
             ok = mbar_wait(&bar_mma, ph_mma);
             ph_mma ^= 1;
+            if (!ok) break;
+            const int nxt = s + (dbuf ? 2 : 1);
+            if (nxt < OZ_S) {
+                mbar_expect_tx(bars[b], bytesA);
+                bulk_g2s(bufs[b], gA(nxt), bytesA, bars[b]);
+            }
         }
         if (!ok) {
             s_fail = 1;
             atomicOr(&st->flags, ST_TIMEOUT);
             // give any copy or MMA still in flight one more bounded wait before the TMEM is freed
-            mbar_wait(&bar_ld, ph_ld);
+            mbar_wait(&bar_ld, ph[0]);
+            if (dbuf) mbar_wait(&bar_ld2, ph[1]);
             mbar_wait(&bar_mma, ph_mma);
         }
     }
@@ -312,7 +376,10 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __rest
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {
-        // C[r, c] = 2^(ea + eb) sum_{d=2..9} block_d 2^(-7 d), each block an exact integer
+        // C[r, c] = 2^(ea + eb) sum_{d=2..9} block_d 2^(-7 d), each block an exact integer below 2^24:
+        // the four leading blocks and the four trailing ones are combined exactly in two 64-bit
+        // integers (below 2^46 each), which float64 holds exactly, and one fused multiply-add
+        // rounds the sum once
         const int r = mtile * 128 + wid * 32 + lane;
         const uint32_t lane_off = (uint32_t)(wid * 32) << 16;
         const int era = ea[r];
@@ -323,11 +390,14 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __rest
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                double acc = 0.0;
+                long long H = 0, L = 0;
 #pragma unroll
-                for (int d = OZ_S - 1; d >= 0; --d) acc = fma((double)blk[d][q], exp2_neg7(d + 2), acc);
+                for (int d = 0; d < 4; ++d) H = H * 128 + (long long)__float2int_rn(blk[d][q]);
+#pragma unroll
+                for (int d = 4; d < 8; ++d) L = L * 128 + (long long)__float2int_rn(blk[d][q]);
+                const double v = fma((double)L, exp2_neg7(9), (double)H * exp2_neg7(5));
                 const int c = ntile * OZ_NT + c0 + q;
-                dst(r, c, ldexp(acc, era + eb[c]));
+                dst(r, c, scale2(v, era + eb[c]));
             }
         }
     }
@@ -362,12 +432,14 @@ static OzWork oz_carve(void* ws, int M, int N, int Kp) {
 }
 
 template <class Dst>
-static int oz_launch_gemm(const OzWork& w, int M, int N, int Kp, Dst dst, Status* st, cudaStream_t s) {
+static int oz_launch_gemm(const OzWork& w, int M, int N, int Kp, Dst dst, Status* st, cudaStream_t s,
+                          const int* skip = nullptr, int cols_per_flag = 1) {
     static std::atomic<unsigned long long> attr{0};
-    const size_t smem = (size_t)Kp * OZ_NT * 16 + (size_t)Kp * 256;
-    if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    const size_t bytesB = (size_t)Kp * OZ_NT * 16, bytesA = (size_t)Kp * 256;
+    const size_t smem = bytesB + (bytesB + 2 * bytesA <= kOzSmemCap ? 2 : 1) * bytesA;
+    if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap));
     dim3 grid((N + OZ_NT - 1) / OZ_NT, (M + 127) / 128);
-    k_oz_gemm<Dst><<<grid, 128, smem, s>>>(w.A, w.B, w.ea, w.eb, Kp, dst, st);
+    k_oz_gemm<Dst><<<grid, 128, smem, s>>>(w.A, w.B, w.ea, w.eb, Kp, dst, st, skip, cols_per_flag, N);
     note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
@@ -382,12 +454,51 @@ int oz_rotate(const double2* V, int64_t n, int m, const double2* Q, int keep, do
     const int R = (int)n;
     SrcBasisRows sa{V, n, m, R};
     SrcRotCols sb{Q, m, m, keep};
-    k_oz_split_a<SrcBasisRows><<<(int)(((n + 127) / 128 * 128 + 127) / 128), 128, 0, s>>>(sa, R, Kp, w.A, w.ea);
+    k_oz_split_a<SrcBasisRows><<<(int)((n + 127) / 128 * 32), 128, 0, s>>>(sa, R, Kp, w.A, w.ea, nullptr);
     note_launch();
-    k_oz_split_b<SrcRotCols><<<((N + OZ_NT - 1) / OZ_NT * OZ_NT + 127) / 128, 128, 0, s>>>(sb, N, Kp, w.B, w.eb);
+    k_oz_split_b<SrcRotCols><<<(N + OZ_NT - 1) / OZ_NT * OZ_NT / 4, 128, 0, s>>>(sb, N, Kp, w.B, w.eb, nullptr, 1);
     note_launch();
     KLST_CK_LAUNCH();
     return oz_launch_gemm(w, R, N, Kp, DstBasis{reinterpret_cast<double*>(Vout), n, R, keep}, st, s);
+}
+
+// D_x of a pencil as the A operand (row j, reduction index m: D_x[j][m], row-major nx x nx), once per pencil
+size_t oz_dx_bytes(int nx) {
+    const int Kp = (nx + 15) / 16 * 16;
+    return (size_t)128 * Kp * OZ_S * 2 + 128 * sizeof(int);
+}
+int oz_split_dx(const double* Dx, int nx, void* buf, cudaStream_t s) {
+    const int Kp = (nx + 15) / 16 * 16;
+    unsigned short* A = (unsigned short*)buf;
+    int* ea = (int*)((char*)buf + (size_t)128 * Kp * OZ_S * 2);
+    SrcColMajor sa{Dx, nx, 1, nx, nx};
+    k_oz_split_a<SrcColMajor><<<32, 128, 0, s>>>(sa, nx, Kp, A, ea, nullptr);
+    note_launch();
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+// workspace of oz_dx_apply for nrhs vectors
+size_t oz_dx_ws_bytes(int nx, int nxi, int nrhs) {
+    const int Kp = (nx + 15) / 16 * 16, N = 4 * nxi * nrhs;
+    const size_t nt = (N + OZ_NT - 1) / OZ_NT;
+    return ((nt * OZ_NT * (size_t)Kp * OZ_S * 2 + 255) & ~size_t(255)) + nt * OZ_NT * sizeof(int) + 256;
+}
+// z_rhs[(c nxi + k) nx + j] = sum_m D_x[j][m] x_rhs[(c nxi + k) nx + m] for every block, in float64 accuracy
+int oz_dx_apply(const void* dxbuf, int nx, int nxi, const double2* x, int64_t ldx, int nrhs, double2* z, void* ws,
+                Status* st, cudaStream_t s, const int* done) {
+    const int Kp = (nx + 15) / 16 * 16, N = 4 * nxi * nrhs;
+    const size_t nt = (N + OZ_NT - 1) / OZ_NT;
+    OzWork w;
+    w.A = (unsigned short*)dxbuf;
+    w.ea = (int*)((const char*)dxbuf + (size_t)128 * Kp * OZ_S * 2);
+    w.B = (unsigned short*)ws;
+    w.eb = (int*)((char*)ws + ((nt * OZ_NT * (size_t)Kp * OZ_S * 2 + 255) & ~size_t(255)));
+    SrcPencilCols sb{reinterpret_cast<const double*>(x), ldx, nx, nxi, N};
+    k_oz_split_b<SrcPencilCols><<<(int)(nt * OZ_NT / 4), 128, 0, s>>>(sb, N, Kp, w.B, w.eb, done, 4 * nxi);
+    note_launch();
+    KLST_CK_LAUNCH();
+    return oz_launch_gemm(w, nx, N, Kp, DstPencilCols{reinterpret_cast<double*>(z), ldx, nx, nxi, N}, st, s, done,
+                          4 * nxi);
 }
 
 int oz_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int M, int N, int K,
@@ -396,9 +507,9 @@ int oz_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, doub
     OzWork w = oz_carve(ws, M, N, Kp);
     SrcColMajor sa{A, lda, 0, M, K};
     SrcColMajor sb{B, ldb, 1, N, K};
-    k_oz_split_a<SrcColMajor><<<(M + 127) / 128, 128, 0, s>>>(sa, M, Kp, w.A, w.ea);
+    k_oz_split_a<SrcColMajor><<<(M + 127) / 128 * 32, 128, 0, s>>>(sa, M, Kp, w.A, w.ea, nullptr);
     note_launch();
-    k_oz_split_b<SrcColMajor><<<((N + OZ_NT - 1) / OZ_NT * OZ_NT + 127) / 128, 128, 0, s>>>(sb, N, Kp, w.B, w.eb);
+    k_oz_split_b<SrcColMajor><<<(N + OZ_NT - 1) / OZ_NT * OZ_NT / 4, 128, 0, s>>>(sb, N, Kp, w.B, w.eb, nullptr, 1);
     note_launch();
     KLST_CK_LAUNCH();
     return oz_launch_gemm(w, M, N, Kp, DstColMajor{C, ldc, M, N}, st, s);

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <vector>
 
-#include "common.cuh"
+#include "factor.cuh"
 
 namespace klst {
 
@@ -218,7 +218,7 @@ __device__ void small_solve(int n, double* J /* n*n row-major */, double* r) {
 // functionals w, the conservative fix C <- C (M C)^{-1}, and G = nu C + (f^e - f) d.
 __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x, const double* xi_y,
                              const double* W, double* gbuf, double* hbuf, double* nu_out, double* macro,
-                             double* G, double* w, Status* st) {
+                             double* G, double* w, double* eneq, Status* st) {
     __shared__ double sm[32 * 16 + 16];
     __shared__ double s_th[4];
     __shared__ double s_MCinv[16];
@@ -348,10 +348,12 @@ __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x,
         macro[3 * nx + j] = Tc;
     }
     __syncthreads();
+    double dev2[1] = {0.0};  // sum_k W_k (g_c - g_c^e)^2 (Eq. L2norm)
     for (int k = threadIdx.x; k < nxi; k += blockDim.x) {
         double xx = xi_x[k], xy = xi_y[k], Wk = W[k];
         double ge = maxw(rp, up, Tp, xx, xy), he = 0.5 * Tp * ge;
         double gk = bp.noneq ? g[k] : ge, hk = bp.noneq ? h[k] : he;
+        dev2[0] += Wk * (gk - ge) * (gk - ge);
         double dxu = xx - up, phi = -1.0 / Tp + (dxu * dxu + xy * xy) / (Tp * Tp);
         double dgT = ge * phi, dhT = 0.5 * ge + 0.5 * Tp * ge * phi;
         double Cr[2][4] = {{ge / rp, ge * 2.0 * dxu / Tp - (4.0 / 3.0) * up * dgT, ge * 2.0 * xy / Tp, (4.0 / 3.0) * dgT},
@@ -372,6 +374,8 @@ __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x,
             }
         }
     }
+    block_sum<1>(dev2, sm);
+    if (threadIdx.x == 0) eneq[j] = sqrt(dev2[0]);
 }
 
 // ------------------------------------------------------------------ dense export (tests)
@@ -439,9 +443,10 @@ extern "C" const char* klst_last_error(void) { return g_err; }
 
 extern "C" void klst_pencil_destroy(klst_pencil p) {
     if (!p) return;
-    double* bufs[] = {p->x, p->Dx, p->DxT, p->xi_x, p->xi_y, p->W, p->nu, p->macro, p->G, p->w};
+    double* bufs[] = {p->x, p->Dx, p->DxT, p->xi_x, p->xi_y, p->W, p->nu, p->macro, p->G, p->w, p->eneq};
     for (double* b : bufs) dfree(b, p->stream);
     dfree(p->status, p->stream);
+    dfree(p->dx_oz, p->stream);
     delete p;
 }
 
@@ -484,6 +489,7 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
     ALLOC(p->macro, 4 * nx);
     ALLOC(p->G, (size_t)nxi * 8 * nx);
     ALLOC(p->w, (size_t)nxi * 8 * nx);
+    ALLOC(p->eneq, nx);
     ALLOC(p->status, 1);
 #undef ALLOC
     cudaError_t e;
@@ -505,8 +511,16 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
     const double p1 = 0.5, p2 = p1 * (1.0 + 2.0 * g * (M * M - 1.0) / (g + 1.0));
     bp.rho2 = r; bp.u2 = bp.u1 / r; bp.T2 = 2.0 * p2 / bp.rho2;
     k_base_state<<<nx, 256, 0, s>>>(bp, p->x, p->xi_x, p->xi_y, p->W, gbuf, gbuf + (size_t)nx * nxi, p->nu,
-                                    p->macro, p->G, p->w, p->status); klst::note_launch();
+                                    p->macro, p->G, p->w, p->eneq, p->status); klst::note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "pencil kernels", __FILE__, __LINE__));
+    // D_x as integer slices for the float64-accurate tensor-core D_x products of the operator
+    {
+        const size_t bytes = oz_dx_bytes(nx);
+        if ((e = dmalloc(&p->dx_oz, bytes, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+        p->footprint += (int64_t)bytes;
+        int rc = oz_split_dx(p->Dx, nx, p->dx_oz, s);
+        if (rc) return fail(rc);
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "build sync", __FILE__, __LINE__));
     dfree(gh, s); dfree(Wq, s); dfree(gbuf, s);
     gh = Wq = gbuf = nullptr;

@@ -388,23 +388,31 @@ __global__ void __launch_bounds__(32) k_schur_q(SchurArgs a) {
             q4[i * 32 + t] = cdf_pack(qi);
         }
     }
-    // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in registers
+    // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in registers; the log
+    // is staged into shared memory 256 entries at a time by the whole warp
+    Rot* slog = reinterpret_cast<Rot*>(q4 + (size_t)m * 32);
     const int nrot = *a.log_count;
     int ci = -1;
     cdf cx = cdf_zero();
-    for (int k = 0; k < nrot; ++k) {
-        const Rot g = a.log[k];
-        cdf x;
-        if (g.i == ci) x = cx;
-        else {
-            if (ci >= 0) q4[ci * 32 + t] = cdf_pack(cx);
-            x = cdf_unpack(q4[g.i * 32 + t]);
+    for (int k0 = 0; k0 < nrot; k0 += 256) {
+        const int cnt = min(256, nrot - k0);
+        for (int i = t; i < cnt; i += 32) slog[i] = a.log[k0 + i];
+        __syncwarp();
+        for (int k = 0; k < cnt; ++k) {
+            const Rot g = slog[k];
+            cdf x;
+            if (g.i == ci) x = cx;
+            else {
+                if (ci >= 0) q4[ci * 32 + t] = cdf_pack(cx);
+                x = cdf_unpack(q4[g.i * 32 + t]);
+            }
+            cdf y = cdf_unpack(q4[(g.i + 1) * 32 + t]);
+            cdf_rot(x, y, df_unpack(g.c), cdf_conj(cdf_unpack(g.s)));
+            q4[g.i * 32 + t] = cdf_pack(x);
+            ci = g.i + 1;
+            cx = y;
         }
-        cdf y = cdf_unpack(q4[(g.i + 1) * 32 + t]);
-        cdf_rot(x, y, df_unpack(g.c), cdf_conj(cdf_unpack(g.s)));
-        q4[g.i * 32 + t] = cdf_pack(x);
-        ci = g.i + 1;
-        cx = y;
+        __syncwarp();
     }
     if (ci >= 0) q4[ci * 32 + t] = cdf_pack(cx);
     if (r < m)
@@ -532,7 +540,7 @@ int launch_schur(const SchurArgs& a, cudaStream_t s) {
     k_schur_qr<<<1, 256, packed, s>>>(a); klst::note_launch();
     prof_end("schur_qr", s);
     prof_begin("schur_q", s);
-    k_schur_q<<<(m + 31) / 32, 32, sizeof(double2) * 32 * m, s>>>(a); klst::note_launch();
+    k_schur_q<<<(m + 31) / 32, 32, sizeof(double2) * 32 * m + sizeof(Rot) * 256, s>>>(a); klst::note_launch();
     prof_end("schur_q", s);
     launch_schur_post(a, s);
     KLST_CK_LAUNCH();

@@ -180,9 +180,8 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
     Rot64* log = reinterpret_cast<Rot64*>(a.log);
     __shared__ double rc[192];
     __shared__ double2 rs[192];
-    __shared__ double s_c;
-    __shared__ double2 s_s, s_mu;
-    __shared__ int s_lo, s_q, s_fail, s_cnt;
+    __shared__ double2 s_mu;
+    __shared__ int s_lo, s_fail, s_cnt;
 #define TT(i, j) sT64[pk64(i, j)]
     for (int j = 0; j < m; ++j)
         for (int i = tid; i <= min(j + 1, m - 1); i += nt) TT(i, j) = a.H[(size_t)j * m + i];
@@ -250,11 +249,13 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
             rs[lo] = sv;
         }
         __syncthreads();
-        // left sweep: rotation i on rows i, i+1 (columns i..m-1); the thread holding column i+1
-        // forms rotation i+1 from its freshly rotated diagonal entry
+        // left sweep: rotation i on rows i, i+1 of the window's columns i..hi; the thread holding
+        // column i+1 forms rotation i+1 from its freshly rotated diagonal entry.  Columns right of
+        // the window (and rows above it, below) are brought up to date afterwards by
+        // k_schur_defer64, one row or column per thread on many SMs.
         for (int i = lo; i < hi; ++i) {
             const int col = i + tid;
-            if (col < m) {
+            if (col <= hi) {
                 const double c = rc[i];
                 const double2 sv = rs[i];
                 double2 x = TT(i, col), y = TT(i + 1, col);
@@ -271,8 +272,8 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
             }
             __syncthreads();
         }
-        // right sweep in bulk: row r receives rotations i >= max(lo, r - 1), in order
-        for (int r = tid; r <= hi; r += nt) {
+        // right sweep in bulk over the window's rows: row r receives rotations i >= max(lo, r - 1)
+        for (int r = lo + tid; r <= hi; r += nt) {
             const int i0 = max(lo, r - 1);
             if (i0 >= hi) continue;
             double2 x = TT(r, i0);
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
         const int base = s_cnt;
         for (int t = tid; t < hi - lo; t += nt) {
             Rot64 g;
-            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = 0;
+            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = (lo << 16) | hi;  // the sweep's window
             log[base + t] = g;
         }
         __syncthreads();
@@ -309,6 +310,53 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
     }
     if (tid == 0) { *a.log_count = s_cnt; a.log_count[1] = total; }
 #undef TT
+}
+
+constexpr int kLogChunk = 256;  // rotation-log entries staged in shared memory at a time
+
+// The updates the window-restricted sweeps left out, from the rotation log: rows above a sweep's
+// window receive its rotations from the right (phase 0, one row per thread), columns right of it
+// from the left (phase 1, one column per thread).  An entry can owe both kinds; left and right
+// rotations commute, so applying every row's right rotations first and then every column's left
+// rotations, each kind in log order, gives the full update.  Entries inside a later window never
+// owe anything (windows are nested or disjoint), so the sweeps never read a stale entry.
+__global__ void __launch_bounds__(32) k_schur_defer64(SchurArgs a, int phase) {
+    extern __shared__ double2 q64[];  // [m][RPC], then the log chunk
+    constexpr int RPC = 4;
+    if (*a.nconv < 0) return;
+    const int m = a.m, t = threadIdx.x, r = blockIdx.x * RPC + t;
+    const bool lane_on = t < RPC && r < m;
+    Rot64* slog = reinterpret_cast<Rot64*>(q64 + (size_t)m * RPC);
+    const Rot64* log = reinterpret_cast<const Rot64*>(a.log);
+    // phase 0: v = row r of T (stride m); phase 1: v = column r (contiguous)
+    if (lane_on)
+        for (int k = 0; k < m; ++k)
+            q64[k * RPC + t] = phase == 0 ? a.H[(size_t)k * m + r] : a.H[(size_t)r * m + k];
+    const int nrot = *a.log_count;
+    for (int k0 = 0; k0 < nrot; k0 += kLogChunk) {
+        const int cnt = min(kLogChunk, nrot - k0);
+        for (int i = t; i < cnt; i += 32) slog[i] = log[k0 + i];
+        __syncwarp();
+        if (lane_on) {
+            for (int k = 0; k < cnt; ++k) {
+                const Rot64 g = slog[k];
+                const int lo = g.pad >> 16, hi = g.pad & 0xFFFF;
+                if (phase == 0 ? (r >= lo) : (r <= hi)) continue;
+                double2 x = q64[g.i * RPC + t], y = q64[(g.i + 1) * RPC + t];
+                if (phase == 0) crot64(x, y, g.c, conj(g.s));  // columns (i, i+1) of row r
+                else crot64(x, y, g.c, g.s);                   // rows (i, i+1) of column r
+                q64[g.i * RPC + t] = x;
+                q64[(g.i + 1) * RPC + t] = y;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane_on)
+        for (int k = 0; k < m; ++k) {
+            const double2 v = q64[k * RPC + t];
+            if (phase == 0) a.H[(size_t)k * m + r] = v;
+            else a.H[(size_t)r * m + k] = v;
+        }
 }
 
 // Reordering: bring the keep Ritz values of largest |mu| to the front of the upper triangular T by
@@ -396,52 +444,66 @@ __global__ void __launch_bounds__(256) k_schur_reorder64(SchurArgs a) {
 
 // ---------------------------------------------------------------- 3. Schur vectors
 // Row r of Q = e_r^T H_0 H_1 ... H_{m-3} G_1^H G_2^H ...: the reflectors, then every logged rotation
-// in order.  One thread per row, four rows per CTA (the float64 pipe of one SM serves few lanes, so
-// the rows are spread over many SMs); the row lives in shared memory.
+// in order.  One warp per CTA, four rows per CTA (the float64 pipe of one SM serves few lanes, so
+// the rows are spread over many SMs); a row lives in shared memory.  The rotation log is staged
+// into shared memory 256 entries at a time by the whole warp, so the serial replay of the four
+// rows reads its rotations from shared memory instead of waiting on L2 for each one.
 __global__ void __launch_bounds__(32) k_schur_q64(SchurArgs a) {
-    extern __shared__ double2 q64[];  // [m][RPC]
+    extern __shared__ double2 q64[];  // [m][RPC], then the log chunk
     constexpr int RPC = 4;
     const int m = a.m, t = threadIdx.x, r = blockIdx.x * RPC + t;
-    if (t >= RPC) return;
-    const double2* Vh = reinterpret_cast<const double2*>(a.Vh);
+    const bool row_lane = t < RPC;
+    Rot64* slog = reinterpret_cast<Rot64*>(q64 + (size_t)m * RPC);
     const Rot64* log = reinterpret_cast<const Rot64*>(a.log);
-    for (int col = 0; col < m; ++col) q64[col * RPC + t] = make_double2(col == r ? 1.0 : 0.0, 0.0);
-    for (int c = 0; c + 2 < m; ++c) {
-        const double tau = a.tau[c];
-        if (tau == 0.0) continue;
-        const double2* vc = Vh + (size_t)c * m;
-        double2 g0 = make_double2(0.0, 0.0), g1 = g0;
-        int i = c + 1;
-        for (; i + 1 < m; i += 2) {
-            cfma(g0, q64[i * RPC + t], vc[i]);
-            cfma(g1, q64[(i + 1) * RPC + t], vc[i + 1]);
-        }
-        if (i < m) cfma(g0, q64[i * RPC + t], vc[i]);
-        const double2 g = (-tau) * (g0 + g1);
-        for (i = c + 1; i < m; ++i) {
-            double2 qi = q64[i * RPC + t];
-            cfma(qi, g, conj(vc[i]));
-            q64[i * RPC + t] = qi;
+    const double2* Vh = reinterpret_cast<const double2*>(a.Vh);
+    if (row_lane) {
+        for (int col = 0; col < m; ++col) q64[col * RPC + t] = make_double2(col == r ? 1.0 : 0.0, 0.0);
+        for (int c = 0; c + 2 < m; ++c) {
+            const double tau = a.tau[c];
+            if (tau == 0.0) continue;
+            const double2* vc = Vh + (size_t)c * m;
+            double2 g0 = make_double2(0.0, 0.0), g1 = g0;
+            int i = c + 1;
+            for (; i + 1 < m; i += 2) {
+                cfma(g0, q64[i * RPC + t], vc[i]);
+                cfma(g1, q64[(i + 1) * RPC + t], vc[i + 1]);
+            }
+            if (i < m) cfma(g0, q64[i * RPC + t], vc[i]);
+            const double2 g = (-tau) * (g0 + g1);
+            for (i = c + 1; i < m; ++i) {
+                double2 qi = q64[i * RPC + t];
+                cfma(qi, g, conj(vc[i]));
+                q64[i * RPC + t] = qi;
+            }
         }
     }
     // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in registers
     const int nrot = *a.log_count;
     int ci = -1;
     double2 cx = make_double2(0.0, 0.0);
-    for (int k = 0; k < nrot; ++k) {
-        const Rot64 g = log[k];
-        double2 x;
-        if (g.i == ci) x = cx;
-        else {
-            if (ci >= 0) q64[ci * RPC + t] = cx;
-            x = q64[g.i * RPC + t];
+    for (int k0 = 0; k0 < nrot; k0 += kLogChunk) {
+        const int cnt = min(kLogChunk, nrot - k0);
+        for (int i = t; i < cnt; i += 32) slog[i] = log[k0 + i];  // the whole warp stages the chunk
+        __syncwarp();
+        if (row_lane) {
+            for (int k = 0; k < cnt; ++k) {
+                const Rot64 g = slog[k];
+                double2 x;
+                if (g.i == ci) x = cx;
+                else {
+                    if (ci >= 0) q64[ci * RPC + t] = cx;
+                    x = q64[g.i * RPC + t];
+                }
+                double2 y = q64[(g.i + 1) * RPC + t];
+                crot64(x, y, g.c, conj(g.s));
+                q64[g.i * RPC + t] = x;
+                ci = g.i + 1;
+                cx = y;
+            }
         }
-        double2 y = q64[(g.i + 1) * RPC + t];
-        crot64(x, y, g.c, conj(g.s));
-        q64[g.i * RPC + t] = x;
-        ci = g.i + 1;
-        cx = y;
+        __syncwarp();  // the chunk is consumed before the next one overwrites it
     }
+    if (!row_lane) return;
     if (ci >= 0) q64[ci * RPC + t] = cx;
     if (r < m)
         for (int col = 0; col < m; ++col) a.Q[(size_t)col * m + r] = q64[col * RPC + t];
@@ -461,11 +523,17 @@ int launch_schur64(const SchurArgs& a, cudaStream_t s) {
     prof_begin("schur_qr", s);
     k_schur_qr64<<<1, 256, packed, s>>>(a); note_launch();
     prof_end("schur_qr", s);
+    prof_begin("schur_defer", s);
+    for (int phase = 0; phase < 2; ++phase) {
+        k_schur_defer64<<<(m + 3) / 4, 32, sizeof(double2) * 4 * m + sizeof(Rot64) * kLogChunk, s>>>(a, phase);
+        note_launch();
+    }
+    prof_end("schur_defer", s);
     prof_begin("schur_reorder", s);
     k_schur_reorder64<<<1, 256, packed, s>>>(a); note_launch();
     prof_end("schur_reorder", s);
     prof_begin("schur_q", s);
-    k_schur_q64<<<(m + 3) / 4, 32, sizeof(double2) * 4 * m, s>>>(a); note_launch();
+    k_schur_q64<<<(m + 3) / 4, 32, sizeof(double2) * 4 * m + sizeof(Rot64) * kLogChunk, s>>>(a); note_launch();
     prof_end("schur_q", s);
     launch_schur_post(a, s);
     KLST_CK_LAUNCH();

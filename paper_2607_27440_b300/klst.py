@@ -39,7 +39,8 @@ class EigsInfo(ctypes.Structure):
                 ("t_factor_ms", c_double), ("t_eigs_ms", c_double), ("max_resid", c_double),
                 ("max_refine_resid", c_double), ("t_apply_ms", c_double), ("t_orth_ms", c_double),
                 ("t_restart_ms", c_double), ("t_schur_ms", c_double),
-                ("reorths", c_int32)]
+                ("reorths", c_int32), ("schur_sweeps", c_int32), ("schur_swaps", c_int32),
+                ("schur_rotations", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +71,8 @@ EXPORTS = {
     "klst_apply_pencil": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "klst_apply_pencil_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "klst_apply_pencil_noalloc_capacity": (ctypes.c_size_t, []),
+    "klst_base_noneq": (c_int32, [c_void_p, c_void_p]),
+    "klst_eigvec_macro": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "klst_factor_shift": (c_int32, [c_void_p, c_double, c_double, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
     "klst_factor_destroy": (None, [c_void_p]),
     "klst_factor_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -264,6 +267,23 @@ class Pencil:
                                                 om.ctypes.data_as(c_void_p) if om is not None else None,
                                                 _stream(stream)))
         return y
+
+    def base_noneq(self):
+        """E_neq(x_j) of the base flow (Eq. L2norm), float64 (nx,)."""
+        out = np.zeros(self.nx)
+        _check(load().klst_base_noneq(self.handle, out.ctypes.data_as(c_void_p)))
+        return out
+
+    def eigvec_macro(self, vecs, stream=None):
+        """(rho^, u^, v^, E^) per point for vectors of shape (nvec, n) or (n,): complex (nvec, 4, nx), and
+        max_x |U^| per vector (Eq. Unormpert)."""
+        vecs = _check_in(vecs, self.n, "vecs")
+        nvec = 1 if vecs.dim() == 1 else vecs.shape[0]
+        m = np.zeros((nvec, 4, self.nx), dtype=np.complex128)
+        um = np.zeros(nvec)
+        _check(load().klst_eigvec_macro(self.handle, _ptr(vecs), nvec, m.ctypes.data_as(c_void_p),
+                                        um.ctypes.data_as(c_void_p), _stream(stream)))
+        return m, um
 
     def factor(self, sigma, precision=FP64, stream=None):
         return Factor(self, sigma, precision, stream)

@@ -216,3 +216,19 @@ def test_apply_c3_paper_shape_residual(klst, prec):
     normA = np.abs(d["Dx"]).sum(axis=1).max() * np.abs(d["xi_x"]).max() + np.abs(d["nu"]).max() + abs(es.sigma)
     bound = 1e3 * 2.220446049250313e-16 * normA * np.linalg.norm(y) / np.linalg.norm(pencil.apply_B(d, x))
     assert rel <= max(bound, 1e-12), (rel, bound)
+
+
+@pytest.mark.parametrize("spec,sigma", [SMALL[2], NX128[1]], ids=["33x9x6", "128x6x4"])
+def test_mixed_residual_tensor_core_matches_cuda_core(klst, spec, sigma, monkeypatch):
+    """The MIXED refinement residual with its D_x products on the tensor cores (default) and on the
+    float64 CUDA cores (KLST_NO_TC=1) refine to the same solution at float64 level."""
+    X = to_dev(wl.random_vectors(spec.n, 2, 31))
+    P = klst.Pencil(spec)
+    out = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("KLST_NO_TC", env)
+        F = P.factor(sigma, precision=klst.MIXED)
+        F.set_refine(6, 1e-15)
+        out.append(to_host(F.apply(X)))
+    err = np.abs(out[0] - out[1]).max(axis=1) / np.abs(out[1]).max(axis=1)
+    assert np.all(err <= 1e-12), err
