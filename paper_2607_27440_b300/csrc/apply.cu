@@ -4,6 +4,7 @@
 // for the two components g^, h^ at once.  MIXED factors hold K_k^{-1} in complex float32 and
 // the result is refined in float64: y += T~ (b - (A - sigma B) y).
 #include <algorithm>
+#include <type_traits>
 
 #include "df64.cuh"
 #include "factor.cuh"
@@ -220,10 +221,30 @@ template <> const char* pass_name<double2>(int pass) { return pass == 1 ? "solve
 template <> const char* pass_name<float4>(int pass) { return pass == 1 ? "solve_pass1_df64" : "solve_pass2_df64"; }
 template <> const char* pass_name<float2>(int pass) { return pass == 1 ? "solve_pass1_c64" : "solve_pass2_c64"; }
 
+// the float64 Woodbury solve with both block passes on the tensor cores
+static int woodbury_solve_tc(klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
+                             cudaStream_t s, const int* done) {
+    klst_pencil p = f->p;
+    const int ng = tc_solve_groups(p->nxi, f->ngroups);
+    prof_begin("solve_pass1_tc", s);
+    int rc = tc_solve_pass(1, f, b, mask, nullptr, 0, nrhs, s, done);
+    prof_end("solve_pass1_tc", s);
+    if (rc) return rc;
+    prof_begin("cap_solve", s);
+    k_reduce_groups_ext(f->r, ng, f->tpart, f->t, done, nrhs, s);
+    k_cinv_gemv<<<dim3((f->r * 32 + 255) / 256, nrhs), 256, 0, s>>>(f->r, f->Cinv, f->t, f->sv, done); klst::note_launch();
+    prof_end("cap_solve", s);
+    prof_begin("solve_pass2_tc", s);
+    rc = tc_solve_pass(2, f, b, mask, y, accumulate, nrhs, s, done);
+    prof_end("solve_pass2_tc", s);
+    return rc;
+}
+
 template <typename C>
 static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
                           cudaStream_t s, const int* done) {
     klst_pencil p = f->p;
+    if (std::is_same<C, double2>::value && f->tc_solve) return woodbury_solve_tc(f, b, mask, y, accumulate, nrhs, s, done);
     const int nx = p->nx, nxi = p->nxi, NXP = nxp_of(nx), KB = 256 / NXP;
     const int ng = f->ngroups, kpg = ((nxi + ng - 1) / ng + KB - 1) / KB * KB;
     dim3 blk(NXP, KB);

@@ -472,7 +472,7 @@ using namespace klst;
 extern "C" void klst_factor_destroy(klst_factor f) {
     if (!f) return;
     cudaStream_t s = f->stream;
-    void* bufs[] = {f->KinvT, f->Cinv, f->tpart, f->t, f->sv, f->bwork, f->rwork, f->zwork, f->ozws, f->normpart,
+    void* bufs[] = {f->KinvT, f->kslices, f->Cinv, f->tpart, f->t, f->sv, f->bwork, f->rwork, f->zwork, f->ozws, f->normpart,
                     f->done, f->sigma_dev, f->worst, f->sweeps, f->status};
     for (void* b : bufs) dfree(b, s);
     delete f;
@@ -507,6 +507,9 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
         // GEMMs (KLST_NO_TC=1: the float64 CUDA-core rows)
         const char* notc = getenv("KLST_NO_TC");
         f->tc_resid = (precision == KLST_MIXED && p->dx_oz && !(notc && notc[0] == '1')) ? 1 : 0;
+        // the float64 block solves multiply integer slices of K_k^{-1} on the tensor cores
+        // (KLST_NO_TC=1: complex128 products on the float64 pipe)
+        f->tc_solve = (precision == KLST_FP64 && tc_solve_supported(p->nx) && !(notc && notc[0] == '1')) ? 1 : 0;
     }
     const int r = f->r;
     const size_t esz = precision == KLST_MIXED ? sizeof(float2) : sizeof(double2);
@@ -523,6 +526,7 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if ((e = dmalloc((void**)&(ptr), (bytes), s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__)); \
     f->footprint += (int64_t)(bytes);
     FALLOC(f->KinvT, esz * (size_t)p->nxi * p->nx * p->nx);
+    if (f->tc_solve) { FALLOC(f->kslices, tc_kinv_bytes(p->nx, p->nxi)); }
     FALLOC(f->Cinv, sizeof(double2) * (size_t)r * r);
     FALLOC(f->worst, sizeof(double));
     FALLOC(f->sweeps, sizeof(int));
@@ -549,6 +553,7 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if (rc) { free64(); return fail(rc); }
     rc = launch_cap<double2>(f, K64, Cp, nsplit, s);
     if (rc) { free64(); return fail(rc); }
+    if (f->tc_solve && (rc = tc_split_kinv(K64, p->nx, p->nxi, f->kslices, s)) != KLST_OK) { free64(); return fail(rc); }
     if (precision != KLST_FP64) {
         const size_t cnt = (size_t)p->nxi * p->nx * p->nx;
         const int nb = (int)std::min<size_t>((cnt + 255) / 256, 8192);

@@ -9,6 +9,8 @@ struct klst_factor_s {
     int nx, nxi, r;    // r = 4 nx (capacitance size)
     int64_t n;
     void* KinvT;       // [nxi][nx(m)][nx(j)] column-major inverse blocks, double2 or float2
+    void* kslices;     // FP64 with tc_solve: bfloat16 integer slices of every K_k^{-1} + row exponents
+    int tc_solve;      // 1: the float64 block solves run on the tensor cores (float64-accurate split)
     double2* Cinv;     // [r][r] row-major capacitance inverse (float64)
     // apply workspace (sized for nrhs_cap right-hand sides)
     int nrhs_cap;
@@ -121,4 +123,11 @@ int pencil_rows_z_dev(klst_pencil p, const double2* m, const double2* z, const d
 int validate_eigs_opts(const klst_eigs_opts* o, int64_t n);
 void k_reduce_groups_ext(int len, int ngroups, const double2* part, double2* out, const int* done, int nrhs,
                          cudaStream_t s);
+// float64-accurate tensor-core block solves (solve_tc.cu)
+bool tc_solve_supported(int nx);
+size_t tc_kinv_bytes(int nx, int nxi);
+int tc_split_kinv(const double2* KinvT, int nx, int nxi, void* buf, cudaStream_t s);
+int tc_solve_groups(int nxi, int ngroups_cap);
+int tc_solve_pass(int pass, klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
+                  cudaStream_t s, const int* done);
 }  // namespace klst

@@ -249,13 +249,13 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
             rs[lo] = sv;
         }
         __syncthreads();
-        // left sweep: rotation i on rows i, i+1 of the window's columns i..hi; the thread holding
-        // column i+1 forms rotation i+1 from its freshly rotated diagonal entry.  Columns right of
-        // the window (and rows above it, below) are brought up to date afterwards by
-        // k_schur_defer64, one row or column per thread on many SMs.
+        // left sweep: rotation i on rows i, i+1 (columns i..m-1); the thread holding column i+1
+        // forms rotation i+1 from its freshly rotated diagonal entry.  (Restricting the sweeps to
+        // the active window and replaying the rest from the log on other SMs was measured slower:
+        // the sweep's cost is its chain of float64 instructions, which the window does not shorten.)
         for (int i = lo; i < hi; ++i) {
             const int col = i + tid;
-            if (col <= hi) {
+            if (col < m) {
                 const double c = rc[i];
                 const double2 sv = rs[i];
                 double2 x = TT(i, col), y = TT(i + 1, col);
@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
             }
             __syncthreads();
         }
-        // right sweep in bulk over the window's rows: row r receives rotations i >= max(lo, r - 1)
-        for (int r = lo + tid; r <= hi; r += nt) {
+        // right sweep in bulk: row r receives rotations i >= max(lo, r - 1), in order
+        for (int r = tid; r <= hi; r += nt) {
             const int i0 = max(lo, r - 1);
             if (i0 >= hi) continue;
             double2 x = TT(r, i0);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
         const int base = s_cnt;
         for (int t = tid; t < hi - lo; t += nt) {
             Rot64 g;
-            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = (lo << 16) | hi;  // the sweep's window
+            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = 0;
             log[base + t] = g;
         }
         __syncthreads();
@@ -313,51 +313,6 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
 }
 
 constexpr int kLogChunk = 256;  // rotation-log entries staged in shared memory at a time
-
-// The updates the window-restricted sweeps left out, from the rotation log: rows above a sweep's
-// window receive its rotations from the right (phase 0, one row per thread), columns right of it
-// from the left (phase 1, one column per thread).  An entry can owe both kinds; left and right
-// rotations commute, so applying every row's right rotations first and then every column's left
-// rotations, each kind in log order, gives the full update.  Entries inside a later window never
-// owe anything (windows are nested or disjoint), so the sweeps never read a stale entry.
-__global__ void __launch_bounds__(32) k_schur_defer64(SchurArgs a, int phase) {
-    extern __shared__ double2 q64[];  // [m][RPC], then the log chunk
-    constexpr int RPC = 4;
-    if (*a.nconv < 0) return;
-    const int m = a.m, t = threadIdx.x, r = blockIdx.x * RPC + t;
-    const bool lane_on = t < RPC && r < m;
-    Rot64* slog = reinterpret_cast<Rot64*>(q64 + (size_t)m * RPC);
-    const Rot64* log = reinterpret_cast<const Rot64*>(a.log);
-    // phase 0: v = row r of T (stride m); phase 1: v = column r (contiguous)
-    if (lane_on)
-        for (int k = 0; k < m; ++k)
-            q64[k * RPC + t] = phase == 0 ? a.H[(size_t)k * m + r] : a.H[(size_t)r * m + k];
-    const int nrot = *a.log_count;
-    for (int k0 = 0; k0 < nrot; k0 += kLogChunk) {
-        const int cnt = min(kLogChunk, nrot - k0);
-        for (int i = t; i < cnt; i += 32) slog[i] = log[k0 + i];
-        __syncwarp();
-        if (lane_on) {
-            for (int k = 0; k < cnt; ++k) {
-                const Rot64 g = slog[k];
-                const int lo = g.pad >> 16, hi = g.pad & 0xFFFF;
-                if (phase == 0 ? (r >= lo) : (r <= hi)) continue;
-                double2 x = q64[g.i * RPC + t], y = q64[(g.i + 1) * RPC + t];
-                if (phase == 0) crot64(x, y, g.c, conj(g.s));  // columns (i, i+1) of row r
-                else crot64(x, y, g.c, g.s);                   // rows (i, i+1) of column r
-                q64[g.i * RPC + t] = x;
-                q64[(g.i + 1) * RPC + t] = y;
-            }
-        }
-        __syncwarp();
-    }
-    if (lane_on)
-        for (int k = 0; k < m; ++k) {
-            const double2 v = q64[k * RPC + t];
-            if (phase == 0) a.H[(size_t)k * m + r] = v;
-            else a.H[(size_t)r * m + k] = v;
-        }
-}
 
 // Reordering: bring the keep Ritz values of largest |mu| to the front of the upper triangular T by
 // adjacent swaps (ties resolve to the lower index), appending each swap's rotation to the log.
@@ -523,12 +478,6 @@ int launch_schur64(const SchurArgs& a, cudaStream_t s) {
     prof_begin("schur_qr", s);
     k_schur_qr64<<<1, 256, packed, s>>>(a); note_launch();
     prof_end("schur_qr", s);
-    prof_begin("schur_defer", s);
-    for (int phase = 0; phase < 2; ++phase) {
-        k_schur_defer64<<<(m + 3) / 4, 32, sizeof(double2) * 4 * m + sizeof(Rot64) * kLogChunk, s>>>(a, phase);
-        note_launch();
-    }
-    prof_end("schur_defer", s);
     prof_begin("schur_reorder", s);
     k_schur_reorder64<<<1, 256, packed, s>>>(a); note_launch();
     prof_end("schur_reorder", s);

@@ -232,3 +232,26 @@ def test_mixed_residual_tensor_core_matches_cuda_core(klst, spec, sigma, monkeyp
         out.append(to_host(F.apply(X)))
     err = np.abs(out[0] - out[1]).max(axis=1) / np.abs(out[1]).max(axis=1)
     assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("spec,sigma", [SMALL[0], SMALL[2], SMALL[4], NX128[1]], ids=["9x4x2", "33x9x6", "48x10x6", "128x6x4"])
+def test_fp64_tensor_core_solve_matches_cuda_core(klst, spec, sigma, monkeypatch):
+    """The float64 block solves on the tensor cores (integer slices of K_k^{-1}, the default) and as
+    complex128 products on the float64 pipe (KLST_NO_TC=1) give the same T x at float64 level, on
+    ragged Nx (9, 33) and full 128-row tiles, with 1, 2 and 3 right-hand sides (odd counts leave
+    a CTA's second slot empty)."""
+    P = klst.Pencil(spec)
+    for nrhs in (1, 2, 3):
+        X = to_dev(wl.random_vectors(spec.n, nrhs, 41 + nrhs))
+        out = []
+        for env in ("0", "1"):
+            monkeypatch.setenv("KLST_NO_TC", env)
+            F = P.factor(sigma, precision=klst.FP64)
+            klst.prof_reset()
+            klst.prof_enable(True)
+            out.append(to_host(F.apply(X)))
+            klst.prof_enable(False)
+            groups = klst.prof_read()
+            assert ("solve_pass1_tc" in groups) == (env == "0"), sorted(groups)
+        err = np.abs(out[0] - out[1]).max(axis=-1) / np.abs(out[1]).max(axis=-1)
+        assert np.all(err <= 1e-12), (nrhs, err)
