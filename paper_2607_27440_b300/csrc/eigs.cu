@@ -388,8 +388,8 @@ struct EigsWork {
     double2 *Va = nullptr, *Vb = nullptr, *S = nullptr, *H = nullptr, *Q = nullptr, *Yc = nullptr, *mu = nullptr;
     double2 *Ysel = nullptr, *musel = nullptr, *Vh = nullptr;
     double *estsel = nullptr, *tau = nullptr;
-    Rot* rlog = nullptr;
-    int* rcount = nullptr;
+    Rot *rlog = nullptr, *rlog2 = nullptr;
+    int *rcount = nullptr, *loff = nullptr, *rdy = nullptr;
     double* npart2 = nullptr;
     int *gate = nullptr, *reorth = nullptr;
     double2 *h = nullptr, *dpart = nullptr, *X = nullptr, *Z = nullptr, *R = nullptr, *om = nullptr;
@@ -509,6 +509,11 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             sc.take(W.tau, m);
             sc.take(W.rlog, log_cap);
             sc.take(W.rcount, 4);
+            if (!dfm) {
+                sc.take(W.rlog2, log_cap);
+                sc.take(W.loff, (size_t)log_cap + 1);
+                sc.take(W.rdy, 256);
+            }
             sc.take(W.npart2, std::max(nblk, 1));
             sc.take(W.gate, 4);
             sc.take(W.reorth, 4);
@@ -688,6 +693,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
         a.m = m; a.lds = lds; a.S = W.S; a.H = W.H; a.Q = W.Q; a.Yc = W.Yc; a.mu = W.mu; a.est = W.est;
         a.Ysel = W.Ysel; a.mu_sel = W.musel; a.est_sel = W.estsel;
         a.Vh = (float4*)W.Vh; a.tau = W.tau; a.log = W.rlog; a.log_cap = log_cap; a.log_count = W.rcount;
+        a.log2 = W.rlog2; a.loff = W.loff; a.rdy = W.rdy;
         a.nconv = W.nconv; a.keep = keep; a.nev = nev; a.tol = o->tol; a.conv = o->conv; a.st = f->status;
         cudaEventRecord(evs[3 * (m + 1)], s);
         // the small Schur step runs in the basis arithmetic: float64 for the float64 basis

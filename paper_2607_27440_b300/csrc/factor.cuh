@@ -66,7 +66,12 @@ struct SchurArgs {
     double* tau;       // m: Householder scalars (0 = no reflection)
     Rot* log;          // Givens rotations of the QR sweeps and the reordering, in order
     int log_cap;
-    int* log_count;
+    int* log_count;    // [0] rotations, [1] QR sweeps, [2] swaps, [3] replay levels (float64 step)
+    // float64 step: the log sorted by replay level (rotations of one level act on disjoint index
+    // pairs), the level ends, and the per-index level counters the sweeps and swaps update
+    Rot* log2;
+    int* loff;         // log_cap + 1
+    int* rdy;          // 256
 };
 
 int launch_schur(const SchurArgs& a, cudaStream_t s);    // double-float sweeps (schur.cu)

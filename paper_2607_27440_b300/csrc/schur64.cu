@@ -174,7 +174,67 @@ __global__ void __launch_bounds__(256) k_schur_house64(SchurArgs a) {
 // Packed upper-Hessenberg storage in shared memory: column j keeps rows 0..j+1 at offset j(j+3)/2.
 __device__ __forceinline__ int pk64(int i, int j) { return j * (j + 3) / 2 + i; }
 
-__global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
+// One component of the rotation [x; y] <- [c s; -conj(s) c] [x; y] (crot64's operation order):
+// q = 0, 1: Re x', Im x'; q = 2, 3: Re y', Im y' -- three float64 operations each, so four lanes
+// rotate one pair at a quarter of the float64 instructions per warp.  Every lane runs the same
+// w = P1 Q1 + (P2 Q2 + P3 Q3) with its operands picked by selects (off the float64 pipe): lanes
+// taking different arithmetic paths would each issue their own float64 instructions.
+__device__ __forceinline__ double crot64_part(double2 x, double2 y, double c, double2 s, int q) {
+    const bool lo = q < 2, odd = q & 1;
+    const double p1 = lo ? c : -s.x;
+    const double q1 = odd ? x.y : x.x;
+    const double p2 = lo ? s.x : (odd ? s.y : -s.y);
+    const double q2 = lo ? (odd ? y.y : y.x) : (odd ? x.x : x.y);
+    const double p3 = lo ? (odd ? s.y : -s.y) : c;
+    const double q3 = lo ? (odd ? y.x : y.y) : (odd ? y.y : y.x);
+    return fma(p1, q1, fma(p2, q2, p3 * q3));
+}
+
+// givens64 by a whole warp (every lane passes the same f, g): lane parity splits the two squared
+// moduli and the two reciprocal square roots, lanes 0, 1, 2 form Re s, Im s and c with one shared
+// instruction shape, and the thresholds compare bit patterns (non-negative float64 values order
+// like their bits), so the dependent chain holds eleven float64 instructions instead of
+// twenty-four.  Same convention and edge cases as givens64.
+__device__ void givens64_warp(double2 f, double2 g, double& c, double2& s) {
+    const int lane = threadIdx.x & 31, h = lane & 1;
+    const double2 u = h ? g : f;
+    const double a2 = fma(u.x, u.x, u.y * u.y);
+    const double o2 = __shfl_xor_sync(0xffffffffu, a2, 1);
+    const double af2 = h ? o2 : a2, ag2 = h ? a2 : o2;
+    const long long tiny = 0x03C2000000000000ll;  // bits of 2^-963 ~ 1e-290
+    if (__double_as_longlong(ag2) <= tiny) { c = 1.0; s = make_double2(0.0, 0.0); return; }
+    if (__double_as_longlong(af2) <= tiny) {
+        const double ig = rsqrt64(ag2);
+        c = 0.0;
+        s = make_double2(g.x * ig, -g.y * ig);
+        return;
+    }
+    const double rr = rsqrt64(h ? af2 : af2 + ag2);  // lane 0: 1 / r, lane 1: 1 / |f|
+    const double ro = __shfl_xor_sync(0xffffffffu, rr, 1);
+    const double q = rr * ro;                          // 1 / (|f| r)
+    // lane 0: Re(f conj g), lane 1: Im(f conj g), lane 2: |f|^2, each times q
+    const int k = lane & 3;
+    const double p1 = k == 0 ? f.x : (k == 1 ? f.y : af2);
+    const double q1 = k == 2 ? 1.0 : g.x;
+    const double p2 = k == 0 ? f.y : (k == 1 ? -f.x : 0.0);
+    const double v = fma(p1, q1, p2 * g.y) * q;
+    c = __shfl_sync(0xffffffffu, v, 2);
+    s = make_double2(__shfl_sync(0xffffffffu, v, 0), __shfl_sync(0xffffffffu, v, 1));
+}
+
+constexpr int kQrThreads = 512;               // 16 warps; the 12 off the first scheduler rotate
+constexpr int kQrSlots = (kQrThreads / 32 / 4) * 3 * 8;  // element pairs per pass (4 lanes each)
+
+// Shifted QR sweeps (explicit single shift, Wilkinson / exceptional shifts, float64 deflation).
+// Within a sweep on the active window [lo, hi], step i applies left rotation i to rows (i, i+1)
+// of every column right of i-1 and, pipelined two steps behind, right rotation i-2 to columns
+// (i-2, i-1) of every row above i: column i-1 of R is final once left rotation i-1 is in, and
+// the two kinds touch disjoint entries within a step.  Each entry pair is rotated by four lanes
+// of a warp that does not share a scheduler with warp 0 (a float64 instruction holds a warp's
+// scheduler for 64 cycles whatever the number of active lanes), while warp 0 rotates the pivot
+// column i+1 and forms rotation i+1 from it, the only dependent chain of the step.  The shift is
+// added back to each diagonal entry when its last rotation has been applied.
+__global__ void __launch_bounds__(kQrThreads) k_schur_qr64(SchurArgs a) {
     extern __shared__ double2 sT64[];
     const int m = a.m, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
     Rot64* log = reinterpret_cast<Rot64*>(a.log);
@@ -182,13 +242,18 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
     __shared__ double2 rs[192];
     __shared__ double2 s_mu;
     __shared__ int s_lo, s_fail, s_cnt;
+    __shared__ int rdy[192], lvb[192];  // replay level bookkeeping (see k_schur_levels64)
 #define TT(i, j) sT64[pk64(i, j)]
     for (int j = 0; j < m; ++j)
         for (int i = tid; i <= min(j + 1, m - 1); i += nt) TT(i, j) = a.H[(size_t)j * m + i];
+    for (int i = tid; i < m; i += nt) rdy[i] = 0;
     if (tid == 0) { s_fail = 0; s_cnt = 0; }
     __syncthreads();
     const double2 zero2 = make_double2(0.0, 0.0);
     const double eps = 2.220446049250313e-16;  // float64 ulp(1): LAPACK's deflation threshold
+    // rotation lanes: warps not on the first scheduler, four lanes per entry pair
+    const bool rot_lane = (wid & 3) != 0;
+    const int slot = ((wid >> 2) * 3 + (wid & 3) - 1) * 8 + (lane >> 2), comp = lane & 3;
     int hi = m - 1, its = 0, total = 0;
     const int max_total = 30 * m;
     while (hi > 0) {
@@ -241,56 +306,94 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
         const double2 mu = s_mu;
         for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = TT(i, i) - mu;
         __syncthreads();
-        if (tid == 0) {
+        if (wid == 0) {
             double c;
             double2 sv;
-            givens64(TT(lo, lo), TT(lo + 1, lo), c, sv);
-            rc[lo] = c;
-            rs[lo] = sv;
+            givens64_warp(TT(lo, lo), TT(lo + 1, lo), c, sv);
+            if (lane == 0) { rc[lo] = c; rs[lo] = sv; }
         }
         __syncthreads();
-        // left sweep: rotation i on rows i, i+1 (columns i..m-1); the thread holding column i+1
-        // forms rotation i+1 from its freshly rotated diagonal entry.  (Restricting the sweeps to
-        // the active window and replaying the rest from the log on other SMs was measured slower:
-        // the sweep's cost is its chain of float64 instructions, which the window does not shorten.)
-        for (int i = lo; i < hi; ++i) {
-            const int col = i + tid;
-            if (col < m) {
-                const double c = rc[i];
-                const double2 sv = rs[i];
-                double2 x = TT(i, col), y = TT(i + 1, col);
-                crot64(x, y, c, sv);
-                TT(i, col) = x;
-                TT(i + 1, col) = (col == i) ? zero2 : y;
-                if (col == i + 1 && i + 1 < hi) {
+        for (int i = lo; i <= hi + 1; ++i) {
+            const int k = i - 2;                                  // right rotation of this step
+            const int nl = (i <= hi - 1) ? m - i : 0;             // left: columns i..m-1
+            const int nr = (k >= lo && k <= hi - 1) ? k + 2 : 0;  // right: rows 0..k+1
+            if (rot_lane) {
+                // at most two passes (m <= 160 < 2 kQrSlots): read and rotate both, then write.  Left
+                // and right items take the same instruction path (operands chosen by selects).
+                int row[2], col[2];
+                double v[2];
+                bool on[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int it = slot + u * kQrSlots;
+                    on[u] = false;
+                    // a warp with no item in this pass issues nothing (uniform over the warp)
+                    if ((slot & ~7) + u * kQrSlots >= nl + nr) continue;
+                    const bool left = it < nl && i + it != i + 1;  // warp 0 owns the pivot column
+                    const bool right = it >= nl && it < nl + nr;
+                    on[u] = left || right;
+                    // left: rows (i, i+1) of column i+it; right: columns (k, k+1) of row it-nl
+                    const int rx = left ? i : it - nl, ry = left ? i + 1 : it - nl;
+                    const int cx = left ? i + it : k, cy = left ? i + it : k + 1;
+                    const int rr = left ? i : k;  // rotation index
+                    double2 x = make_double2(0.0, 0.0), y = x, sv = x;
+                    double cv = 1.0;
+                    if (on[u]) {
+                        x = TT(rx, cx);
+                        y = TT(ry, cy);
+                        cv = rc[rr];
+                        sv = left ? rs[rr] : conj(rs[rr]);
+                    }
+                    double w = crot64_part(x, y, cv, sv, comp);
+                    if (left && cx == i && comp >= 2) w = 0.0;  // the annihilated subdiagonal entry
+                    if (right) {
+                        // a diagonal entry is final after its last right rotation: add the shift back
+                        const int r = it - nl;
+                        if (r == k && comp < 2) w += comp == 0 ? mu.x : mu.y;
+                        if (r == k + 1 && k + 1 == hi && comp >= 2) w += comp == 2 ? mu.x : mu.y;
+                    }
+                    row[u] = comp < 2 ? rx : ry;
+                    col[u] = comp < 2 ? cx : cy;
+                    v[u] = w;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (on[u]) {
+                        double* e = reinterpret_cast<double*>(&TT(row[u], col[u]));
+                        e[comp & 1] = v[u];
+                    }
+            } else if (wid == 0 && i <= hi - 1) {
+                // the pivot column i+1: rotated by lanes 0..3, then rotation i+1 from its new diagonal
+                const double2 x = TT(i, i + 1), y = TT(i + 1, i + 1);
+                const double w = crot64_part(x, y, rc[i], rs[i], comp);
+                const double yr = __shfl_sync(0xffffffffu, w, 2), yi = __shfl_sync(0xffffffffu, w, 3);
+                if (lane < 4) reinterpret_cast<double*>(&TT(comp < 2 ? i : i + 1, i + 1))[comp & 1] = w;
+                if (i + 1 <= hi - 1) {
                     double c2;
                     double2 s2;
-                    givens64(y, TT(i + 2, i + 1), c2, s2);
-                    rc[i + 1] = c2;
-                    rs[i + 1] = s2;
+                    givens64_warp(make_double2(yr, yi), TT(i + 2, i + 1), c2, s2);
+                    if (lane == 0) { rc[i + 1] = c2; rs[i + 1] = s2; }
                 }
             }
             __syncthreads();
         }
-        // right sweep in bulk: row r receives rotations i >= max(lo, r - 1), in order
-        for (int r = tid; r <= hi; r += nt) {
-            const int i0 = max(lo, r - 1);
-            if (i0 >= hi) continue;
-            double2 x = TT(r, i0);
-            for (int i = i0; i < hi; ++i) {
-                double2 y = TT(r, i + 1);
-                crot64(x, y, rc[i], conj(rs[i]));
-                TT(r, i) = x;
-                x = y;
+        if (tid == 0) {
+            // replay level of rotation j: one past the last level that touched index j or j+1
+            int lv = max(rdy[lo], rdy[lo + 1]);
+            lvb[lo] = lv;
+            for (int j = lo + 1; j < hi; ++j) {
+                lv = max(lv + 1, rdy[j + 1]);
+                lvb[j] = lv;
             }
-            TT(r, hi) = x;
+            for (int j = lo; j < hi; ++j) rdy[j] = lvb[j] + 1;
+            rdy[hi] = lvb[hi - 1] + 1;
         }
         __syncthreads();
-        for (int i = lo + tid; i <= hi; i += nt) TT(i, i) = TT(i, i) + mu;
         const int base = s_cnt;
         for (int t = tid; t < hi - lo; t += nt) {
             Rot64 g;
-            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = 0;
+            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = lvb[lo + t];
             log[base + t] = g;
         }
         __syncthreads();
@@ -308,160 +411,275 @@ __global__ void __launch_bounds__(256) k_schur_qr64(SchurArgs a) {
         const int i = idx % m, j = idx / m;
         a.H[idx] = (i <= j) ? TT(i, j) : zero2;
     }
+    for (int i = tid; i < m; i += nt) a.rdy[i] = rdy[i];
     if (tid == 0) { *a.log_count = s_cnt; a.log_count[1] = total; }
 #undef TT
 }
 
-constexpr int kLogChunk = 256;  // rotation-log entries staged in shared memory at a time
-
-// Reordering: bring the keep Ritz values of largest |mu| to the front of the upper triangular T by
-// adjacent swaps (ties resolve to the lower index), appending each swap's rotation to the log.
-__global__ void __launch_bounds__(256) k_schur_reorder64(SchurArgs a) {
+// Reordering: bring the keep Ritz values of largest |mu| to the front of the upper triangular T in
+// descending |mu| (ties to the lower index), the others after them in their original order -- the
+// order a selection of the largest remaining |mu| with adjacent swaps produces.  Every diagonal
+// entry gets its target position, and an odd-even transposition network sorts by it: in each
+// round the out-of-order pairs (i, i+1) of one parity swap together (LAPACK ztrexc's rotation for
+// each).  Swaps of a round touch disjoint row pairs on the left and disjoint column pairs on the
+// right, and their rotations are formed from entries no other swap of the round changes; all
+// left rotations go first, then all right ones, since both can hit one entry.  Entry pairs are
+// rotated by four lanes each (crot64_part), and every swap's rotation is logged in round order.
+constexpr int kReThreads = 512;
+__global__ void __launch_bounds__(kReThreads) k_schur_reorder64(SchurArgs a) {
     extern __shared__ double2 sT64[];
-    const int m = a.m, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int m = a.m, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     if (*a.nconv < 0) return;  // the QR sweeps failed; the host reports it
     Rot64* log = reinterpret_cast<Rot64*>(a.log);
-    __shared__ double s_c;
-    __shared__ double2 s_s;
-    __shared__ int s_q, s_fail, s_cnt, s_swaps;
+    __shared__ int tgt[192], rnk[192], sw_i[96], offL[97], offR[97];
+    __shared__ unsigned long long key[192];
+    __shared__ double sw_c[96];
+    __shared__ double2 sw_s[96];
+    __shared__ int s_ns, s_fail, s_cnt, s_swaps;
+    __shared__ int rdy[192], sw_lv[96];
 #define TT(i, j) sT64[pk64(i, j)]
     for (int j = 0; j < m; ++j)
         for (int i = tid; i <= min(j + 1, m - 1); i += nt) TT(i, j) = a.H[(size_t)j * m + i];
+    // |mu|^2 as an ordering key (non-negative float64 orders like its bits)
+    for (int i = tid; i < m; i += nt) {
+        const double2 d = a.H[(size_t)i * m + i];
+        key[i] = (unsigned long long)__double_as_longlong(fma(d.x, d.x, d.y * d.y));
+    }
+    for (int i = tid; i < m; i += nt) rdy[i] = a.rdy[i];
     if (tid == 0) { s_fail = 0; s_cnt = *a.log_count; s_swaps = 0; }
     __syncthreads();
-    const double2 zero2 = make_double2(0.0, 0.0);
-    for (int p = 0; p < a.keep; ++p) {
-        if (wid == 0) {
-            double bv = -1.0;
-            int q = p;
-            for (int i = p + lane; i < m; i += 32) {
-                const double v = abs2(TT(i, i));
-                if (v > bv) { bv = v; q = i; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int oq = __shfl_xor_sync(0xffffffffu, q, o);
-                if (ov > bv || (ov == bv && oq < q)) { bv = ov; q = oq; }
-            }
-            if (lane == 0) {
-                s_q = q;
-                if (s_cnt + (q - p) > a.log_cap) { s_fail = 2; s_q = p; }
+    // target positions: the rank in descending |mu| (ties to the lower index) for the keep largest;
+    // keep + the number of unselected entries before i for the others
+    for (int i = tid; i < m; i += nt) {
+        int rank = 0;
+        for (int j = 0; j < m; ++j) rank += (key[j] > key[i] || (key[j] == key[i] && j < i)) ? 1 : 0;
+        rnk[i] = rank;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) {
+        int r = rnk[i];
+        if (r >= a.keep) {
+            int u = 0;
+            for (int j = 0; j < i; ++j) u += rnk[j] >= a.keep ? 1 : 0;
+            r = a.keep + u;
+        }
+        tgt[i] = r;
+    }
+    const int comp = lane & 3, slot = tid >> 2, nslot = nt >> 2;
+    for (int round = 0, parity = 0, quiet = 0; quiet < 2 && round <= m + 1; ++round, parity ^= 1) {
+        __syncthreads();  // every thread has read the previous round's s_ns
+        // the swaps of this round, in increasing i
+        if (tid == 0) {
+            int ns = 0;
+            for (int i = parity; i + 1 < m; i += 2)
+                if (tgt[i] > tgt[i + 1]) sw_i[ns++] = i;
+            s_ns = ns;
+            if (s_cnt + ns > a.log_cap) { s_fail = 2; s_ns = 0; }
+            offL[0] = 0; offR[0] = 0;
+            for (int q = 0; q < s_ns; ++q) {
+                offL[q + 1] = offL[q] + (m - 2 - sw_i[q]);
+                offR[q + 1] = offR[q] + sw_i[q];
             }
         }
         __syncthreads();
-        const int q = s_q;
-        for (int i = q - 1; i >= p; --i) {
-            if (tid == 0) {
-                double c;
-                double2 sv;
-                givens64(TT(i, i + 1), TT(i + 1, i + 1) - TT(i, i), c, sv);
-                s_c = c;
-                s_s = sv;
-                Rot64 g;
-                g.s = sv; g.c = c; g.i = i; g.pad = 0;
-                log[s_cnt] = g;
-                s_cnt = s_cnt + 1;
-                s_swaps = s_swaps + 1;
-            }
-            __syncthreads();
-            const double c = s_c;
-            const double2 sv = s_s, sc = conj(sv);
-            const double2 t11 = TT(i, i), t22 = TT(i + 1, i + 1);
-            for (int idx = tid; idx < (m - i - 2) + i; idx += nt) {
-                if (idx < m - i - 2) {
-                    const int col = i + 2 + idx;
-                    double2 x = TT(i, col), y = TT(i + 1, col);
-                    crot64(x, y, c, sv);
-                    TT(i, col) = x; TT(i + 1, col) = y;
-                } else {
-                    const int row = idx - (m - i - 2);
-                    double2 x = TT(row, i), y = TT(row, i + 1);
-                    crot64(x, y, c, sc);
-                    TT(row, i) = x; TT(row, i + 1) = y;
+        const int ns = s_ns;
+        quiet = ns == 0 ? quiet + 1 : 0;
+        if (ns == 0) { if (s_fail) break; continue; }
+        for (int q = tid; q < ns; q += nt) {
+            const int i = sw_i[q];
+            double c;
+            double2 sv;
+            givens64(TT(i, i + 1), TT(i + 1, i + 1) - TT(i, i), c, sv);
+            sw_c[q] = c;
+            sw_s[q] = sv;
+            const int lv = max(rdy[i], rdy[i + 1]);  // the swaps of a round touch disjoint pairs
+            sw_lv[q] = lv;
+            Rot64 g;
+            g.s = sv; g.c = c; g.i = i; g.pad = lv;
+            log[s_cnt + q] = g;
+        }
+        __syncthreads();
+        // left rotations: rows (i, i+1) of columns i+2..m-1, then right: columns (i, i+1) of rows 0..i-1
+        for (int phase = 0; phase < 2; ++phase) {
+            const int* off = phase == 0 ? offL : offR;
+            const int total = off[ns];
+            for (int base = 0; base < total; base += nslot) {
+                if (base + (slot & ~7) >= total) continue;  // nothing for this warp (uniform)
+                const int it = base + slot;
+                int rw = 0, cl = 0;
+                double v = 0.0;
+                const bool on = it < total;
+                if (on) {
+                    int lo = 0, hi = ns - 1;  // the swap q with off[q] <= it < off[q + 1]
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (off[mid] <= it) lo = mid; else hi = mid - 1;
+                    }
+                    const int i = sw_i[lo], u = it - off[lo];
+                    if (phase == 0) {
+                        const int col = i + 2 + u;
+                        v = crot64_part(TT(i, col), TT(i + 1, col), sw_c[lo], sw_s[lo], comp);
+                        rw = comp < 2 ? i : i + 1;
+                        cl = col;
+                    } else {
+                        const int row = u;
+                        v = crot64_part(TT(row, i), TT(row, i + 1), sw_c[lo], conj(sw_s[lo]), comp);
+                        rw = row;
+                        cl = comp < 2 ? i : i + 1;
+                    }
                 }
+                __syncwarp();
+                if (on) reinterpret_cast<double*>(&TT(rw, cl))[comp & 1] = v;
+                __syncwarp();
             }
-            __syncthreads();
-            if (tid == 0) { TT(i, i) = t22; TT(i + 1, i + 1) = t11; }
             __syncthreads();
         }
+        for (int q = tid; q < ns; q += nt) {
+            const int i = sw_i[q];
+            const double2 t11 = TT(i, i);
+            TT(i, i) = TT(i + 1, i + 1);
+            TT(i + 1, i + 1) = t11;
+            const int tg = tgt[i];
+            tgt[i] = tgt[i + 1];
+            tgt[i + 1] = tg;
+            rdy[i] = rdy[i + 1] = sw_lv[q] + 1;
+        }
+        __syncthreads();
+        if (tid == 0) { s_cnt += ns; s_swaps += ns; }
+        __syncthreads();
     }
     if (s_fail) {
         if (tid == 0) { atomicOr(&a.st->flags, ST_NOCONV_QR); *a.nconv = -1; *a.log_count = 0; }
         return;
     }
+    const double2 zero2 = make_double2(0.0, 0.0);
     for (int idx = tid; idx < m * m; idx += nt) {
         const int i = idx % m, j = idx / m;
         a.H[idx] = (i <= j) ? TT(i, j) : zero2;
     }
-    if (tid == 0) { *a.log_count = s_cnt; a.log_count[2] = s_swaps; }
+    if (tid == 0) {
+        int nlev = 0;
+        for (int i = 0; i < m; ++i) nlev = max(nlev, rdy[i]);
+        *a.log_count = s_cnt;
+        a.log_count[2] = s_swaps;
+        a.log_count[3] = nlev;
+    }
 #undef TT
 }
 
 // ---------------------------------------------------------------- 3. Schur vectors
-// Row r of Q = e_r^T H_0 H_1 ... H_{m-3} G_1^H G_2^H ...: the reflectors, then every logged rotation
-// in order.  One warp per CTA, four rows per CTA (the float64 pipe of one SM serves few lanes, so
-// the rows are spread over many SMs); a row lives in shared memory.  The rotation log is staged
-// into shared memory 256 entries at a time by the whole warp, so the serial replay of the four
-// rows reads its rotations from shared memory instead of waiting on L2 for each one.
-__global__ void __launch_bounds__(32) k_schur_q64(SchurArgs a) {
-    extern __shared__ double2 q64[];  // [m][RPC], then the log chunk
-    constexpr int RPC = 4;
-    const int m = a.m, t = threadIdx.x, r = blockIdx.x * RPC + t;
-    const bool row_lane = t < RPC;
-    Rot64* slog = reinterpret_cast<Rot64*>(q64 + (size_t)m * RPC);
+// Replay levels.  Row r of Q is e_r^T H_0 H_1 ... H_{m-3} G_1^H G_2^H ... (the reflectors, then every
+// logged rotation in order).  A rotation acts on entries (i, i+1) of the row only, so two rotations
+// on disjoint pairs commute: the sweeps and swaps above give rotation k the level one past the last
+// level that touched i or i+1, every rotation of one level acts on a disjoint pair, and replaying
+// the levels in order gives the same product (each entry sees its rotations in log order).  The
+// QR sweeps follow one another two indices apart, so the levels number about twice the sweeps
+// rather than the rotations.  One CTA sorts the log by level (counting sort; the order within a
+// level is immaterial), leaving in loff[l] the end of level l.
+__global__ void __launch_bounds__(1024) k_schur_levels64(SchurArgs a) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    if (*a.nconv < 0) return;
+    const int nrot = a.log_count[0], nlev = a.log_count[3];
     const Rot64* log = reinterpret_cast<const Rot64*>(a.log);
+    Rot64* out = reinterpret_cast<Rot64*>(a.log2);
+    __shared__ int wsum[32];
+    __shared__ int s_carry;
+    for (int l = tid; l <= nlev; l += nt) a.loff[l] = 0;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int k = tid; k < nrot; k += nt) atomicAdd(&a.loff[log[k].pad], 1);
+    __syncthreads();
+    // exclusive scan of the level counts, in place
+    for (int base = 0; base < nlev; base += nt) {
+        const int l = base + tid;
+        const int v = l < nlev ? a.loff[l] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < (nt >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;  // inclusive prefix of the warp totals
+        }
+        __syncthreads();
+        const int incl = x + (wid > 0 ? wsum[wid - 1] : 0);
+        if (l < nlev) a.loff[l] = s_carry + incl - v;
+        __syncthreads();
+        if (tid == nt - 1) s_carry += incl;
+        __syncthreads();
+    }
+    for (int k = tid; k < nrot; k += nt) {
+        const Rot64 g = log[k];
+        out[atomicAdd(&a.loff[g.pad], 1)] = g;
+    }
+}
+
+// One CTA per row of Q.  Warp 0 applies the reflectors (the lanes split each reflector's dot
+// product and update); then the CTA replays the levels: four lanes per rotation, one component
+// each (crot64_part), a level's rotations at once, the next level's bounds and entries loaded
+// while the current one is applied.
+constexpr int kQThreads = 256;
+__global__ void __launch_bounds__(kQThreads) k_schur_q64(SchurArgs a) {
+    extern __shared__ double2 qrow[];  // [m]
+    const int m = a.m, r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const double2* Vh = reinterpret_cast<const double2*>(a.Vh);
-    if (row_lane) {
-        for (int col = 0; col < m; ++col) q64[col * RPC + t] = make_double2(col == r ? 1.0 : 0.0, 0.0);
+    const Rot64* lg = reinterpret_cast<const Rot64*>(a.log2);
+    if (wid == 0) {
+        for (int col = lane; col < m; col += 32) qrow[col] = make_double2(col == r ? 1.0 : 0.0, 0.0);
+        __syncwarp();
         for (int c = 0; c + 2 < m; ++c) {
             const double tau = a.tau[c];
             if (tau == 0.0) continue;
             const double2* vc = Vh + (size_t)c * m;
-            double2 g0 = make_double2(0.0, 0.0), g1 = g0;
-            int i = c + 1;
-            for (; i + 1 < m; i += 2) {
-                cfma(g0, q64[i * RPC + t], vc[i]);
-                cfma(g1, q64[(i + 1) * RPC + t], vc[i + 1]);
-            }
-            if (i < m) cfma(g0, q64[i * RPC + t], vc[i]);
-            const double2 g = (-tau) * (g0 + g1);
-            for (i = c + 1; i < m; ++i) {
-                double2 qi = q64[i * RPC + t];
+            double2 g = make_double2(0.0, 0.0);
+            for (int i = c + 1 + lane; i < m; i += 32) cfma(g, qrow[i], vc[i]);
+            g = (-tau) * make_double2(warp_sum(g.x), warp_sum(g.y));
+            for (int i = c + 1 + lane; i < m; i += 32) {
+                double2 qi = qrow[i];
                 cfma(qi, g, conj(vc[i]));
-                q64[i * RPC + t] = qi;
+                qrow[i] = qi;
             }
+            __syncwarp();
         }
     }
-    // runs of rotations in planes (i, i+1), (i+1, i+2), ... carry column i+1 in registers
-    const int nrot = *a.log_count;
-    int ci = -1;
-    double2 cx = make_double2(0.0, 0.0);
-    for (int k0 = 0; k0 < nrot; k0 += kLogChunk) {
-        const int cnt = min(kLogChunk, nrot - k0);
-        for (int i = t; i < cnt; i += 32) slog[i] = log[k0 + i];  // the whole warp stages the chunk
-        __syncwarp();
-        if (row_lane) {
-            for (int k = 0; k < cnt; ++k) {
-                const Rot64 g = slog[k];
-                double2 x;
-                if (g.i == ci) x = cx;
-                else {
-                    if (ci >= 0) q64[ci * RPC + t] = cx;
-                    x = q64[g.i * RPC + t];
-                }
-                double2 y = q64[(g.i + 1) * RPC + t];
-                crot64(x, y, g.c, conj(g.s));
-                q64[g.i * RPC + t] = x;
-                ci = g.i + 1;
-                cx = y;
-            }
+    __syncthreads();
+    const int nlev = *a.nconv < 0 ? 0 : a.log_count[3];
+    const int grp = tid >> 2, comp = tid & 3, ngrp = kQThreads / 4;
+    int beg = 0;
+    int end = nlev > 0 ? a.loff[0] : 0;
+    Rot64 cur;
+    if (nlev > 0 && grp < end) cur = lg[grp];
+    for (int l = 0; l < nlev; ++l) {
+        // prefetch the next level's end and this thread's entry of it
+        const int nend = l + 1 < nlev ? a.loff[l + 1] : end;
+        Rot64 nxt;
+        if (l + 1 < nlev && end + grp < nend) nxt = lg[end + grp];
+        for (int k0 = beg; k0 < end; k0 += ngrp) {
+            if (k0 + (grp & ~7) >= end) continue;  // nothing for this warp (uniform)
+            const int k = k0 + grp;
+            const bool on = k < end;
+            const Rot64 g = k0 == beg ? cur : (on ? lg[k] : cur);
+            double w = 0.0;
+            if (on) w = crot64_part(qrow[g.i], qrow[g.i + 1], g.c, conj(g.s), comp);
+            __syncwarp();
+            if (on) reinterpret_cast<double*>(&qrow[comp < 2 ? g.i : g.i + 1])[comp & 1] = w;
+            __syncwarp();
         }
-        __syncwarp();  // the chunk is consumed before the next one overwrites it
+        __syncthreads();
+        beg = end;
+        end = nend;
+        cur = nxt;
     }
-    if (!row_lane) return;
-    if (ci >= 0) q64[ci * RPC + t] = cx;
-    if (r < m)
-        for (int col = 0; col < m; ++col) a.Q[(size_t)col * m + r] = q64[col * RPC + t];
+    for (int col = tid; col < m; col += kQThreads) a.Q[(size_t)col * m + r] = qrow[col];
 }
 
 int launch_schur64(const SchurArgs& a, cudaStream_t s) {
@@ -476,13 +694,14 @@ int launch_schur64(const SchurArgs& a, cudaStream_t s) {
     k_schur_house64<<<1, 256, 0, s>>>(a); note_launch();
     prof_end("schur_house", s);
     prof_begin("schur_qr", s);
-    k_schur_qr64<<<1, 256, packed, s>>>(a); note_launch();
+    k_schur_qr64<<<1, kQrThreads, packed, s>>>(a); note_launch();
     prof_end("schur_qr", s);
     prof_begin("schur_reorder", s);
-    k_schur_reorder64<<<1, 256, packed, s>>>(a); note_launch();
+    k_schur_reorder64<<<1, kReThreads, packed, s>>>(a); note_launch();
     prof_end("schur_reorder", s);
     prof_begin("schur_q", s);
-    k_schur_q64<<<(m + 3) / 4, 32, sizeof(double2) * 4 * m + sizeof(Rot64) * kLogChunk, s>>>(a); note_launch();
+    k_schur_levels64<<<1, 1024, 0, s>>>(a); note_launch();
+    k_schur_q64<<<m, kQThreads, sizeof(double2) * m, s>>>(a); note_launch();
     prof_end("schur_q", s);
     launch_schur_post(a, s);
     KLST_CK_LAUNCH();
