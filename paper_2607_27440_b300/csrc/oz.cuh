@@ -175,4 +175,44 @@ __device__ __forceinline__ double oz_combine(const float blk[OZ_S]) {
     return fma((double)L, exp2_neg7(9), (double)H * exp2_neg7(5));
 }
 
+// ---- nine-slice variant (63-bit fixed point): x ~= 2^e sum_{s=0..8} d_s 2^(-7 (s + 1)), |x| < 2^e
+constexpr int OZ_S9 = 9;
+
+__device__ __forceinline__ long long oz_fixed63(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0;
+    const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int sh = E - 1012 - e;         // F = x 2^(63 - e): |F| < 2^63 because |x| < 2^e
+    long long F;
+    if (sh >= 0) F = M << sh;            // sh <= 10
+    else F = (-sh >= 63) ? 0 : (M >> (-sh));
+    return b < 0 ? -F : F;
+}
+
+__device__ __forceinline__ void oz_digits9(long long F, int dig[OZ_S9]) {
+#pragma unroll
+    for (int s = OZ_S9 - 1; s >= 1; --s) {
+        const int d = (int)((F + 64) & 127) - 64;
+        dig[s] = d;
+        F = (F - d) >> 7;
+    }
+    dig[0] = (int)F;
+}
+
+// the exact sum_{d=0..8} blk[d] 2^(-7 (d + 2)) of nine diagonal blocks (integers below 2^24): the
+// leading four and the trailing five are combined exactly in 64-bit integers (below 2^46 and 2^53),
+// which float64 holds exactly, and one fused multiply-add rounds the sum once
+__device__ __forceinline__ double oz_combine9(const float blk[OZ_S9]) {
+    long long H = 0, L = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) H = H * 128 + (long long)__float2int_rn(blk[d]);
+#pragma unroll
+    for (int d = 4; d < 9; ++d) L = L * 128 + (long long)__float2int_rn(blk[d]);
+    return fma((double)L, exp2_neg7(10), (double)H * exp2_neg7(5));
+}
+
+// instruction descriptor of kind::f16 with the A operand MN-major (transpose bit 15)
+__host__ __device__ constexpr uint32_t idesc_bf16_amn(int M, int N) { return idesc_bf16(M, N) | (1u << 15); }
+
 }  // namespace klst

@@ -22,7 +22,7 @@
 #include <algorithm>
 #include <atomic>
 
-#include "oz.cuh"
+#include "tcstream.cuh"
 
 namespace klst {
 
@@ -83,73 +83,60 @@ struct TcSolveArgs {
     Status* st;
 };
 
-size_t tc_solve_smem(int nx) {
-    const size_t Kp = tc_kp(nx);
-    return 2 * Kp * 256 + Kp * 128 + 4 * (size_t)nx * sizeof(double2);
-}
-
-// PASS 1: z = K^{-1} (masked b), accumulating t_a(j) += sum_c w^c_a(j, k) z_c(j) per CTA.
+// The block solves as a tcstream policy: unit = velocity block k = g + i G; its loads are the
+// eight slices of K_k^{-1}, each in one or two K halves of at most 16 k-chunks (32 KB); B holds the
+// block's two right-hand sides split into eight slices, stacked along N ([kchunk][slice][8 cols]).
+// PASS 1: z = K^{-1} (masked b), running t_a(j) += sum_c w^c_a(j, k) z_c(j) per thread.
 // PASS 2: y = K^{-1} (masked b + sum_a G^c_a s_a).
 template <int PASS>
-__global__ void __launch_bounds__(128, 1) k_solve_tc(TcSolveArgs a) {
-    const int r0 = blockIdx.y * 2;
-    const bool on0 = r0 < a.nrhs && !(a.done && a.done[r0]);
-    const bool on1 = r0 + 1 < a.nrhs && !(a.done && a.done[r0 + 1]);
-    if (!on0 && !on1) return;  // uniform over the CTA, before any allocation
-    extern __shared__ __align__(128) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t bar_ld[2], bar_mma;
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_fail, s_emax[4];
-    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const int nx = a.nx, nxi = a.nxi, Kp = a.Kp, nkc = Kp / 8;
-    const int g = blockIdx.x, Gs = gridDim.x;
-    const uint32_t bytesA = (uint32_t)Kp * 256;
-    unsigned char* sA[2] = {tc_smem, tc_smem + bytesA};
-    unsigned char* sB = tc_smem + 2 * (size_t)bytesA;                  // [kchunk][8 slices][8 cols][16 B]
-    double2* sV = reinterpret_cast<double2*>(sB + (size_t)Kp * 128);  // [rhs in pair][g, h][nx]
-    constexpr uint32_t kCols = 128;                                    // 9 diagonal blocks x 8 columns
-    if (tid == 0) {
-        mbar_init(&bar_ld[0], 1);
-        mbar_init(&bar_ld[1], 1);
-        mbar_init(&bar_mma, 1);
-        s_fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+struct SolvePolicy {
+    static constexpr int stage_bytes = 32 * 1024;
+    static constexpr int nstages = 4;
+    static constexpr int b_bytes = 256 * 128;                       // Kp <= 256
+    static constexpr int x_bytes = 4 * 128 * 16 + 2 * 4 * 4 + 16;  // sV [4][nx] + exponents [2][4]
+    static constexpr int tmem_cols = 128;                           // 9 diagonal blocks x 8 columns
+    static constexpr uint32_t tmem_alloc = 256;
+    TcSolveArgs a;
+    int g, G, nblk, nh;      // CTA index, CTA count, its blocks, K halves per slice
+    int r0;
+    bool on0, on1;
+    double2 acc[2][4];       // PASS 1 running sums of t (epilogue threads)
+
+    __device__ int nunits() const { return nblk; }
+    __device__ int nloads(int) const { return OZ_S * nh; }
+    __device__ int kc_of(int h) const {  // k-chunks of half h
+        const int nkc = a.Kp / 8;
+        return nh == 1 ? nkc : (h == 0 ? 16 : nkc - 16);
     }
-    if (wid == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(kCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    __device__ const void* src(int i, int l) const {
+        const size_t k = (size_t)g + (size_t)i * G;
+        const int s = l / nh, h = l % nh;
+        return a.As + ((k * OZ_S + s) * (a.Kp / 8) + h * 16) * 1024;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = tmem_base;
-    const int nblk = (nxi - g + Gs - 1) / Gs;  // blocks k = g + i Gs
-    const int nsl = nblk * OZ_S;               // slices streamed by this CTA, in order
-    auto slice_src = [&](int q) {
-        const size_t k = (size_t)g + (size_t)(q / OZ_S) * Gs;
-        return a.As + ((k * OZ_S + (q % OZ_S)) * nkc) * 1024;
-    };
-    // thread 0's pipeline state: slice q lives in stage q & 1; its barrier phase is (q >> 1) & 1
-    int issued = 0, consumed = 0;
-    uint32_t ph_mma = 0;
-    if (tid == 0)
-        for (; issued < 2 && issued < nsl; ++issued) {
-            mbar_expect_tx(&bar_ld[issued], bytesA);
-            bulk_g2s(sA[issued], slice_src(issued), bytesA, &bar_ld[issued]);
+    __device__ uint32_t bytes(int, int l) const { return (uint32_t)kc_of(l % nh) * 2048; }
+    __device__ bool per_unit_b() const { return true; }
+    __device__ void mma(int, int l, uint32_t aB, uint32_t bB, uint32_t tcol) const {
+        const int s = l / nh, h = l % nh;
+        const int cnt = OZ_S - s, np = cnt + (cnt & 1);
+        const uint32_t idesc = idesc_bf16(128, np * TC_NB);
+        const uint32_t dcol = tcol + (uint32_t)(s * TC_NB);
+        const int ksteps = kc_of(h) / 2;
+        const uint32_t bh = bB + (uint32_t)(h * 16) * (OZ_S * TC_NB * 16);
+        for (int kk = 0; kk < ksteps; ++kk) {
+            const uint64_t ad = sdesc(aB + kk * 2 * 2048, 2048, 128);
+            const uint64_t bd = sdesc(bh + kk * 2 * (OZ_S * TC_NB * 16), OZ_S * TC_NB * 16, 128);
+            mma_bf16(dcol, ad, bd, idesc, (s > 0 || h > 0 || kk > 0) ? 1u : 0u);
         }
-    double2 acc[2][4];
-#pragma unroll
-    for (int rl = 0; rl < 2; ++rl)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[rl][q] = make_double2(0.0, 0.0);
-    const int j = wid * 32 + lane;  // the output row (TMEM lane) of this thread
-    for (int i = 0; i < nblk; ++i) {
-        const int k = g + i * Gs;
-        // 1. the block's right-hand sides in float64 (sV) and their largest exponents
-        if (tid < 4) s_emax[tid] = 0;
-        __syncthreads();
-        if (tid < nx) {
-            const bool bc = a.mask && is_bc(tid, nx, a.xi_x[k]);
+    }
+    __device__ int* emax(unsigned char* sX, int b) const { return reinterpret_cast<int*>(sX + 4 * 128 * 16) + b * 4; }
+    __device__ void prep(int i, unsigned char* sB, unsigned char* sX, int t) const {
+        const int nx = a.nx, nxi = a.nxi, k = g + i * G, nkc = a.Kp / 8;
+        double2* sV = reinterpret_cast<double2*>(sX);
+        int* em = emax(sX, i & 1);
+        if (t < 4) em[t] = 0;
+        epi_sync();
+        if (t < nx) {
+            const bool bc = a.mask && is_bc(t, nx, a.xi_x[k]);
 #pragma unroll
             for (int rl = 0; rl < 2; ++rl)
 #pragma unroll
@@ -157,29 +144,28 @@ __global__ void __launch_bounds__(128, 1) k_solve_tc(TcSolveArgs a) {
                     double2 v = make_double2(0.0, 0.0);
                     if (rl == 0 ? on0 : on1) {
                         const int rhs = r0 + rl;
-                        if (!bc) v = a.b[rhs * a.ldb + ((int64_t)c * nxi + k) * nx + tid];
+                        if (!bc) v = a.b[rhs * a.ldb + ((int64_t)c * nxi + k) * nx + t];
                         if (PASS == 2) {
-                            const double* Gk = a.G + (size_t)k * 8 * nx + tid;
+                            const double* Gk = a.G + (size_t)k * 8 * nx + t;
                             const double2* sr = a.sv + (size_t)rhs * 4 * nx;
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const double gv = Gk[(c * 4 + q) * nx];
-                                const double2 s = sr[q * nx + tid];
-                                v.x = fma(gv, s.x, v.x);
-                                v.y = fma(gv, s.y, v.y);
+                                const double2 sq = sr[q * nx + t];
+                                v.x = fma(gv, sq.x, v.x);
+                                v.y = fma(gv, sq.y, v.y);
                             }
                         }
                     }
-                    sV[(rl * 2 + c) * nx + tid] = v;
-                    atomicMax(&s_emax[rl * 2 + c], max(dexp(v.x), dexp(v.y)));
+                    sV[(rl * 2 + c) * nx + t] = v;
+                    atomicMax(&em[rl * 2 + c], max(dexp(v.x), dexp(v.y)));
                 }
         }
-        __syncthreads();
-        // 2. split B = [[Re v, Im v], [-Im v, Re v]] per vector into the stacked slice layout
-        for (int item = tid; item < nkc * TC_NB; item += 128) {
+        epi_sync();
+        for (int item = t; item < nkc * TC_NB; item += kTsEpi) {
             const int c = item & 7, kc = item >> 3;
             const int vec = c >> 1, part = c & 1;
-            const int e = s_emax[vec] - 1022;
+            const int e = em[vec] - 1022;
             const double2* vv = sV + vec * nx;
             int dig[8][OZ_S];
 #pragma unroll
@@ -191,118 +177,94 @@ __global__ void __launch_bounds__(128, 1) k_solve_tc(TcSolveArgs a) {
                 oz_digits(oz_fixed(x, e), dig[q]);
             }
 #pragma unroll
-            for (int t = 0; t < OZ_S; ++t) {
+            for (int s = 0; s < OZ_S; ++s) {
                 uint4 wv;
-                wv.x = bf16_of_int(dig[0][t]) | ((unsigned)bf16_of_int(dig[1][t]) << 16);
-                wv.y = bf16_of_int(dig[2][t]) | ((unsigned)bf16_of_int(dig[3][t]) << 16);
-                wv.z = bf16_of_int(dig[4][t]) | ((unsigned)bf16_of_int(dig[5][t]) << 16);
-                wv.w = bf16_of_int(dig[6][t]) | ((unsigned)bf16_of_int(dig[7][t]) << 16);
-                *reinterpret_cast<uint4*>(sB + ((size_t)(kc * OZ_S + t) * TC_NB + c) * 16) = wv;
+                wv.x = bf16_of_int(dig[0][s]) | ((unsigned)bf16_of_int(dig[1][s]) << 16);
+                wv.y = bf16_of_int(dig[2][s]) | ((unsigned)bf16_of_int(dig[3][s]) << 16);
+                wv.z = bf16_of_int(dig[4][s]) | ((unsigned)bf16_of_int(dig[5][s]) << 16);
+                wv.w = bf16_of_int(dig[6][s]) | ((unsigned)bf16_of_int(dig[7][s]) << 16);
+                *reinterpret_cast<uint4*>(sB + ((size_t)(kc * OZ_S + s) * TC_NB + c) * 16) = wv;
             }
         }
-        // the generic-proxy stores above must be visible to the tensor core's (async proxy) reads
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // 3. thread 0: slice s of the block times the stacked B slices t = 0..7-s (padded to an even
-        // count; the padding's products land in the unused ninth diagonal block) into blocks s..
-        if (tid == 0 && !s_fail) {
-            bool ok = true;
-            for (int s = 0; s < OZ_S && ok; ++s) {
-                const int q = i * OZ_S + s, stg = q & 1;
-                ok = mbar_wait(&bar_ld[stg], (uint32_t)((q >> 1) & 1));
-                if (!ok) break;
-                ++consumed;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int cnt = OZ_S - s, np = cnt + (cnt & 1);
-                const uint32_t idesc = idesc_bf16(128, np * TC_NB);
-                const uint32_t dcol = tbase + (uint32_t)(s * TC_NB);
-                const uint32_t aBase = smem_u32(sA[stg]), bBase = smem_u32(sB);
-                for (int kk = 0; kk < Kp / 16; ++kk) {
-                    const uint64_t ad = sdesc(aBase + kk * 2 * 2048, 2048, 128);
-                    const uint64_t bd = sdesc(bBase + kk * 2 * (OZ_S * TC_NB * 16), OZ_S * TC_NB * 16, 128);
-                    mma_bf16(dcol, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                }
-                mma_commit(&bar_mma);
-                ok = mbar_wait(&bar_mma, ph_mma);
-                ph_mma ^= 1;
-                if (!ok) break;
-                if (issued < nsl) {  // refill this stage with slice q + 2 (possibly of the next block)
-                    mbar_expect_tx(&bar_ld[stg], bytesA);
-                    bulk_g2s(sA[stg], slice_src(issued), bytesA, &bar_ld[stg]);
-                    ++issued;
-                }
-            }
-            if (!ok) {
-                s_fail = 1;
-                atomicOr(&a.st->flags, ST_TIMEOUT);
-                // one more bounded wait for every copy and MMA still in flight before TMEM and the
-                // shared buffers are released
-                for (int q = consumed; q < issued; ++q) mbar_wait(&bar_ld[q & 1], (uint32_t)((q >> 1) & 1));
-                mbar_wait(&bar_mma, ph_mma);
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (s_fail) break;
-        // 4. epilogue: row j of the block's 8 output columns, exact diagonal sums -> float64
-        float blk[OZ_S][8];
-        const uint32_t lane_off = (uint32_t)(wid * 32) << 16;
-#pragma unroll
-        for (int d = 0; d < OZ_S; ++d) tmem_ld8(tbase + lane_off + (uint32_t)(d * TC_NB), blk[d]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (j < nx) {
-            const int era = a.ea[(size_t)k * 128 + j];
-            double z[TC_NB];
-#pragma unroll
-            for (int c = 0; c < TC_NB; ++c) {
-                float col[OZ_S];
-#pragma unroll
-                for (int d = 0; d < OZ_S; ++d) col[d] = blk[d][c];
-                z[c] = scale2(oz_combine(col), era + s_emax[c >> 1] - 1022);
-            }
-#pragma unroll
-            for (int rl = 0; rl < 2; ++rl) {
-                if (!(rl == 0 ? on0 : on1)) continue;
-                const double2 zg = make_double2(z[rl * 4 + 0], z[rl * 4 + 1]);
-                const double2 zh = make_double2(z[rl * 4 + 2], z[rl * 4 + 3]);
-                if (PASS == 1) {
-                    const double* wk = a.w + (size_t)k * 8 * nx + j;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const double wg = wk[q * nx], wh = wk[(4 + q) * nx];
-                        acc[rl][q].x += wg * zg.x + wh * zh.x;
-                        acc[rl][q].y += wg * zg.y + wh * zh.y;
-                    }
-                } else {
-                    double2* yr = a.y + (r0 + rl) * a.ldb;
-                    const size_t ig = (size_t)k * nx + j, ih = ((size_t)nxi + k) * nx + j;
-                    if (a.accumulate) {
-                        yr[ig] = yr[ig] + zg;
-                        yr[ih] = yr[ih] + zh;
-                    } else {
-                        yr[ig] = zg;
-                        yr[ih] = zh;
-                    }
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (PASS == 1 && !s_fail && j < nx) {
+    __device__ void epilogue(int i, uint32_t tcol, unsigned char* sX, int quarter, int lane) {
+        const int nx = a.nx, nxi = a.nxi, k = g + i * G, j = quarter * 32 + lane;
+        float blk[OZ_S][8];
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+#pragma unroll
+        for (int d = 0; d < OZ_S; ++d) tmem_ld8(tcol + lane_off + (uint32_t)(d * TC_NB), blk[d]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (j >= nx) return;
+        const int* em = emax(sX, i & 1);
+        const int era = a.ea[(size_t)k * 128 + j];
+        double z[TC_NB];
+#pragma unroll
+        for (int c = 0; c < TC_NB; ++c) {
+            float col[OZ_S];
+#pragma unroll
+            for (int d = 0; d < OZ_S; ++d) col[d] = blk[d][c];
+            z[c] = scale2(oz_combine(col), era + em[c >> 1] - 1022);
+        }
 #pragma unroll
         for (int rl = 0; rl < 2; ++rl) {
             if (!(rl == 0 ? on0 : on1)) continue;
-            double2* tp = a.tpart + ((size_t)(r0 + rl) * a.ngroups + g) * 4 * nx + j;
+            const double2 zg = make_double2(z[rl * 4 + 0], z[rl * 4 + 1]);
+            const double2 zh = make_double2(z[rl * 4 + 2], z[rl * 4 + 3]);
+            if (PASS == 1) {
+                const double* wk = a.w + (size_t)k * 8 * nx + j;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tp[q * nx] = acc[rl][q];
+                for (int q = 0; q < 4; ++q) {
+                    const double wg = wk[q * nx], wh = wk[(4 + q) * nx];
+                    acc[rl][q].x += wg * zg.x + wh * zh.x;
+                    acc[rl][q].y += wg * zg.y + wh * zh.y;
+                }
+            } else {
+                double2* yr = a.y + (r0 + rl) * a.ldb;
+                const size_t ig = (size_t)k * nx + j, ih = ((size_t)nxi + k) * nx + j;
+                if (a.accumulate) {
+                    yr[ig] = yr[ig] + zg;
+                    yr[ih] = yr[ih] + zh;
+                } else {
+                    yr[ig] = zg;
+                    yr[ih] = zh;
+                }
+            }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
+    __device__ void finish(unsigned char*, int quarter, int lane) const {
+        const int j = quarter * 32 + lane;
+        if (PASS != 1 || j >= a.nx) return;
+#pragma unroll
+        for (int rl = 0; rl < 2; ++rl) {
+            if (!(rl == 0 ? on0 : on1)) continue;
+            double2* tp = a.tpart + ((size_t)(r0 + rl) * a.ngroups + g) * 4 * a.nx + j;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tp[q * a.nx] = acc[rl][q];
+        }
+    }
+};
+
+// one CTA per (k-group, right-hand-side pair); the pair's flags decide before anything is allocated
+template <int PASS>
+__global__ void __launch_bounds__(kTsThreads, 1) k_solve_tc(TcSolveArgs a) {
+    const int r0 = blockIdx.y * 2;
+    const bool on0 = r0 < a.nrhs && !(a.done && a.done[r0]);
+    const bool on1 = r0 + 1 < a.nrhs && !(a.done && a.done[r0 + 1]);
+    if (!on0 && !on1) return;
+    SolvePolicy<PASS> p;
+    p.a = a;
+    p.g = blockIdx.x;
+    p.G = gridDim.x;
+    p.nblk = (a.nxi - p.g + p.G - 1) / p.G;
+    p.nh = a.Kp > 128 ? 2 : 1;
+    p.r0 = r0;
+    p.on0 = on0;
+    p.on1 = on1;
+#pragma unroll
+    for (int rl = 0; rl < 2; ++rl)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) p.acc[rl][q] = make_double2(0.0, 0.0);
+    tcstream_body(p, a.st);
 }
 
 // number of CTAs (k-groups) of the tensor-core passes
@@ -311,11 +273,10 @@ int tc_solve_groups(int nxi, int ngroups_cap) { return std::max(1, std::min({nxi
 int tc_solve_pass(int pass, klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
                   cudaStream_t s, const int* done) {
     static std::atomic<unsigned long long> attr{0};
+    const size_t smem = tcstream_smem<SolvePolicy<1>>();
     if (once_per_device(attr)) {
-        // the largest request (Nx = 128); the opt-in limit also covers the kernel's static shared memory
-        const int cap = (int)tc_solve_smem(128);
-        KLST_CK(cudaFuncSetAttribute(k_solve_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-        KLST_CK(cudaFuncSetAttribute(k_solve_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        KLST_CK(cudaFuncSetAttribute(k_solve_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KLST_CK(cudaFuncSetAttribute(k_solve_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     klst_pencil p = f->p;
     TcSolveArgs a;
@@ -327,9 +288,8 @@ int tc_solve_pass(int pass, klst_factor f, const double2* b, int mask, double2* 
     a.G = p->G; a.sv = f->sv; a.y = y; a.accumulate = accumulate;
     a.done = done; a.st = f->status;
     dim3 grid(a.ngroups, (nrhs + 1) / 2);
-    const size_t smem = tc_solve_smem(p->nx);
-    if (pass == 1) k_solve_tc<1><<<grid, 128, smem, s>>>(a);
-    else k_solve_tc<2><<<grid, 128, smem, s>>>(a);
+    if (pass == 1) k_solve_tc<1><<<grid, kTsThreads, smem, s>>>(a);
+    else k_solve_tc<2><<<grid, kTsThreads, smem, s>>>(a);
     note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
