@@ -331,6 +331,26 @@ int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s) {
     const size_t dsm32 = sizeof(float2) * a.chunk, dsm64 = sizeof(double2) * a.chunk;
     const size_t usm = sizeof(double2) * (m + 1);
     const int nred = jd ? m : nc;
+    if (a.sl) {
+        // the float64 passes as exact integer-slice products on the tensor cores (orth_tc.cu)
+        int rc;
+        prof_begin("orth1_f32dots_tcupdate", s);
+        k_dots_f32<<<a.nchunks, 256, dsm32, s>>>(a.V, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
+        k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.nchunks, nc, a.ldp, a.h1, jd); note_launch();
+        if ((rc = gs_update_tc(a.sl, a.n, a.h1, a.w, nullptr, false, j, jd, a.st, s)) != KLST_OK) return rc;
+        prof_end("orth1_f32dots_tcupdate", s);
+        prof_begin("orth2_tc", s);
+        if ((rc = gs_dots_tc(a.sl, a.n, a.w, a.part, a.ldp, j, jd, a.st, s)) != KLST_OK) return rc;
+        k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.ntc, nc, a.ldp, a.h2, jd); note_launch();
+        if ((rc = gs_update_tc(a.sl, a.n, a.h2, a.w, a.npart, true, j, jd, a.st, s)) != KLST_OK) return rc;
+        k_finish64<<<1, 256, 0, s>>>(a.h1, a.h2, a.npart, a.ntc, j, a.S, a.lds, a.beta, a.st, jd); note_launch();
+        prof_end("orth2_tc", s);
+        prof_begin("orth_scale", s);
+        scale64_split(a.w, a.n, a.beta, a.V, a.vcur, j + 1, a.sl, jd, a.nscale, s);
+        prof_end("orth_scale", s);
+        KLST_CK_LAUNCH();
+        return KLST_OK;
+    }
     prof_begin("orth1_f32dots_f64update", s);
     k_dots_f32<<<a.nchunks, 256, dsm32, s>>>(a.V, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
     k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.nchunks, nc, a.ldp, a.h1, jd); note_launch();
