@@ -40,7 +40,7 @@ int64_t solve_footprint(const klst_pencil_desc& d, int precision, const klst_eig
     b += 31 * m * m * 32 + 8 * m * m * 16;                                       // Schur work and rotation log
     if (o.arith != KLST_ARITH_DF64) b += 31 * m * m * 36 + 2048;                 // float64 step: sorted log + levels
     if (o.arith != KLST_ARITH_DF64 && basis_slices_supported((int)m))            // integer slices of the basis
-        b += (int64_t)basis_slices_bytes(n) + 256 * (m + 1) * 16;
+        b += (int64_t)basis_slices_bytes(n) + n * (m + 1) * 8 + 256 * (m + 1) * 16;
     if (o.arith != KLST_ARITH_DF64 && 2 * m <= 256)                              // tensor-core rotation slices
         b += (int64_t)oz_workspace_bytes((int)n, 2 * (int)std::max<int64_t>(m, nev), (int)(2 * m));
     return b + (64 << 20);

@@ -396,6 +396,7 @@ struct EigsWork {
     double2 *wbuf = nullptr, *vcur = nullptr;
     char* ozws = nullptr;         // float64 basis: workspace of the tensor-core rotation
     unsigned short* sl = nullptr; // float64 basis: its integer slices (tensor-core Gram-Schmidt)
+    float2* v32 = nullptr;        // float64 basis truncated to complex float32 (first-pass coefficients)
     double2 *mw = nullptr, *mp = nullptr;
     double *est = nullptr, *npart = nullptr, *beta = nullptr, *nrm = nullptr;
     int* nconv = nullptr;
@@ -523,7 +524,10 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             sc.take(W.reorth, 4);
             sc.take(W.h, 2 * (m + 1));
             sc.take(W.dpart, (size_t)std::max(nchunks, gs_groups) * (m + 1));
-            if (use_tcgs) sc.take(W.sl, basis_slices_bytes(n) / sizeof(unsigned short));
+            if (use_tcgs) {
+                sc.take(W.sl, basis_slices_bytes(n) / sizeof(unsigned short));
+                sc.take(W.v32, (size_t)n * (m + 1));
+            }
             sc.take(W.npart, (size_t)std::max(nblk, 1) * std::max(nev, 1) + 64);
             sc.take(W.beta, 4);
             sc.take(W.nrm, nev + 4);
@@ -574,7 +578,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     KLST_CK_LAUNCH();
     if (use_tcgs) {
         KLST_CK(cudaMemsetAsync(W.sl, 0, basis_slices_bytes(n), s));
-        if ((rc = split_basis(V, n, 0, 1, W.sl, s)) != KLST_OK) return fail(rc);
+        if ((rc = split_basis(V, n, 0, 1, W.sl, W.v32, s)) != KLST_OK) return fail(rc);
     }
     // phase timers: event pairs recorded per step (eager launches) or per cycle (graph mode) and
     // read after each restart synchronisation; created below once the mode is known
@@ -614,7 +618,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
     oa.n = n; oa.m = m; oa.w = wbuf; oa.vcur = vcur; oa.chunk = chunk; oa.nchunks = nchunks; oa.ldp = m + 1;
     oa.part = W.dpart; oa.h1 = W.h; oa.h2 = W.h + (m + 1); oa.nupd = nblk; oa.npart = W.npart2; oa.nscale = nblk;
     oa.S = W.S; oa.lds = lds; oa.beta = W.beta; oa.st = f->status;
-    oa.sl = use_tcgs ? W.sl : nullptr; oa.ntc = gs_groups;
+    oa.sl = use_tcgs ? W.sl : nullptr; oa.v32 = W.v32; oa.ntc = gs_groups;
     auto f64_orth = [&](double2* Vb, int j, const int* jd) -> int {
         oa.V = Vb;
         return orth64_step(oa, j, jd, s);
@@ -753,7 +757,7 @@ extern "C" int klst_eigs(klst_factor f, const klst_eigs_opts* o, double* evals_h
             KLST_CK_LAUNCH();
             KLST_CK(cudaMemcpyAsync(Valt + (int64_t)keep * n, V + (int64_t)m * n, sizeof(double2) * n,
                                     cudaMemcpyDeviceToDevice, s));
-            if (use_tcgs && (rc = split_basis(Valt, n, 0, keep + 1, W.sl, s)) != KLST_OK) return fail(rc);
+            if (use_tcgs && (rc = split_basis(Valt, n, 0, keep + 1, W.sl, W.v32, s)) != KLST_OK) return fail(rc);
             cudaEventRecord(evs[3 * (m + 1) + 3], s);
             KLST_CK(cudaEventSynchronize(evs[3 * (m + 1) + 3]));
             float a4 = 0;

@@ -110,6 +110,7 @@ struct Orth64Args {
     double* beta;      // out: ||w''||
     Status* st;
     unsigned short* sl;  // non-NULL: integer slices of V, the float64 passes run on the tensor cores
+    float2* v32;         // with sl: V truncated to complex float32 (the first-pass coefficients' operand)
     int ntc;             // CTAs of the tensor-core passes (gs_tc_groups)
 };
 int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s);
@@ -117,13 +118,13 @@ int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s);
 size_t basis_slices_bytes(int64_t n);
 bool basis_slices_supported(int m);
 int gs_tc_groups(int64_t n);
-int split_basis(const double2* V, int64_t n, int c0, int c1, unsigned short* SL, cudaStream_t s);
+int split_basis(const double2* V, int64_t n, int c0, int c1, unsigned short* SL, float2* V32, cudaStream_t s);
 int gs_update_tc(const unsigned short* SL, int64_t n, const double2* h, double2* w, double* npart, bool second,
                  int j, const int* jd, Status* st, cudaStream_t s);
-int gs_dots_tc(const unsigned short* SL, int64_t n, const double2* w, double2* part, int ldp, int j, const int* jd,
-               Status* st, cudaStream_t s);
+int gs_update_dots_tc(const unsigned short* SL, int64_t n, const double2* h, double2* w, double2* part, int ldp,
+                      int j, const int* jd, Status* st, cudaStream_t s);
 void scale64_split(const double2* w, int64_t n, const double* beta, double2* V, double2* vcopy, int col,
-                   unsigned short* SL, const int* jd, int nblk, cudaStream_t s);
+                   unsigned short* SL, float2* V32, const int* jd, int nblk, cudaStream_t s);
 // vcol = vcopy = w / *beta (the first basis vector)
 void k_scale64_ext(const double2* w, int64_t n, const double* beta, double2* vcol, double2* vcopy, int64_t ldv,
                    int nblk, cudaStream_t s);

@@ -17,26 +17,18 @@
 #include <algorithm>
 
 #include "df64.cuh"
-#include "factor.cuh"
+#include "oz.cuh"
 
 namespace klst {
-
-// Leading 24 significand bits of a float64 as a float32 (truncation), by integer operations only:
-// the B300 converts float64 at the float64 rate, this stays on the integer and float32 pipes.
-// Values below 2^-126 in magnitude become 0 (the basis vectors have unit norm and w = T v_j is
-// far inside the float32 range, so nothing else reaches the limits).
-__device__ __forceinline__ float trunc_f32(double x) {
-    const long long b = __double_as_longlong(x);
-    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    const int ef = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-    const unsigned f = (hi & 0x80000000u) | ((unsigned)ef << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    return (ef > 0 && ef < 255) ? __uint_as_float(f) : 0.0f;
-}
 
 // part[chunk * ldp + col] = sum_{i in chunk} conj(V[i, col]) w[i] in float32 arithmetic on
 // truncated operands (first-pass coefficients).  Four columns per warp pass, two rows per lane
 // iteration; the per-chunk sums are stored as float64.
-__global__ void __launch_bounds__(256) k_dots_f32(const double2* __restrict__ V, int64_t ldv, int ncols,
+// The basis is read in float64 (truncated on the fly) or from its truncated float32 copy.
+__device__ __forceinline__ float f32_of(double x) { return trunc_f32(x); }
+__device__ __forceinline__ float f32_of(float x) { return x; }
+template <typename VT>
+__global__ void __launch_bounds__(256) k_dots_f32(const VT* __restrict__ V, int64_t ldv, int ncols,
                                                   const double2* __restrict__ w, int64_t n, int chunk,
                                                   double2* __restrict__ part, int ldp, const int* __restrict__ jdev) {
     if (jdev) ncols = *jdev + 1;
@@ -52,21 +44,21 @@ __global__ void __launch_bounds__(256) k_dots_f32(const double2* __restrict__ V,
     const double2 z2 = make_double2(0.0, 0.0);
     for (int col = 4 * wid; col < ncols; col += 4 * nw) {
         const int nq = min(4, ncols - col);
-        const double2* vc = V + col * ldv + r0;
+        const VT* vc = V + col * ldv + r0;
         float2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int i = lane;
         for (; i + 32 < len; i += 64) {
-            double2 x0[4], x1[4];
+            VT x0[4], x1[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                x0[q] = (q < nq) ? vc[q * ldv + i] : z2;
-                x1[q] = (q < nq) ? vc[q * ldv + i + 32] : z2;
+                x0[q] = (q < nq) ? vc[q * ldv + i] : VT{};
+                x1[q] = (q < nq) ? vc[q * ldv + i + 32] : VT{};
             }
             const float2 w0 = sw32[i], w1 = sw32[i + 32];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float vr0 = trunc_f32(x0[q].x), vi0 = trunc_f32(x0[q].y);
-                const float vr1 = trunc_f32(x1[q].x), vi1 = trunc_f32(x1[q].y);
+                const float vr0 = f32_of(x0[q].x), vi0 = f32_of(x0[q].y);
+                const float vr1 = f32_of(x1[q].x), vi1 = f32_of(x1[q].y);
                 a[q].x = fmaf(vr0, w0.x, a[q].x); a[q].x = fmaf(vi0, w0.y, a[q].x);
                 a[q].y = fmaf(vr0, w0.y, a[q].y); a[q].y = fmaf(-vi0, w0.x, a[q].y);
                 a[q].x = fmaf(vr1, w1.x, a[q].x); a[q].x = fmaf(vi1, w1.y, a[q].x);
@@ -78,8 +70,8 @@ __global__ void __launch_bounds__(256) k_dots_f32(const double2* __restrict__ V,
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (q < nq) {
-                    const double2 x = vc[q * ldv + i];
-                    const float vr = trunc_f32(x.x), vi = trunc_f32(x.y);
+                    const VT x = vc[q * ldv + i];
+                    const float vr = f32_of(x.x), vi = f32_of(x.y);
                     a[q].x = fmaf(vr, w0.x, a[q].x); a[q].x = fmaf(vi, w0.y, a[q].x);
                     a[q].y = fmaf(vr, w0.y, a[q].y); a[q].y = fmaf(-vi, w0.x, a[q].y);
                 }
@@ -334,25 +326,26 @@ int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s) {
     if (a.sl) {
         // the float64 passes as exact integer-slice products on the tensor cores (orth_tc.cu)
         int rc;
-        prof_begin("orth1_f32dots_tcupdate", s);
-        k_dots_f32<<<a.nchunks, 256, dsm32, s>>>(a.V, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
+        prof_begin("orth1_f32dots", s);
+        k_dots_f32<float2><<<a.nchunks, 256, dsm32, s>>>(a.v32, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
         k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.nchunks, nc, a.ldp, a.h1, jd); note_launch();
-        if ((rc = gs_update_tc(a.sl, a.n, a.h1, a.w, nullptr, false, j, jd, a.st, s)) != KLST_OK) return rc;
-        prof_end("orth1_f32dots_tcupdate", s);
-        prof_begin("orth2_tc", s);
-        if ((rc = gs_dots_tc(a.sl, a.n, a.w, a.part, a.ldp, j, jd, a.st, s)) != KLST_OK) return rc;
+        prof_end("orth1_f32dots", s);
+        prof_begin("orth_tc_update1_dots2", s);
+        if ((rc = gs_update_dots_tc(a.sl, a.n, a.h1, a.w, a.part, a.ldp, j, jd, a.st, s)) != KLST_OK) return rc;
         k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.ntc, nc, a.ldp, a.h2, jd); note_launch();
+        prof_end("orth_tc_update1_dots2", s);
+        prof_begin("orth_tc_update2", s);
         if ((rc = gs_update_tc(a.sl, a.n, a.h2, a.w, a.npart, true, j, jd, a.st, s)) != KLST_OK) return rc;
         k_finish64<<<1, 256, 0, s>>>(a.h1, a.h2, a.npart, a.ntc, j, a.S, a.lds, a.beta, a.st, jd); note_launch();
-        prof_end("orth2_tc", s);
+        prof_end("orth_tc_update2", s);
         prof_begin("orth_scale", s);
-        scale64_split(a.w, a.n, a.beta, a.V, a.vcur, j + 1, a.sl, jd, a.nscale, s);
+        scale64_split(a.w, a.n, a.beta, a.V, a.vcur, j + 1, a.sl, a.v32, jd, a.nscale, s);
         prof_end("orth_scale", s);
         KLST_CK_LAUNCH();
         return KLST_OK;
     }
     prof_begin("orth1_f32dots_f64update", s);
-    k_dots_f32<<<a.nchunks, 256, dsm32, s>>>(a.V, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
+    k_dots_f32<double2><<<a.nchunks, 256, dsm32, s>>>(a.V, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
     k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.nchunks, nc, a.ldp, a.h1, jd); note_launch();
     k_update64<<<a.nupd, 256, usm, s>>>(a.V, a.n, nc, a.h1, a.w, a.n, nullptr, jd); note_launch();
     prof_end("orth1_f32dots_f64update", s);

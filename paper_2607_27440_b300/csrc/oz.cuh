@@ -175,6 +175,18 @@ __device__ __forceinline__ double oz_combine(const float blk[OZ_S]) {
     return fma((double)L, exp2_neg7(9), (double)H * exp2_neg7(5));
 }
 
+// Leading 24 significand bits of a float64 as a float32 (truncation), by integer operations only:
+// the B300 converts float64 at the float64 rate, this stays on the integer and float32 pipes.
+// Values below 2^-126 in magnitude become 0 (the basis vectors have unit norm and w = T v_j is
+// far inside the float32 range, so nothing else reaches the limits).
+__device__ __forceinline__ float trunc_f32(double x) {
+    const long long b = __double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int ef = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    const unsigned f = (hi & 0x80000000u) | ((unsigned)ef << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return (ef > 0 && ef < 255) ? __uint_as_float(f) : 0.0f;
+}
+
 // ---- nine-slice variant (63-bit fixed point): x ~= 2^e sum_{s=0..8} d_s 2^(-7 (s + 1)), |x| < 2^e
 constexpr int OZ_S9 = 9;
 

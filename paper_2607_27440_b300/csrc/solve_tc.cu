@@ -92,10 +92,10 @@ template <int PASS>
 struct SolvePolicy {
     static constexpr int stage_bytes = 32 * 1024;
     static constexpr int nstages = 4;
-    static constexpr int b_bytes = 256 * 128;                       // Kp <= 256
+    static constexpr int NT = 2, NBB = 2;                           // double-buffered TMEM and B
+    static constexpr int b_total = 2 * 256 * 128;                   // Kp <= 256
     static constexpr int x_bytes = 4 * 128 * 16 + 2 * 4 * 4 + 16;  // sV [4][nx] + exponents [2][4]
-    static constexpr int tmem_cols = 128;                           // 9 diagonal blocks x 8 columns
-    static constexpr uint32_t tmem_alloc = 256;
+    static constexpr uint32_t tmem_alloc = 256;                     // 2 x (9 diagonal blocks x 8 columns)
     TcSolveArgs a;
     int g, G, nblk, nh;      // CTA index, CTA count, its blocks, K halves per slice
     int r0;
@@ -114,18 +114,34 @@ struct SolvePolicy {
         return a.As + ((k * OZ_S + s) * (a.Kp / 8) + h * 16) * 1024;
     }
     __device__ uint32_t bytes(int, int l) const { return (uint32_t)kc_of(l % nh) * 2048; }
-    __device__ bool per_unit_b() const { return true; }
-    __device__ void mma(int, int l, uint32_t aB, uint32_t bB, uint32_t tcol) const {
+    __device__ int tbuf(int i) const { return i & 1; }
+    __device__ int tuse(int i) const { return i >> 1; }
+    __device__ bool needs_b(int) const { return true; }
+    __device__ int bbuf(int i) const { return i & 1; }
+    __device__ int buse(int i) const { return i >> 1; }
+    __device__ uint32_t tcol_off(int tb) const { return (uint32_t)tb * 128; }
+    __device__ int b_off(int bb) const { return bb * 256 * 128; }
+    __device__ int b_wait_load(int) const { return 0; }
+    __device__ int first_prep() const { return 0; }
+    __device__ int prep_before(int i) const { return i + 1 < nblk ? i + 1 : -1; }
+    __device__ int prep_after(int) const { return -1; }
+    __device__ void mma(int i, int l, uint32_t aB, uint32_t bB, uint32_t tcol) const {
         const int s = l / nh, h = l % nh;
         const int cnt = OZ_S - s, np = cnt + (cnt & 1);
         const uint32_t idesc = idesc_bf16(128, np * TC_NB);
         const uint32_t dcol = tcol + (uint32_t)(s * TC_NB);
         const int ksteps = kc_of(h) / 2;
-        const uint32_t bh = bB + (uint32_t)(h * 16) * (OZ_S * TC_NB * 16);
-        for (int kk = 0; kk < ksteps; ++kk) {
-            const uint64_t ad = sdesc(aB + kk * 2 * 2048, 2048, 128);
-            const uint64_t bd = sdesc(bh + kk * 2 * (OZ_S * TC_NB * 16), OZ_S * TC_NB * 16, 128);
-            mma_bf16(dcol, ad, bd, idesc, (s > 0 || h > 0 || kk > 0) ? 1u : 0u);
+        const uint32_t bh = bB + (uint32_t)b_off(i & 1) + (uint32_t)(h * 16) * (OZ_S * TC_NB * 16);
+        // descriptors advance by adding the address step (field = address / 16) to their low bits:
+        // the issuing thread then spends a few cycles per MMA instead of rebuilding both
+        uint64_t ad = sdesc(aB, 2048, 128), bd = sdesc(bh, OZ_S * TC_NB * 16, 128);
+        const uint64_t as = (2 * 2048) >> 4, bs = (2 * OZ_S * TC_NB * 16) >> 4;
+        mma_bf16(dcol, ad, bd, idesc, (s > 0 || h > 0) ? 1u : 0u);
+#pragma unroll 4
+        for (int kk = 1; kk < ksteps; ++kk) {
+            ad += as;
+            bd += bs;
+            mma_bf16(dcol, ad, bd, idesc, 1u);
         }
     }
     __device__ int* emax(unsigned char* sX, int b) const { return reinterpret_cast<int*>(sX + 4 * 128 * 16) + b * 4; }

@@ -29,44 +29,51 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Policy interface (all device functions, called by the roles named above):
-//   int nunits() const                          units of this CTA (unit i is the CTA's i-th)
+//   int nunits() const                          units of this CTA, in MMA order
 //   int nloads(int i) const                     loads of unit i
 //   const void* src(int i, int l) const         global source of load l of unit i
 //   uint32_t bytes(int i, int l) const          its size (multiple of 16, <= stage_bytes)
 //   void mma(int i, int l, uint32_t a, uint32_t b, uint32_t tcol) const
 //                                               the MMAs of load l (one thread), A at shared
-//                                               address a, B buffer at b, accumulator at TMEM tcol
-//   bool per_unit_b() const                     false: B is prepared once (unit 0) and kept
-//   void prep(int i, unsigned char* sB, unsigned char* sX, int t) const
+//                                               address a, the B region at b (buffers at b_off),
+//                                               accumulator at TMEM tcol
+//   int b_wait_load(int i) const                the first load of unit i that reads its new B
+//   int tbuf(int i), tuse(int i) const          unit i's TMEM accumulator (< NT) and how many
+//                                               earlier units used it
+//   bool needs_b(int i) const                   unit i waits for a freshly prepared B
+//   int bbuf(int i), buse(int i) const          its B buffer (< NBB) and that buffer's earlier uses
+//                                               (counting the units that prepare B only)
+//   uint32_t tcol_off(int tb) const, int b_off(int bb) const   buffer placements
+//   int first_prep(), prep_before(int i), prep_after(int i) const
+//                                               the unit whose B the B/epilogue threads prepare
+//                                               first, before the epilogue of unit i and after it
+//                                               (-1: none); epilogues run in unit order
+//   void prep(int i, unsigned char* sB, unsigned char* sX, int t)
 //                                               B of unit i into sB (t = 0..127); sX is scratch
 //   void epilogue(int i, uint32_t tcol, unsigned char* sX, int quarter, int lane)
 //                                               TMEM lanes quarter*32 + lane of unit i (may keep
 //                                               running sums in the thread's copy of the policy)
 //   void finish(unsigned char* sX, int quarter, int lane) after the last epilogue
-// and the sizes stage_bytes, nstages, b_bytes, x_bytes, tmem_cols (per accumulator).
+// and the constants stage_bytes, nstages, b_total, x_bytes, NT, NBB, tmem_alloc.
 // The body of a kernel launched with kTsThreads threads and tcstream_smem<P>() bytes of dynamic
-// shared memory; p is the thread's own copy of the policy (the epilogue may keep running sums in it).
+// shared memory; p is the thread's own copy of the policy.
 template <class P>
 __device__ __forceinline__ void tcstream_body(P& p, Status* st) {
     extern __shared__ __align__(128) unsigned char ts_smem[];
-    constexpr int NS = P::nstages;
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], bfull[2], bempty[2], tfull[2], tempty[2];
+    constexpr int NS = P::nstages, NT = P::NT, NBB = P::NBB;
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], bfull[NBB], bempty[NBB], tfull[NT], tempty[NT];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_fail;
     __shared__ int s_issued, s_consumed;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     unsigned char* stages = ts_smem;
-    unsigned char* sB[2] = {ts_smem + NS * P::stage_bytes, ts_smem + NS * P::stage_bytes + P::b_bytes};
-    unsigned char* sX = ts_smem + NS * P::stage_bytes + 2 * P::b_bytes;
+    unsigned char* sBase = ts_smem + NS * P::stage_bytes;
+    unsigned char* sX = sBase + P::b_total;
     constexpr uint32_t kCols = P::tmem_alloc;
     if (tid == 0) {
         for (int q = 0; q < NS; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&bfull[b], kTsEpi);
-            mbar_init(&bempty[b], 1);
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kTsEpi);
-        }
+        for (int b = 0; b < NBB; ++b) { mbar_init(&bfull[b], kTsEpi); mbar_init(&bempty[b], 1); }
+        for (int b = 0; b < NT; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kTsEpi); }
         s_fail = 0;
         s_issued = 0;
         s_consumed = 0;
@@ -108,53 +115,58 @@ __device__ __forceinline__ void tcstream_body(P& p, Status* st) {
             // MMA issuer
             int q = 0;
             for (int i = 0; i < nu && !s_fail; ++i) {
-                const int b = i & 1, use = i >> 1;
-                const int bb = p.per_unit_b() ? b : 0;
-                const int buse = p.per_unit_b() ? use : 0;
-                if ((p.per_unit_b() || i == 0) && !mbar_wait(&bfull[bb], (uint32_t)(buse & 1))) { fail(); break; }
-                if (!mbar_wait(&tempty[b], (uint32_t)((use & 1) ^ 1))) { fail(); break; }
+                const int tb = p.tbuf(i), bb = p.bbuf(i);
+                const bool nb = p.needs_b(i);
+                const int bl = nb ? p.b_wait_load(i) : -1;
+                if (!mbar_wait(&tempty[tb], (uint32_t)((p.tuse(i) & 1) ^ 1))) { fail(); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t tcol = tbase + (uint32_t)(b * P::tmem_cols);
+                const uint32_t tcol = tbase + p.tcol_off(tb);
+                const uint32_t bsm = smem_u32(sBase);
                 const int nl = p.nloads(i);
                 bool ok = true;
                 for (int l = 0; l < nl; ++l, ++q) {
                     const int stg = q % NS, su = q / NS;
+                    // the unit's new B is waited for only before the first load that reads it
+                    if (l == bl && !mbar_wait(&bfull[bb], (uint32_t)(p.buse(i) & 1))) { ok = false; break; }
                     if (!mbar_wait(&full[stg], (uint32_t)(su & 1))) { ok = false; break; }
                     s_consumed = q + 1;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    p.mma(i, l, smem_u32(stages + stg * P::stage_bytes), smem_u32(sB[bb]), tcol);
+                    p.mma(i, l, smem_u32(stages + stg * P::stage_bytes), bsm, tcol);
                     mma_commit(&empty[stg]);
                 }
                 if (!ok) { fail(); break; }
-                mma_commit(&tfull[b]);
-                if (p.per_unit_b()) mma_commit(&bempty[bb]);
+                mma_commit(&tfull[tb]);
+                if (nb) mma_commit(&bempty[bb]);
             }
         }
     } else {
         // B preparation and epilogue (128 threads, TMEM lane quarter = warp % 4)
         const int t = tid - 64, quarter = wid & 3;
         auto prep_unit = [&](int i) {
-            const int b = i & 1, use = i >> 1;
-            if (!mbar_wait(&bempty[b], (uint32_t)((use & 1) ^ 1))) fail();
+            const int bb = p.bbuf(i);
+            if (!mbar_wait(&bempty[bb], (uint32_t)((p.buse(i) & 1) ^ 1))) fail();
             epi_sync();
             if (s_fail) return;
-            p.prep(i, sB[b], sX, t);
+            p.prep(i, sBase + p.b_off(bb), sX, t);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&bfull[b]);
+            mbar_arrive(&bfull[bb]);
         };
-        if (nu > 0) prep_unit(0);
+        if (nu > 0 && p.first_prep() >= 0) prep_unit(p.first_prep());
         for (int i = 0; i < nu; ++i) {
             epi_sync();
             if (s_fail) break;
-            if (p.per_unit_b() && i + 1 < nu) prep_unit(i + 1);
-            const int b = i & 1, use = i >> 1;
-            if (!mbar_wait(&tfull[b], (uint32_t)(use & 1))) fail();
+            const int pb = p.prep_before(i);
+            if (pb >= 0) prep_unit(pb);
+            const int tb = p.tbuf(i);
+            if (!mbar_wait(&tfull[tb], (uint32_t)(p.tuse(i) & 1))) fail();
             epi_sync();
             if (s_fail) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            p.epilogue(i, tbase + (uint32_t)(b * P::tmem_cols), sX, quarter, lane);
+            p.epilogue(i, tbase + p.tcol_off(tb), sX, quarter, lane);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&tempty[b]);
+            mbar_arrive(&tempty[tb]);
+            const int pa = p.prep_after(i);
+            if (pa >= 0) prep_unit(pa);
         }
         epi_sync();
         if (!s_fail) p.finish(sX, quarter, lane);
@@ -175,6 +187,6 @@ __device__ __forceinline__ void tcstream_body(P& p, Status* st) {
 }
 
 template <class P>
-size_t tcstream_smem() { return (size_t)P::nstages * P::stage_bytes + 2 * (size_t)P::b_bytes + P::x_bytes; }
+size_t tcstream_smem() { return (size_t)P::nstages * P::stage_bytes + (size_t)P::b_total + P::x_bytes; }
 
 }  // namespace klst
