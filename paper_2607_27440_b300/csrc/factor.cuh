@@ -121,8 +121,8 @@ int gs_tc_groups(int64_t n);
 int split_basis(const double2* V, int64_t n, int c0, int c1, unsigned short* SL, float2* V32, cudaStream_t s);
 int gs_update_tc(const unsigned short* SL, int64_t n, const double2* h, double2* w, double* npart, bool second,
                  int j, const int* jd, Status* st, cudaStream_t s);
-int gs_update_dots_tc(const unsigned short* SL, int64_t n, const double2* h, double2* w, double2* part, int ldp,
-                      int j, const int* jd, Status* st, cudaStream_t s);
+int gs_dots_tc(const unsigned short* SL, int64_t n, const double2* w, double2* part, int ldp, int j, const int* jd,
+               Status* st, cudaStream_t s);
 void scale64_split(const double2* w, int64_t n, const double* beta, double2* V, double2* vcopy, int col,
                    unsigned short* SL, float2* V32, const int* jd, int nblk, cudaStream_t s);
 // vcol = vcopy = w / *beta (the first basis vector)

@@ -330,10 +330,13 @@ int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s) {
         k_dots_f32<float2><<<a.nchunks, 256, dsm32, s>>>(a.v32, a.n, nc, a.w, a.n, a.chunk, a.part, a.ldp, jd); note_launch();
         k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.nchunks, nc, a.ldp, a.h1, jd); note_launch();
         prof_end("orth1_f32dots", s);
-        prof_begin("orth_tc_update1_dots2", s);
-        if ((rc = gs_update_dots_tc(a.sl, a.n, a.h1, a.w, a.part, a.ldp, j, jd, a.st, s)) != KLST_OK) return rc;
+        prof_begin("orth_tc_update1", s);
+        if ((rc = gs_update_tc(a.sl, a.n, a.h1, a.w, nullptr, false, j, jd, a.st, s)) != KLST_OK) return rc;
+        prof_end("orth_tc_update1", s);
+        prof_begin("orth_tc_dots2", s);
+        if ((rc = gs_dots_tc(a.sl, a.n, a.w, a.part, a.ldp, j, jd, a.st, s)) != KLST_OK) return rc;
         k_reduce_cols64<<<nred, 128, 0, s>>>(a.part, a.ntc, nc, a.ldp, a.h2, jd); note_launch();
-        prof_end("orth_tc_update1_dots2", s);
+        prof_end("orth_tc_dots2", s);
         prof_begin("orth_tc_update2", s);
         if ((rc = gs_update_tc(a.sl, a.n, a.h2, a.w, a.npart, true, j, jd, a.st, s)) != KLST_OK) return rc;
         k_finish64<<<1, 256, 0, s>>>(a.h1, a.h2, a.npart, a.ntc, j, a.S, a.lds, a.beta, a.st, jd); note_launch();

@@ -17,10 +17,12 @@
 // K <= 256 every diagonal sum stays below 2^24 ((2 x 128 x 64 + 7 x 64 x 64) x 256), exact in
 // float32; the epilogue combines the nine diagonals with integer operations and one rounding.
 //
-// Per Arnoldi step (orth64_step with slices): first-pass coefficients on the float32 pipes as
-// before; w' = w - V h1 (all nine slices); h2 = V^H w' (nine slices, partial sums per CTA, then
-// k_reduce_cols64); w'' = w' - V h2 with six A slices: h2 ~ 1e-7 ||w|| after a float32 first pass,
-// so V truncated to 2^-41 changes w'' by ~1e-19 ||w|| per entry, far below float64 rounding.
+// Per Arnoldi step (orth64_step with slices): first-pass coefficients on the float32 pipes from a
+// truncated float32 copy of V; w' = w - V h1 (all nine slices); h2 = V^H w' (nine slices, partial
+// sums per CTA, then k_reduce_cols64); w'' = w' - V h2 with six A slices: h2 ~ 1e-7 ||w|| after a
+// float32 first pass, so V truncated to 2^-41 changes w'' by ~1e-19 ||w|| per entry, far below
+// float64 rounding.  (One pass that fused the first update with the second dots, re-reading the
+// slices from L2, was measured no faster than the two passes.)
 #include <algorithm>
 #include <atomic>
 
@@ -258,167 +260,101 @@ struct UpdPolicy {
     }
 };
 
-// Both products of every tile: U_t is w' = w - V h1 on tile t, D_t the tile's share of h2 = V^H w'.
-// D_t reads the same slices again (from L2, loaded two tiles earlier) and its B -- the tile of w'
-// -- is split by the epilogue threads that computed it, so one HBM read of the slices serves both
-// products of the step.  Unit c pairs U_c (c < n) with D_{c-2} (c >= 2) and alternates their loads,
-// so the HBM stream of one tile and the L2 re-read of another are in flight together; the lag of
-// two tiles lets U_c's epilogue and the split of w'_c finish while unit c + 1 runs.  TMEM: unit c
-// uses buffer c mod 2 (columns 0..31 U, 32..95 D, two M halves); B: h1 in buffer 0, the tiles of
-// w' alternate in buffers 1, 2.
-struct FusedPolicy {
+// part[g][c] = sum over the CTA's tiles of conj(V[r, c]) w[r] (all nine slices; B = one tile of w,
+// split per tile by the B/epilogue threads into the other buffer while the current tile multiplies)
+struct DotPolicy {
     static constexpr int stage_bytes = 32 * 1024;
     static constexpr int nstages = 5;
-    static constexpr int NT = 2, NBB = 3;
-    static constexpr int b_total = kSlKc * 512 + 2 * 16 * 512;  // h1 (K <= 256), two w' tiles (K = 128)
+    static constexpr int NT = 2, NBB = 2;
+    static constexpr int b_total = 2 * 16 * 512;  // two w tiles, K = 128 rows each
     static constexpr int x_bytes = 64;
-    static constexpr uint32_t tmem_alloc = 256;
+    static constexpr uint32_t tmem_alloc = 128;   // 2 x (two M halves (k < 128, k >= 128) x 32)
     GsArgs a;
     GsShape sh;
     int g, G, ntl;
-    double2 wk;        // this thread's row of w' (epilogue of U_c -> B of D_c)
-    double acc[2][2];  // dots: [M half][B column] running sums
+    double acc[2][2];  // [M half][B column] running sums of this lane's row k
 
-    __device__ int nunits() const { return ntl + 2; }
-    __device__ bool has_u(int c) const { return c < ntl; }
-    __device__ bool has_d(int c) const { return c >= 2; }
-    __device__ int nl1() const { return OZ_S9 * sh.nh; }
-    __device__ int nloads(int c) const { return (has_u(c) ? nl1() : 0) + (has_d(c) ? nl1() : 0); }
-    // load l of unit c -> (is_dot, index within that product)
-    __device__ bool load_is_dot(int c, int l) const {
-        if (!has_u(c)) return true;
-        if (!has_d(c)) return false;
-        return (l & 1) != 0;
+    __device__ int nunits() const { return ntl; }
+    __device__ int nloads(int) const { return OZ_S9 * sh.nh; }
+    __device__ const void* src(int i, int l) const {
+        const size_t t = (size_t)g + (size_t)i * G;
+        const int s = l / sh.nh, h = l % sh.nh;
+        return a.SL + ((t * OZ_S9 + s) * kSlKc + h * 16) * 1024;
     }
-    __device__ int load_ix(int c, int l) const { return (has_u(c) && has_d(c)) ? (l >> 1) : l; }
-    __device__ const void* src(int c, int l) const {
-        const bool d = load_is_dot(c, l);
-        const int x = load_ix(c, l), s = x / sh.nh, h = x % sh.nh;
-        const size_t tile = (size_t)g + (size_t)(d ? c - 2 : c) * G;
-        return a.SL + ((tile * OZ_S9 + s) * kSlKc + h * 16) * 1024;
-    }
-    __device__ uint32_t bytes(int c, int l) const { return (uint32_t)sh.kc_of(load_ix(c, l) % sh.nh) * 2048; }
-    __device__ int tbuf(int c) const { return c & 1; }
-    __device__ int tuse(int c) const { return c >> 1; }
-    __device__ bool needs_b(int c) const { return c == 0 || has_d(c); }
-    __device__ int bbuf(int c) const { return c == 0 ? 0 : 1 + (c & 1); }
-    __device__ int buse(int c) const { return c == 0 ? 0 : (c - 2) >> 1; }
-    __device__ int b_wait_load(int c) const { return c == 0 ? 0 : (has_u(c) ? 1 : 0); }
-    __device__ uint32_t tcol_off(int tb) const { return (uint32_t)tb * 128; }
-    __device__ int b_off(int bb) const { return bb == 0 ? 0 : kSlKc * 512 + (bb - 1) * 16 * 512; }
+    __device__ uint32_t bytes(int, int l) const { return (uint32_t)sh.kc_of(l % sh.nh) * 2048; }
+    __device__ int tbuf(int i) const { return i & 1; }
+    __device__ int tuse(int i) const { return i >> 1; }
+    __device__ bool needs_b(int) const { return true; }
+    __device__ int bbuf(int i) const { return i & 1; }
+    __device__ int buse(int i) const { return i >> 1; }
+    __device__ int b_wait_load(int) const { return 0; }
+    __device__ uint32_t tcol_off(int tb) const { return (uint32_t)tb * 64; }
+    __device__ int b_off(int bb) const { return bb * 16 * 512; }
     __device__ int first_prep() const { return 0; }
-    __device__ int prep_before(int) const { return -1; }
-    // after U_c's epilogue, the B of D_c (part of unit c + 2)
-    __device__ int prep_after(int c) const { return has_u(c) ? c + 2 : -1; }
-    __device__ void mma(int c, int l, uint32_t aB, uint32_t bB, uint32_t tcol) const {
-        const int x = load_ix(c, l), s = x / sh.nh, h = x % sh.nh;
-        if (!load_is_dot(c, l)) {
-            const uint32_t idesc = idesc_bf16(128, s == 0 ? 32 : 16);
-            // h1: B buffer 0
-            gs_update_mmas(aB, bB + (uint32_t)(h * 16) * 512, tcol + (uint32_t)(2 * s), idesc, sh.kc_of(h) / 2,
-                           s > 0 || h > 0);
-        } else {
-            // M half h holds k = 128 h .. 128 h + 127; rows beyond the loaded k-chunks are stale
-            // integer slices or zeros (the stages are cleared first), and their TMEM lanes are not read
-            const uint32_t idesc = idesc_bf16_amn(128, s == 0 ? 32 : 16);
-            const uint32_t dc = tcol + 32 + (uint32_t)(h * 32 + 2 * s);
-            uint64_t ad = sdesc(aB, 128, 2048), bd = sdesc(bB + (uint32_t)b_off(bbuf(c)), 512, 128);
-            mma_bf16(dc, ad, bd, idesc, s > 0 ? 1u : 0u);
+    __device__ int prep_before(int i) const { return i + 1 < ntl ? i + 1 : -1; }
+    __device__ int prep_after(int) const { return -1; }
+    __device__ void mma(int i, int l, uint32_t aB, uint32_t bB, uint32_t tcol) const {
+        // M half h holds k = 128 h .. 128 h + 127; rows beyond the loaded k-chunks are stale integer
+        // slices or zeros (the stages are cleared first), and their TMEM lanes are not read
+        const int s = l / sh.nh, h = l % sh.nh;
+        const uint32_t idesc = idesc_bf16_amn(128, s == 0 ? 32 : 16);
+        const uint32_t dc = tcol + (uint32_t)(h * 32 + 2 * s);
+        uint64_t ad = sdesc(aB, 128, 2048), bd = sdesc(bB + (uint32_t)b_off(i & 1), 512, 128);
+        mma_bf16(dc, ad, bd, idesc, s > 0 ? 1u : 0u);
 #pragma unroll
-            for (int kk = 1; kk < 8; ++kk) {
-                ad += 256 >> 4;
-                bd += (2 * 512) >> 4;
-                mma_bf16(dc, ad, bd, idesc, 1u);
-            }
+        for (int kk = 1; kk < 8; ++kk) {
+            ad += 256 >> 4;
+            bd += (2 * 512) >> 4;
+            mma_bf16(dc, ad, bd, idesc, 1u);
         }
     }
-    __device__ void prep(int c, unsigned char* sB, unsigned char* sX, int t) const {
-        int* em = reinterpret_cast<int*>(sX);  // [0]: h1, [1 + 2 (c mod 2) + col]: the w' tile of D_{c-2}
-        if (c == 0) {
-            if (t == 0) em[0] = 0;
-            epi_sync();
-            int e = 0;
-            for (int cc = t; cc <= sh.j; cc += kTsEpi) e = max(e, max(dexp(a.h[cc].x), dexp(a.h[cc].y)));
-            atomicMax(&em[0], e);
-            epi_sync();
-            const int eh = em[0] - 1022;
-            for (int item = t; item < sh.kcu * 2; item += kTsEpi) {
-                const int kc = item >> 1, col = item & 1;
-                double x[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int k = kc * 8 + q, cc = k >> 1, p = k & 1;
-                    double v = 0.0;
-                    if (cc <= sh.j) {
-                        const double2 hv = a.h[cc];
-                        v = col == 0 ? (p == 0 ? hv.x : -hv.y) : (p == 0 ? hv.y : hv.x);
-                    }
-                    x[q] = v;
-                }
-                put_b_chunk(sB, kc, col, x, eh);
-            }
-            return;
-        }
-        // the tile of w' this thread's epilogue produced: row = TMEM lane of the thread
-        const int row = ((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31);
-        int* ew = em + 1 + 2 * (c & 1);
-        if (t < 2) ew[t] = 0;
+    __device__ void prep(int i, unsigned char* sB, unsigned char* sX, int t) const {
+        int* em = reinterpret_cast<int*>(sX) + 2 * (i & 1);
+        if (t < 2) em[t] = 0;
         epi_sync();
-        atomicMax(&ew[0], dexp(wk.x));
-        atomicMax(&ew[1], dexp(wk.y));
+        const int64_t r = ((int64_t)g + (int64_t)i * G) * 128 + t;
+        const double2 v = r < a.n ? a.w[r] : make_double2(0.0, 0.0);
+        atomicMax(&em[0], dexp(v.x));
+        atomicMax(&em[1], dexp(v.y));
         epi_sync();
+        // row t of B: columns (Re w, Im w), K-major [row chunk][16 slices x 2 columns][8 rows]
         int dr[OZ_S9], di[OZ_S9];
-        oz_digits9(oz_fixed63(wk.x, ew[0] - 1022), dr);
-        oz_digits9(oz_fixed63(wk.y, ew[1] - 1022), di);
+        oz_digits9(oz_fixed63(v.x, em[0] - 1022), dr);
+        oz_digits9(oz_fixed63(v.y, em[1] - 1022), di);
         unsigned short* b16 = reinterpret_cast<unsigned short*>(sB);
-        const int kc = row >> 3, kk = row & 7;
+        const int kc = t >> 3, kk = t & 7;
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
             b16[((size_t)kc * 32 + s * 2 + 0) * 8 + kk] = s < OZ_S9 ? bf16_of_int(dr[s]) : 0;
             b16[((size_t)kc * 32 + s * 2 + 1) * 8 + kk] = s < OZ_S9 ? bf16_of_int(di[s]) : 0;
         }
     }
-    __device__ void epilogue(int c, uint32_t tcol, unsigned char* sX, int quarter, int lane) {
-        const int* em = reinterpret_cast<const int*>(sX);
-        const uint32_t loff = (uint32_t)(quarter * 32) << 16;
-        if (has_d(c)) {
-            const int* ew = em + 1 + 2 * (c & 1);
-            const int e0 = ew[0] - 1022 + 1, e1 = ew[1] - 1022 + 1;
+    __device__ void epilogue(int i, uint32_t tcol, unsigned char* sX, int quarter, int lane) {
+        const int* em = reinterpret_cast<const int*>(sX) + 2 * (i & 1);
+        const int e0 = em[0] - 1022 + 1, e1 = em[1] - 1022 + 1;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h >= sh.nh) break;  // uniform over the CTA
-                double v0, v1;
-                diag_pair(tcol + 32 + (uint32_t)(h * 32) + loff, v0, v1);
-                acc[h][0] += scale2(v0, e0);
-                acc[h][1] += scale2(v1, e1);
-            }
-        }
-        if (has_u(c)) {
+        for (int h = 0; h < 2; ++h) {
+            if (h >= sh.nh) break;  // uniform over the CTA
             double v0, v1;
-            diag_pair(tcol + loff, v0, v1);
-            const int e = em[0] - 1022 + 1;
-            const int64_t r = ((int64_t)g + (int64_t)c * G) * 128 + quarter * 32 + lane;
-            wk = make_double2(0.0, 0.0);
-            if (r < a.n) {
-                const double2 wv = a.w[r];
-                wk = make_double2(wv.x - scale2(v0, e), wv.y - scale2(v1, e));
-                a.w[r] = wk;
-            }
+            diag_pair(tcol + (uint32_t)(h * 32) + ((uint32_t)(quarter * 32) << 16), v0, v1);
+            acc[h][0] += scale2(v0, e0);
+            acc[h][1] += scale2(v1, e1);
         }
     }
+    // lanes k = 2c and 2c + 1 hold (Re V, Im V) x (Re w, Im w): h_c = sum conj(V) w
     __device__ void finish(unsigned char*, int quarter, int lane) const {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const double o0 = __shfl_xor_sync(0xffffffffu, acc[h][0], 1);
             const double o1 = __shfl_xor_sync(0xffffffffu, acc[h][1], 1);
-            const int k = h * 128 + quarter * 32 + lane, cc = k >> 1;
-            if ((lane & 1) == 0 && h < sh.nh && cc <= sh.j)
-                a.part[(size_t)g * a.ldp + cc] = make_double2(acc[h][0] + o1, acc[h][1] - o0);
+            const int k = h * 128 + quarter * 32 + lane, c = k >> 1;
+            if ((lane & 1) == 0 && h < sh.nh && c <= sh.j)
+                a.part[(size_t)g * a.ldp + c] = make_double2(acc[h][0] + o1, acc[h][1] - o0);
         }
     }
 };
 
-// the stages start zeroed so that the dots' stale k-chunks are integers (see FusedPolicy::mma)
+// the stages start zeroed so that the dots' stale k-chunks are integers (see DotPolicy::mma)
 template <class P>
 __device__ __forceinline__ void clear_stages() {
     extern __shared__ __align__(128) unsigned char ts_smem[];
@@ -439,16 +375,15 @@ __global__ void __launch_bounds__(kTsThreads, 1) k_upd_tc(GsArgs a) {
     tcstream_body(p, a.st);
 }
 
-__global__ void __launch_bounds__(kTsThreads, 1) k_fused_tc(GsArgs a) {
-    FusedPolicy p;
+__global__ void __launch_bounds__(kTsThreads, 1) k_dot_tc(GsArgs a) {
+    DotPolicy p;
     p.a = a;
     p.sh.set(a.jd ? *a.jd : a.j);
     p.g = blockIdx.x;
     p.G = gridDim.x;
     p.ntl = (a.ntiles - p.g + p.G - 1) / p.G;
-    p.wk = make_double2(0.0, 0.0);
     for (int h = 0; h < 2; ++h) p.acc[h][0] = p.acc[h][1] = 0.0;
-    clear_stages<FusedPolicy>();
+    clear_stages<DotPolicy>();
     tcstream_body(p, a.st);
 }
 
@@ -474,16 +409,16 @@ int gs_update_tc(const unsigned short* SL, int64_t n, const double2* h, double2*
     return KLST_OK;
 }
 
-// w <- w - V h1 and part = per-CTA partial sums of V^H w (the updated w) in one pass
-int gs_update_dots_tc(const unsigned short* SL, int64_t n, const double2* h, double2* w, double2* part, int ldp,
-                      int j, const int* jd, Status* st, cudaStream_t s) {
+// part[g][c] = per-CTA partial sums of V^H w over the step's j + 1 columns (reduced by k_reduce_cols64)
+int gs_dots_tc(const unsigned short* SL, int64_t n, const double2* w, double2* part, int ldp, int j, const int* jd,
+               Status* st, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
-    const size_t sm = tcstream_smem<FusedPolicy>();
-    if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t sm = tcstream_smem<DotPolicy>();
+    if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_dot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     GsArgs a{};
-    a.SL = SL; a.n = n; a.ntiles = (int)((n + 127) / 128); a.h = h; a.w = w; a.part = part; a.ldp = ldp;
+    a.SL = SL; a.n = n; a.ntiles = (int)((n + 127) / 128); a.w = const_cast<double2*>(w); a.part = part; a.ldp = ldp;
     a.jd = jd; a.j = j; a.st = st;
-    k_fused_tc<<<gs_tc_groups(n), kTsThreads, sm, s>>>(a);
+    k_dot_tc<<<gs_tc_groups(n), kTsThreads, sm, s>>>(a);
     note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;
