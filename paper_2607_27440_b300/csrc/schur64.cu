@@ -12,9 +12,12 @@ namespace klst {
 struct Rot64 {         // rotation [c s; -conj(s) c] of rows/columns (i, i+1), float64
     double2 s;
     double c;
-    int i;
-    int pad;
+    int i;             // bits 0..7: i; 8..15 and 16..23: the QR sweep's window lo, hi (0, m - 1 for swaps)
+    int pad;           // replay level
 };
+__device__ __forceinline__ int rot_i(const Rot64& g) { return g.i & 0xFF; }
+__device__ __forceinline__ int rot_lo(const Rot64& g) { return (g.i >> 8) & 0xFF; }
+__device__ __forceinline__ int rot_hi(const Rot64& g) { return (g.i >> 16) & 0xFF; }
 static_assert(sizeof(Rot64) == sizeof(Rot), "the rotation log is shared by both arithmetics");
 
 __device__ __forceinline__ double cabs1_64(double2 a) { return fabs(a.x) + fabs(a.y); }
@@ -227,9 +230,11 @@ constexpr int kQrSlots = (kQrThreads / 32 / 4) * 3 * 8;  // element pairs per pa
 
 // Shifted QR sweeps (explicit single shift, Wilkinson / exceptional shifts, float64 deflation).
 // Within a sweep on the active window [lo, hi], step i applies left rotation i to rows (i, i+1)
-// of every column right of i-1 and, pipelined two steps behind, right rotation i-2 to columns
-// (i-2, i-1) of every row above i: column i-1 of R is final once left rotation i-1 is in, and
-// the two kinds touch disjoint entries within a step.  Each entry pair is rotated by four lanes
+// of the window's columns i..hi and, pipelined two steps behind, right rotation i-2 to columns
+// (i-2, i-1) of the window's rows lo..i-1: column i-1 of R is final once left rotation i-1 is in,
+// and the two kinds touch disjoint entries within a step.  The entries right of the window and
+// above it receive the sweep's rotations afterwards (k_schur_defer64), since later sweeps read
+// only entries inside their own windows, which are nested in or disjoint from this one.  Each entry pair is rotated by four lanes
 // of a warp that does not share a scheduler with warp 0 (a float64 instruction holds a warp's
 // scheduler for 64 cycles whatever the number of active lanes), while warp 0 rotates the pivot
 // column i+1 and forms rotation i+1 from it, the only dependent chain of the step.  The shift is
@@ -315,8 +320,8 @@ __global__ void __launch_bounds__(kQrThreads) k_schur_qr64(SchurArgs a) {
         __syncthreads();
         for (int i = lo; i <= hi + 1; ++i) {
             const int k = i - 2;                                  // right rotation of this step
-            const int nl = (i <= hi - 1) ? m - i : 0;             // left: columns i..m-1
-            const int nr = (k >= lo && k <= hi - 1) ? k + 2 : 0;  // right: rows 0..k+1
+            const int nl = (i <= hi - 1) ? hi + 1 - i : 0;        // left: columns i..hi of the window
+            const int nr = (k >= lo && k <= hi - 1) ? k + 2 - lo : 0;  // right: rows lo..k+1
             if (rot_lane) {
                 // at most two passes (m <= 160 < 2 kQrSlots): read and rotate both, then write.  Left
                 // and right items take the same instruction path (operands chosen by selects).
@@ -332,8 +337,8 @@ __global__ void __launch_bounds__(kQrThreads) k_schur_qr64(SchurArgs a) {
                     const bool left = it < nl && i + it != i + 1;  // warp 0 owns the pivot column
                     const bool right = it >= nl && it < nl + nr;
                     on[u] = left || right;
-                    // left: rows (i, i+1) of column i+it; right: columns (k, k+1) of row it-nl
-                    const int rx = left ? i : it - nl, ry = left ? i + 1 : it - nl;
+                    // left: rows (i, i+1) of column i+it; right: columns (k, k+1) of row lo+it-nl
+                    const int rx = left ? i : lo + it - nl, ry = left ? i + 1 : lo + it - nl;
                     const int cx = left ? i + it : k, cy = left ? i + it : k + 1;
                     const int rr = left ? i : k;  // rotation index
                     double2 x = make_double2(0.0, 0.0), y = x, sv = x;
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(kQrThreads) k_schur_qr64(SchurArgs a) {
                     if (left && cx == i && comp >= 2) w = 0.0;  // the annihilated subdiagonal entry
                     if (right) {
                         // a diagonal entry is final after its last right rotation: add the shift back
-                        const int r = it - nl;
+                        const int r = lo + it - nl;
                         if (r == k && comp < 2) w += comp == 0 ? mu.x : mu.y;
                         if (r == k + 1 && k + 1 == hi && comp >= 2) w += comp == 2 ? mu.x : mu.y;
                     }
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(kQrThreads) k_schur_qr64(SchurArgs a) {
         const int base = s_cnt;
         for (int t = tid; t < hi - lo; t += nt) {
             Rot64 g;
-            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = lo + t; g.pad = lvb[lo + t];
+            g.s = rs[lo + t]; g.c = rc[lo + t]; g.i = (lo + t) | (lo << 8) | (hi << 16); g.pad = lvb[lo + t];
             log[base + t] = g;
         }
         __syncthreads();
@@ -412,7 +417,13 @@ __global__ void __launch_bounds__(kQrThreads) k_schur_qr64(SchurArgs a) {
         a.H[idx] = (i <= j) ? TT(i, j) : zero2;
     }
     for (int i = tid; i < m; i += nt) a.rdy[i] = rdy[i];
-    if (tid == 0) { *a.log_count = s_cnt; a.log_count[1] = total; }
+    if (tid == 0) {
+        int nlev = 0;
+        for (int i = 0; i < m; ++i) nlev = max(nlev, rdy[i]);
+        *a.log_count = s_cnt;
+        a.log_count[1] = total;
+        a.log_count[3] = nlev;
+    }
 #undef TT
 }
 
@@ -495,7 +506,7 @@ __global__ void __launch_bounds__(kReThreads) k_schur_reorder64(SchurArgs a) {
             const int lv = max(rdy[i], rdy[i + 1]);  // the swaps of a round touch disjoint pairs
             sw_lv[q] = lv;
             Rot64 g;
-            g.s = sv; g.c = c; g.i = i; g.pad = lv;
+            g.s = sv; g.c = c; g.i = i | ((m - 1) << 16); g.pad = lv;
             log[s_cnt + q] = g;
         }
         __syncthreads();
@@ -669,9 +680,10 @@ __global__ void __launch_bounds__(kQThreads) k_schur_q64(SchurArgs a) {
             const bool on = k < end;
             const Rot64 g = k0 == beg ? cur : (on ? lg[k] : cur);
             double w = 0.0;
-            if (on) w = crot64_part(qrow[g.i], qrow[g.i + 1], g.c, conj(g.s), comp);
+            const int gi = rot_i(g);
+            if (on) w = crot64_part(qrow[gi], qrow[gi + 1], g.c, conj(g.s), comp);
             __syncwarp();
-            if (on) reinterpret_cast<double*>(&qrow[comp < 2 ? g.i : g.i + 1])[comp & 1] = w;
+            if (on) reinterpret_cast<double*>(&qrow[comp < 2 ? gi : gi + 1])[comp & 1] = w;
             __syncwarp();
         }
         __syncthreads();
@@ -680,6 +692,52 @@ __global__ void __launch_bounds__(kQThreads) k_schur_q64(SchurArgs a) {
         cur = nxt;
     }
     for (int col = tid; col < m; col += kQThreads) a.Q[(size_t)col * m + r] = qrow[col];
+}
+
+// The updates the window-restricted QR sweeps left out, replayed by level like the Schur vectors:
+// phase 0, one CTA per row r of T, applies the right rotations of every sweep whose window starts
+// below r (entries (r, i), (r, i+1)); phase 1, one CTA per column c, the left rotations of every
+// sweep whose window ends above c (entries (i, c), (i+1, c)).  Left and right rotations commute, so
+// applying all the right ones first and then all the left ones gives the full update; within one
+// row or column the level order keeps every entry's rotations in log order.
+__global__ void __launch_bounds__(kQThreads) k_schur_defer64(SchurArgs a, int phase) {
+    extern __shared__ double2 qrow[];  // [m]: the row (phase 0) or column (phase 1)
+    const int m = a.m, r = blockIdx.x, tid = threadIdx.x;
+    if (*a.nconv < 0) return;
+    const Rot64* lg = reinterpret_cast<const Rot64*>(a.log2);
+    for (int k = tid; k < m; k += kQThreads) qrow[k] = phase == 0 ? a.H[(size_t)k * m + r] : a.H[(size_t)r * m + k];
+    __syncthreads();
+    const int nlev = a.log_count[3];
+    const int grp = tid >> 2, comp = tid & 3, ngrp = kQThreads / 4;
+    int beg = 0;
+    for (int l = 0; l < nlev; ++l) {
+        const int end = a.loff[l];
+        for (int k0 = beg; k0 < end; k0 += ngrp) {
+            if (k0 + (grp & ~7) >= end) continue;  // nothing for this warp (uniform)
+            const int k = k0 + grp;
+            Rot64 g;
+            bool on = k < end;
+            if (on) {
+                g = lg[k];
+                on = phase == 0 ? (r < rot_lo(g)) : (r > rot_hi(g));
+            }
+            double w = 0.0;
+            int gi = 0;
+            if (on) {
+                gi = rot_i(g);
+                w = crot64_part(qrow[gi], qrow[gi + 1], g.c, phase == 0 ? conj(g.s) : g.s, comp);
+            }
+            __syncwarp();
+            if (on) reinterpret_cast<double*>(&qrow[comp < 2 ? gi : gi + 1])[comp & 1] = w;
+            __syncwarp();
+        }
+        __syncthreads();
+        beg = end;
+    }
+    for (int k = tid; k < m; k += kQThreads) {
+        if (phase == 0) a.H[(size_t)k * m + r] = qrow[k];
+        else a.H[(size_t)r * m + k] = qrow[k];
+    }
 }
 
 int launch_schur64(const SchurArgs& a, cudaStream_t s) {
@@ -696,6 +754,13 @@ int launch_schur64(const SchurArgs& a, cudaStream_t s) {
     prof_begin("schur_qr", s);
     k_schur_qr64<<<1, kQrThreads, packed, s>>>(a); note_launch();
     prof_end("schur_qr", s);
+    prof_begin("schur_defer", s);
+    k_schur_levels64<<<1, 1024, 0, s>>>(a); note_launch();
+    for (int phase = 0; phase < 2; ++phase) {
+        k_schur_defer64<<<m, kQThreads, sizeof(double2) * m, s>>>(a, phase);
+        note_launch();
+    }
+    prof_end("schur_defer", s);
     prof_begin("schur_reorder", s);
     k_schur_reorder64<<<1, kReThreads, packed, s>>>(a); note_launch();
     prof_end("schur_reorder", s);
