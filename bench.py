@@ -11,6 +11,7 @@ purification and explicit residuals (klst_eigs).  Only eigenpairs with explicit 
 Multi-GPU runs (torchrun) solve independent pencils per rank (replicas; weak scaling).
 """
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -42,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 latency figures")
+    ap.add_argument("--max-restarts", type=int, default=None,
+                    help="cap the eigensolve's restarts (bounded runs for profiling; the line is then not a bench value)")
     ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
                     help="Poisson arrival rates of the serving runs (1/s), comma-separated")
     ap.add_argument("--serve-window", type=float, default=6.0, help="arrival window of each serving run (s)")
@@ -143,6 +146,16 @@ DF64_OPS_PER_CMAC = 60
 # with the algorithmic bytes of the same launches; an entry must be dropped when its kernels change.
 _V101 = 101 * 281088 * 16  # 101 basis columns
 _W = 281088 * 16           # one n-vector
+# float64 path (profiles/c3_fp64_tensor_core_solve_and_gram_schmidt_kernels.md: Arnoldi step
+# j = 110, 28 k-chunks of the basis slices); the Gram-Schmidt figures hold for that step's launch
+_KC110 = 2196 * 28 * 2048  # one slice of the 28 k-chunks of every 128-row tile
+NCU_TRAFFIC_C3_FP64 = {
+    "solve_pass1_tc": (589.822e6 + 3.436e6, 575.7e6 + _W, "k_solve_tc<1>"),
+    "solve_pass2_tc": (589.840e6 + 6.973e6, 575.7e6 + 2 * _W, "k_solve_tc<2>"),
+    "orth_tc_update1": (1137.921e6 + 7.500e6, 9 * _KC110 + 2 * _W, "k_upd_tc<9,0> at j = 110"),
+    "orth_tc_dots2": (1137.923e6 + 4.056e6, 9 * _KC110 + _W, "k_dot_tc at j = 110"),
+    "orth_tc_update2": (760.120e6 + 7.483e6, 6 * _KC110 + 2 * _W, "k_upd_tc<6,1> at j = 110"),
+}
 NCU_TRAFFIC_C3 = {
     "solve_pass1_df64": (301.4e6 + 5.4e6, 288e6 + _W, "k_solve_pass1"),
     "solve_pass2_df64": (301.4e6 + 6.2e6, 288e6 + 2 * _W, "k_solve_pass2"),
@@ -285,8 +298,9 @@ def kernel_rooflines(groups, spec, es, info_list, steps, peaks, path="fp64", fp6
                          f"complex MACs)", achieved=fl / avg_s / 1e12, peak=fp64_peak, hbm_gbs=by / avg_s / 1e9)
         if "peak" in e:
             e["frac"] = e["achieved"] / e["peak"]
-        if spec.n == 281088 and name in NCU_TRAFFIC_C3:
-            t, alg, what = NCU_TRAFFIC_C3[name]
+        table = NCU_TRAFFIC_C3 if path == "df64" else NCU_TRAFFIC_C3_FP64
+        if spec.n == 281088 and name in table:
+            t, alg, what = table[name]
             e["ncu_traffic"] = {"bytes": t, "algorithmic_bytes": alg, "ratio": t / alg, "kernels": what}
         out[name] = e
     return out
@@ -332,6 +346,8 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     spec, es, sigma = workload(args.workload, rank)
+    if args.max_restarts is not None:
+        es = dataclasses.replace(es, max_restarts=args.max_restarts)
     n = spec.n
     from paper_2607_27440_b300 import workloads as wl
     v0_host = torch.from_numpy(wl.start_vector(n, es.seed)).to(torch.complex128)
