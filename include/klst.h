@@ -245,16 +245,17 @@ int klst_eigvec_macro(klst_pencil p, const void* q, int32_t nvec, double* macro_
  * (Eqs. parShiftInvert, parLUfactor).  A - sigma B = K - U V^H where K is block
  * diagonal with one Nx x Nx block per node k (xi_x,k D_x + nu + i beta xi_y,k - sigma,
  * inflow rows replaced by identity rows; shared by g^ and h^) and U V^H is the
- * rank-4-per-point BGK moment coupling.  Computes every K_k^{-1} (batched
- * Gauss-Jordan with partial pivoting), the capacitance C = I - V^H K^{-1} U
- * (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan with partial pivoting: for 4 Nx <= 384 one launch of one
+ * rank-4-per-point BGK moment coupling.  Computes every K_k^{-1} (for Nx <= 128 a complex float32
+ * Gauss-Jordan inverse refined to float64 accuracy by Newton-Schulz steps on the tensor cores, see
+ * klst_factor_inverse_info; otherwise batched float64 Gauss-Jordan with partial pivoting), the
+ * capacitance C = I - V^H K^{-1} U (4 Nx x 4 Nx) and C^{-1} (Gauss-Jordan with partial pivoting: for 4 Nx <= 384 one launch of one
  * thread-block cluster holding the matrix in its CTAs' shared memory, otherwise one launch per
  * pivot; both give the same result).  KLST_NO_CLUSTER_GJ=1 in the environment selects the
  * per-pivot launches.  precision: KLST_FP64 (all float64),
  * KLST_MIXED (K_k^{-1} stored in complex float32, each apply corrected by float64 iterative refinement)
  * or KLST_DF64 (K_k^{-1} stored as double-float pairs, the same bytes as float64, and the block solves
  * run in double-float arithmetic on the float32 pipes; ~2^-48 accuracy without refinement).
- * K_k^{-1} and the capacitance are always formed in float64.
+ * K_k^{-1} and the capacitance are always formed to float64 accuracy.
  * Errors: KLST_ESINGULAR (zero pivot), KLST_ENOMEM.  Synchronising.
  */
 int klst_factor_shift(klst_pencil p, double sigma_re, double sigma_im, int32_t precision,
@@ -264,6 +265,21 @@ void klst_factor_destroy(klst_factor f);
 /* Factor metadata: the pencil it belongs to, its shift and precision; any out may be NULL. */
 int klst_factor_info(klst_factor f, double* sigma_re, double* sigma_im, int32_t* precision,
                      int64_t* footprint_bytes, double* t_factor_ms);
+
+/*
+ * klst_factor_inverse_info -- how the block inverses K_k^{-1} of f were formed (Eq. parLUfactor for
+ * the blocks K_k).  *method: 1 = a complex float32 Gauss-Jordan inverse X_0 refined by Newton-Schulz
+ * steps X <- X + X (I - K_k X), whose products run as float64-accurate integer-slice GEMMs on the
+ * tensor cores (Nx <= 128; each step squares I - K_k X); 0 = float64 Gauss-Jordan with partial
+ * pivoting (Nx > 128, or KLST_NO_TC=1 in the environment).  *steps: Newton-Schulz steps taken (the
+ * largest over the block ranges processed together); *fallback: block ranges whose float32 inverse
+ * was too poor for the iteration to converge (max |I - K X_0| Nx >= 1/2) and that were inverted by
+ * float64 Gauss-Jordan instead; *resid: the largest |I - K_k X| entry computed before the last step
+ * (the entries after it are bounded by (Nx resid)^2 plus float64 rounding).  The blocks are processed
+ * in ranges sized to 768 MB of scratch (KLST_NS_RANGE=n in the environment: n blocks per range); the
+ * result does not depend on the range size.  Any out may be NULL.  Errors: KLST_EINVAL (f NULL).
+ */
+int klst_factor_inverse_info(klst_factor f, int32_t* method, int32_t* steps, int32_t* fallback, double* resid);
 
 /*
  * klst_apply_shift_invert -- y = (A - sigma B)^{-1} B x  (the operator T of Eq. parShiftInvert).

@@ -31,6 +31,8 @@ int64_t solve_footprint(const klst_pencil_desc& d, int precision, const klst_eig
     b += nxi * nx * nx * 16 + (precision == KLST_MIXED ? nxi * nx * nx * 8 : precision == KLST_DF64 ? nxi * nx * nx * 16 : 0);
     if (precision == KLST_FP64 && tc_solve_supported((int)nx))                   // tensor-core slices of K^{-1}
         b += (int64_t)tc_kinv_bytes((int)nx, (int)nxi);
+    if (ns_inverse_supported((int)nx))                                           // Newton-Schulz scratch
+        b += (int64_t)ns_scratch_bytes((int)nx, (int)nxi);
     b += 11 * r * r * 16;                                                        // capacitance buffers
     b += 2 * n * (m + 1) * 16 + 3 * n * nev * 16;                                // Krylov bases + extraction
     b += (precision == KLST_MIXED ? 3 * n * nev * 16 + (int64_t)oz_dx_ws_bytes((int)nx, (int)nxi, (int)nev) : 0);  // refinement work

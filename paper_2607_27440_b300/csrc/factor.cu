@@ -404,6 +404,22 @@ static int launch_block_gj(klst_factor f, C* out, cudaStream_t s) {
     return KLST_OK;
 }
 
+// K_k^{-1} for the blocks k0 .. k0 + nk - 1 into out (column-major, [k - k0][m][j]): float64
+// (double2) or the complex float32 start of the tensor-core Newton-Schulz inverse (float2)
+template <typename C>
+int block_gj_range(klst_factor f, int k0, int nk, C* out, cudaStream_t s) {
+    klst_pencil p = f->p;
+    const size_t bytes = sizeof(C) * p->nx * p->nx;
+    const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
+    if (use_smem) KLST_CK(cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    k_block_gj<C><<<nk, 256, use_smem ? bytes : 0, s>>>(p->nx, nk, p->desc.beta, f->sigma, p->Dx, p->xi_x + k0,
+                                                        p->xi_y + k0, p->nu, out, use_smem, f->status); klst::note_launch();
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+template int block_gj_range<double2>(klst_factor, int, int, double2*, cudaStream_t);
+template int block_gj_range<float2>(klst_factor, int, int, float2*, cudaStream_t);
+
 template <typename C>
 static int launch_cap(klst_factor f, const C* Kinv, double2* Cp, int nsplit, cudaStream_t s) {
     klst_pencil p = f->p;
@@ -510,6 +526,9 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
         // the float64 block solves multiply integer slices of K_k^{-1} on the tensor cores
         // (KLST_NO_TC=1: complex128 products on the float64 pipe)
         f->tc_solve = (precision == KLST_FP64 && tc_solve_supported(p->nx) && !(notc && notc[0] == '1')) ? 1 : 0;
+        // the block inverses: float32 Gauss-Jordan + float64-accurate tensor-core Newton-Schulz steps
+        // (KLST_NO_TC=1: float64 Gauss-Jordan)
+        f->tc_factor = (p->dx_oz && ns_inverse_supported(p->nx) && !(notc && notc[0] == '1')) ? 1 : 0;
     }
     const int r = f->r;
     const size_t esz = precision == KLST_MIXED ? sizeof(float2) : sizeof(double2);
@@ -549,7 +568,17 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
             return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     }
     auto free64 = [&]() { if (precision != KLST_FP64) dfree(K64, s); };
-    int rc = launch_block_gj<double2>(f, K64, s);
+    int rc;
+    if (f->tc_factor) {
+        int info[2];
+        rc = ns_block_inverses(f, K64, s, info, &f->ns_resid);
+        f->ns_steps = info[0];
+        f->ns_fallback = info[1];
+    } else {
+        prof_begin("factor_gj64", s);
+        rc = launch_block_gj<double2>(f, K64, s);
+        prof_end("factor_gj64", s);
+    }
     if (rc) { free64(); return fail(rc); }
     rc = launch_cap<double2>(f, K64, Cp, nsplit, s);
     if (rc) { free64(); return fail(rc); }
@@ -603,6 +632,15 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if ((rc = factor_reserve(f, 1, s)) != KLST_OK) return fail(rc);
     f->t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = f;
+    return KLST_OK;
+}
+
+extern "C" int klst_factor_inverse_info(klst_factor f, int32_t* method, int32_t* steps, int32_t* fallback, double* resid) {
+    if (!f) { set_error("factor is NULL"); return KLST_EINVAL; }
+    if (method) *method = f->tc_factor;
+    if (steps) *steps = f->ns_steps;
+    if (fallback) *fallback = f->ns_fallback;
+    if (resid) *resid = f->ns_resid;
     return KLST_OK;
 }
 

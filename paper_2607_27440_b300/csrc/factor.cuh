@@ -11,6 +11,10 @@ struct klst_factor_s {
     void* KinvT;       // [nxi][nx(m)][nx(j)] column-major inverse blocks, double2 or float2
     void* kslices;     // FP64 with tc_solve: bfloat16 integer slices of every K_k^{-1} + row exponents
     int tc_solve;      // 1: the float64 block solves run on the tensor cores (float64-accurate split)
+    int tc_factor;     // 1: K_k^{-1} by a float32 inverse + tensor-core Newton-Schulz steps
+    int ns_steps;      // Newton-Schulz steps taken (largest over the block ranges)
+    int ns_fallback;   // block ranges inverted by float64 Gauss-Jordan instead
+    double ns_resid;   // largest |I - K X| entry before the last step
     double2* Cinv;     // [r][r] row-major capacitance inverse (float64)
     // apply workspace (sized for nrhs_cap right-hand sides)
     int nrhs_cap;
@@ -147,6 +151,10 @@ bool tc_solve_supported(int nx);
 size_t tc_kinv_bytes(int nx, int nxi);
 int tc_split_kinv(const double2* KinvT, int nx, int nxi, void* buf, cudaStream_t s);
 int tc_solve_groups(int nxi, int ngroups_cap);
+// tensor-core block inverses (factor_tc.cu)
+bool ns_inverse_supported(int nx);
+size_t ns_scratch_bytes(int nx, int nxi);
+int ns_block_inverses(klst_factor f, double2* K64, cudaStream_t s, int info[2], double* rlast);
 int tc_solve_pass(int pass, klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
                   cudaStream_t s, const int* done);
 }  // namespace klst

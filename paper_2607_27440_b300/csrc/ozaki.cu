@@ -28,12 +28,10 @@
 #include <atomic>
 #include <cstring>
 
-#include "oz.cuh"
+#include "oz_gemm.cuh"
 
 namespace klst {
 
-constexpr int OZ_NT = 32;      // output columns per CTA (8 diagonal blocks x 32 = 256 TMEM columns)
-constexpr size_t kOzSmemCap = 200 * 1024;  // dynamic shared memory the GEMM may use
 
 
 // Element sources: the GEMM's A rows and B columns as functions (row, k) -> double
@@ -81,19 +79,6 @@ struct SrcPencilCols {  // Z = D_x Y: column col = rhs * 4 nxi + 2 p + reim of Y
 };
 
 
-// B operand: one warp per column c (a row of B^T) into the stacked slice layout of its N-tile.
-// skip (optional): per column group of cols_per_flag columns, a flag that marks the group done.
-template <class Src>
-__global__ void __launch_bounds__(128) k_oz_split_b(Src src, int N, int Kp, unsigned short* __restrict__ out,
-                                                    int* __restrict__ eb, const int* __restrict__ skip, int cols_per_flag) {
-    const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int ntile = c / OZ_NT, cc = c % OZ_NT;
-    if (ntile >= (N + OZ_NT - 1) / OZ_NT) return;
-    if (skip && c < N && skip[c / cols_per_flag]) return;
-    const int nkc = Kp / 8;
-    auto dst = [&](int sl, int kc) { return out + ((((size_t)ntile * nkc + kc) * OZ_S + sl) * OZ_NT + cc) * 8; };
-    oz_split_row(src, c, Kp, dst, eb + c);
-}
 
 
 
@@ -102,6 +87,7 @@ struct DstColMajor {    // C[c * ld + r]
     double* p;
     int64_t ld;
     int R, N;
+    __device__ void done() {}
     __device__ void operator()(int r, int c, double v) const {
         if (r < R && c < N) p[(int64_t)c * ld + r] = v;
     }
@@ -110,6 +96,7 @@ struct DstBasis {       // column c < keep -> Re V'[r, c], c >= keep -> Im V'[r,
     double* p;
     int64_t ld;
     int R, keep;
+    __device__ void done() {}
     __device__ void operator()(int r, int c, double v) const {
         if (r < R && c < 2 * keep) p[((int64_t)(c < keep ? c : c - keep) * ld + r) * 2 + (c < keep ? 0 : 1)] = v;
     }
@@ -119,6 +106,7 @@ struct DstPencilCols {  // C[j, col] -> z_rhs[p nx + j] component reim, the layo
     double* z;
     int64_t ldz;
     int nx, nxi, N;
+    __device__ void done() {}
     __device__ void operator()(int r, int col, double v) const {
         if (r >= nx || col >= N) return;
         const int per = 4 * nxi, rhs = col / per, cc = col - rhs * per;
@@ -126,131 +114,6 @@ struct DstPencilCols {  // C[j, col] -> z_rhs[p nx + j] component reim, the layo
     }
 };
 
-// One CTA = one 128-row M tile x OZ_NT output columns; four warps.  Thread 0 loads (bulk copies)
-// and issues the MMAs; every warp then drains its 32 TMEM lanes.  smem: the N-tile's stacked B
-// slices (K x OZ_NT x 16 B) and one A slice (K x 256 B).  Waits are bounded: on a timeout the CTA
-// sets ST_TIMEOUT in *st, skips the remaining work, frees its TMEM and returns.
-
-template <class Dst>
-__global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __restrict__ As,
-                                                    const unsigned short* __restrict__ Bs,
-                                                    const int* __restrict__ ea, const int* __restrict__ eb, int Kp,
-                                                    Dst dst, Status* st, const int* __restrict__ skip, int cols_per_flag,
-                                                    int N) {
-    {
-        // every column of this tile belongs to finished work: nothing to do (before any allocation)
-        const int c0 = blockIdx.x * OZ_NT, c1 = min(N, c0 + OZ_NT) - 1;
-        if (skip && skip[c0 / cols_per_flag] && skip[c1 / cols_per_flag]) return;
-    }
-    extern __shared__ __align__(128) unsigned char oz_smem[];
-    __shared__ __align__(8) uint64_t bar_ld, bar_ld2, bar_mma;
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
-    const int ntile = blockIdx.x, mtile = blockIdx.y;
-    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const int nkc = Kp / 8;
-    const uint32_t bytesB = (uint32_t)Kp * OZ_NT * 16;   // nkc x OZ_S x OZ_NT x 16 B
-    const uint32_t bytesA = (uint32_t)Kp * 256;          // nkc x 128 x 16 B
-    unsigned char* sB = oz_smem;
-    unsigned char* sA0 = oz_smem + bytesB;
-    // two A buffers when they fit (the next slice loads while the current one multiplies)
-    const bool dbuf = (size_t)bytesB + 2 * (size_t)bytesA <= kOzSmemCap;
-    unsigned char* sA1 = dbuf ? sA0 + bytesA : sA0;
-    constexpr uint32_t kCols = 256;                      // 8 diagonal blocks x OZ_NT
-    if (tid == 0) {
-        mbar_init(&bar_ld, 1);
-        mbar_init(&bar_ld2, 1);
-        mbar_init(&bar_mma, 1);
-        s_fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (wid == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)), "r"(kCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = tmem_base;
-    if (tid == 0) {
-        const unsigned short* gB = Bs + (size_t)ntile * nkc * OZ_S * OZ_NT * 8;
-        auto gA = [&](int s) { return As + (((size_t)mtile * OZ_S + s) * nkc) * 128 * 8; };
-        // slice s is loaded into buffer s & 1 on barrier bar[s & 1]; with one buffer both are the same
-        uint64_t* bars[2] = {&bar_ld, dbuf ? &bar_ld2 : &bar_ld};
-        unsigned char* bufs[2] = {sA0, sA1};
-        uint32_t ph[2] = {0, 0}, ph_mma = 0;
-        bool ok = true;
-        mbar_expect_tx(bars[0], bytesA + bytesB);
-        bulk_g2s(bufs[0], gA(0), bytesA, bars[0]);
-        bulk_g2s(sB, gB, bytesB, bars[0]);
-        if (dbuf) {
-            mbar_expect_tx(bars[1], bytesA);
-            bulk_g2s(bufs[1], gA(1), bytesA, bars[1]);
-        }
-        for (int s = 0; s < OZ_S && ok; ++s) {
-            const int b = dbuf ? (s & 1) : 0;
-            ok = mbar_wait(bars[b], ph[b]);
-            ph[b] ^= 1;
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // a_s x [b_1 .. b_{8-s}] (N = (8 - s) x OZ_NT) into diagonal blocks s+1 .. 8 (0-based d-2)
-            const int nst = OZ_S - s;
-            const uint32_t idesc = idesc_bf16(128, nst * OZ_NT);
-            const uint32_t dcol = tbase + (uint32_t)(s * OZ_NT);
-            const uint32_t aBase = smem_u32(bufs[b]), bBase = smem_u32(sB);
-            for (int kk = 0; kk < Kp / 16; ++kk) {
-                const uint64_t ad = sdesc(aBase + kk * 2 * 2048, 2048, 128);
-                const uint64_t bd = sdesc(bBase + kk * 2 * (OZ_S * OZ_NT * 16), OZ_S * OZ_NT * 16, 128);
-                mma_bf16(dcol, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-            }
-            mma_commit(&bar_mma);
-            // the buffer is reused only after the MMAs reading it have completed
-            ok = mbar_wait(&bar_mma, ph_mma);
-            ph_mma ^= 1;
-            if (!ok) break;
-            const int nxt = s + (dbuf ? 2 : 1);
-            if (nxt < OZ_S) {
-                mbar_expect_tx(bars[b], bytesA);
-                bulk_g2s(bufs[b], gA(nxt), bytesA, bars[b]);
-            }
-        }
-        if (!ok) {
-            s_fail = 1;
-            atomicOr(&st->flags, ST_TIMEOUT);
-            // give any copy or MMA still in flight one more bounded wait before the TMEM is freed
-            mbar_wait(&bar_ld, ph[0]);
-            if (dbuf) mbar_wait(&bar_ld2, ph[1]);
-            mbar_wait(&bar_mma, ph_mma);
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!s_fail) {
-        // C[r, c] = 2^(ea + eb) sum_{d=2..9} block_d 2^(-7 d), each block an exact integer below 2^24
-        const int r = mtile * 128 + wid * 32 + lane;
-        const uint32_t lane_off = (uint32_t)(wid * 32) << 16;
-        const int era = ea[r];
-        for (int c0 = 0; c0 < OZ_NT; c0 += 8) {
-            float blk[OZ_S][8];
-#pragma unroll
-            for (int d = 0; d < OZ_S; ++d) tmem_ld8(tbase + lane_off + (uint32_t)(d * OZ_NT + c0), blk[d]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float col[OZ_S];
-#pragma unroll
-                for (int d = 0; d < OZ_S; ++d) col[d] = blk[d][q];
-                const double v = oz_combine(col);
-                const int c = ntile * OZ_NT + c0 + q;
-                dst(r, c, scale2(v, era + eb[c]));
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
-}
 
 // ------------------------------------------------------------------ host side
 size_t oz_workspace_bytes(int M, int N, int K) {
@@ -285,7 +148,7 @@ static int oz_launch_gemm(const OzWork& w, int M, int N, int Kp, Dst dst, Status
     const size_t smem = bytesB + (bytesB + 2 * bytesA <= kOzSmemCap ? 2 : 1) * bytesA;
     if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap));
     dim3 grid((N + OZ_NT - 1) / OZ_NT, (M + 127) / 128);
-    k_oz_gemm<Dst><<<grid, 128, smem, s>>>(w.A, w.B, w.ea, w.eb, Kp, dst, st, skip, cols_per_flag, N);
+    k_oz_gemm<Dst><<<grid, 128, smem, s>>>(w.A, w.B, w.ea, w.eb, Kp, dst, st, skip, cols_per_flag, N, 0);
     note_launch();
     KLST_CK_LAUNCH();
     return KLST_OK;

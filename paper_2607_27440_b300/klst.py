@@ -76,6 +76,7 @@ EXPORTS = {
     "klst_factor_shift": (c_int32, [c_void_p, c_double, c_double, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
     "klst_factor_destroy": (None, [c_void_p]),
     "klst_factor_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "klst_factor_inverse_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "klst_apply_shift_invert": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "klst_factor_set_refine": (c_int32, [c_void_p, c_int32, c_double]),
     "klst_factor_check": (c_int32, [c_void_p, c_void_p]),
@@ -311,6 +312,14 @@ class Factor:
             self.handle = None
 
     __del__ = close
+
+    def inverse_info(self):
+        """klst_factor_inverse_info: {"method": 1 tensor-core Newton-Schulz | 0 float64 Gauss-Jordan,
+        "steps", "fallback", "resid"}."""
+        m, st, fb, r = c_int32(), c_int32(), c_int32(), c_double()
+        _check(load().klst_factor_inverse_info(self.handle, ctypes.byref(m), ctypes.byref(st), ctypes.byref(fb),
+                                               ctypes.byref(r)))
+        return {"method": m.value, "steps": st.value, "fallback": fb.value, "resid": r.value}
 
     def set_refine(self, max_refine, refine_tol):
         _check(load().klst_factor_set_refine(self.handle, max_refine, refine_tol))
