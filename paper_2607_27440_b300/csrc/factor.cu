@@ -221,6 +221,144 @@ __global__ void __launch_bounds__(256) k_gj_step(int r, int p, const double2* __
     }
 }
 
+// Bounded grid-wide barrier for the cooperative Gauss-Jordan (every CTA of the grid is resident):
+// the last CTA to arrive resets the counter and advances the generation; the others poll it with a
+// limit, after which the barrier returns false.  Thread 0 of each CTA arrives; the result is
+// broadcast to the CTA.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned& my_gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned g = my_gen;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long it = 0;
+            while (*(volatile unsigned*)gen == g) {
+                if (++it > (1ll << 24)) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        my_gen = g + 1;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The per-pivot Gauss-Jordan of k_gj_step with all r pivots in one cooperative launch: step p reads
+// buffer p % 2 (through L2: other CTAs wrote it) and writes buffer (p + 1) % 2, and a grid barrier
+// separates the steps instead of a kernel boundary.  Same arithmetic, so the same result.  A barrier
+// that gives up sets ST_TIMEOUT and ends the CTA's loop.
+__global__ void __launch_bounds__(256) k_gj_coop(int r, double2* __restrict__ b0, double2* __restrict__ b1,
+                                                 int* __restrict__ perm, unsigned* __restrict__ barw, Status* st) {
+    extern __shared__ double2 sh[];
+    double2* prow = sh;
+    double2* rowp = sh + r;
+    double2* fcol = sh + 2 * r;   // [rows_per]
+    __shared__ double rv[8];
+    __shared__ int ri[8];
+    __shared__ int s_piv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rows_per = (r + gridDim.x - 1) / gridDim.x;
+    const int r0 = min(r, blockIdx.x * rows_per), r1 = min(r, r0 + rows_per);
+    unsigned my_gen = *(volatile unsigned*)(barw + 32);
+    for (int p = 0; p < r; ++p) {
+        const double2* src = (p & 1) ? b1 : b0;
+        double2* dst = (p & 1) ? b0 : b1;
+        double best = -1;
+        int bi = r;
+        for (int i = p + tid; i < r; i += nt) {
+            const double v = abs2(__ldcg(src + (size_t)i * r + p));
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = rv[0];
+            int i0 = ri[0];
+            for (int w = 1; w < (nt >> 5); ++w)
+                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+            if (!(b > 0) && blockIdx.x == 0) atomicOr(&st->flags, ST_SINGULAR);
+            s_piv = i0 < r ? i0 : p;
+            if (blockIdx.x == 0) perm[p] = s_piv;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        for (int c = tid; c < r; c += nt) {
+            prow[c] = __ldcg(src + (size_t)piv * r + c);
+            rowp[c] = __ldcg(src + (size_t)p * r + c);
+        }
+        __syncthreads();
+        double2 inv = prow[p];
+        if (!(abs2(inv) > 0)) inv.x = 1;
+        inv = cinv(inv);
+        // the multipliers of the CTA's rows, once per row
+        if (tid < r1 - r0) {
+            const int i = r0 + tid;
+            fcol[tid] = ((i == piv) ? rowp[p] : __ldcg(src + (size_t)i * r + p)) * inv;
+        }
+        __syncthreads();
+        for (int i = r0; i < r1; ++i) {
+            const double2 f = fcol[i - r0];
+            const double2* si = (i == piv) ? rowp : nullptr;
+            for (int c = tid; c < r; c += nt) {
+                double2 v;
+                if (i == p) v = (c == p) ? inv : prow[c] * inv;
+                else {
+                    const double2 sv = si ? si[c] : __ldcg(src + (size_t)i * r + c);
+                    v = (c == p) ? -f : sv - f * prow[c];
+                }
+                dst[(size_t)i * r + c] = v;
+            }
+        }
+        if (!grid_barrier(barw, barw + 32, my_gen)) {
+            if (tid == 0) atomicOr(&st->flags, ST_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// Launches k_gj_coop on up to one CTA per SM when the device can hold the whole grid at once
+// (cooperative launch); returns false (and launches nothing) otherwise.
+static bool launch_gj_coop(int r, double2* b0, double2* b1, int* perm, unsigned* barw, Status* st, cudaStream_t s) {
+    static std::mutex mu;
+    static int per_sm = -1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (per_sm < 0) {
+            int coop = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+            int nb = 0;
+            if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gj_coop, 256, sizeof(double2) * (2 * 512 + 256)) != cudaSuccess)
+                nb = 0;
+            per_sm = nb;
+            cudaGetLastError();
+        }
+    }
+    int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
+    if (per_sm < 1 || r > 512 || (r + nb - 1) / nb > 256) return false;
+    const size_t smem = sizeof(double2) * (2 * r + (r + nb - 1) / nb);
+    void* args[] = {&r, &b0, &b1, &perm, &barw, &st};
+    if (cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3(nb), dim3(256), args, smem, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    klst::note_launch();
+    return true;
+}
+
 // The same Gauss-Jordan inverse in one launch of one thread-block cluster of NC CTAs, for
 // r <= 384: CTA q keeps rows [q rpc, (q+1) rpc) in shared memory; per pivot the CTAs exchange
 // their column-maximum candidates and read the pivot row and row p through distributed shared
@@ -554,7 +692,7 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if ((e = dmalloc((void**)&Cp, sizeof(double2) * (size_t)nsplit * r * r, s)) != cudaSuccess ||
         (e = dmalloc((void**)&b0, sizeof(double2) * (size_t)r * r, s)) != cudaSuccess ||
         (e = dmalloc((void**)&b1, sizeof(double2) * (size_t)r * r, s)) != cudaSuccess ||
-        (e = dmalloc((void**)&bar, sizeof(int) * r, s)) != cudaSuccess)
+        (e = dmalloc((void**)&bar, sizeof(int) * (r + 128), s)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     cudaMemsetAsync(f->status, 0, sizeof(Status), s);
     cudaMemsetAsync(f->worst, 0, sizeof(double), s);
@@ -605,9 +743,17 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
         const int nb = std::max(1, std::min(device_sm_count(), (r + 3) / 4));
         const size_t smem = sizeof(double2) * 2 * r;
         int* perm = (int*)bar;
-        for (int p = 0; p < r; ++p) {
-            k_gj_step<<<nb, 256, smem, s>>>(r, p, (p & 1) ? b1 : b0, (p & 1) ? b0 : b1, perm, f->status);
-            klst::note_launch();
+        // one cooperative launch with grid barriers between the pivots, else one launch per pivot
+        // (KLST_NO_COOP_GJ=1: always per pivot); both give the same result
+        unsigned* barw = (unsigned*)(bar + r + 32);   // counter, generation 32 words later
+        cudaMemsetAsync(barw, 0, sizeof(unsigned) * 64, s);
+        const char* nocoop = getenv("KLST_NO_COOP_GJ");
+        if (!(nocoop && nocoop[0] == '1') && launch_gj_coop(r, b0, b1, perm, barw, f->status, s)) {
+        } else {
+            for (int p = 0; p < r; ++p) {
+                k_gj_step<<<nb, 256, smem, s>>>(r, p, (p & 1) ? b1 : b0, (p & 1) ? b0 : b1, perm, f->status);
+                klst::note_launch();
+            }
         }
         k_gj_unpermute<<<std::min(1024, (r * r + 255) / 256), 256, sizeof(int) * r, s>>>(r, (r & 1) ? b1 : b0,
                                                                                         (r & 1) ? b0 : b1, perm); klst::note_launch();
@@ -628,6 +774,10 @@ extern "C" int klst_factor_shift(klst_pencil p, double sr, double si, int32_t pr
     if (hst.flags & ST_SINGULAR) {
         set_error("zero pivot: a shifted block K_k - sigma or the capacitance matrix is singular");
         return fail(KLST_ESINGULAR);
+    }
+    if (hst.flags & ST_TIMEOUT) {
+        set_error("factorisation: a bounded wait of a tensor-core product or a grid barrier gave up");
+        return fail(KLST_ETIMEOUT);
     }
     if ((rc = factor_reserve(f, 1, s)) != KLST_OK) return fail(rc);
     f->t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -156,19 +156,186 @@ struct DstXUpd {
     __device__ void done() {}
 };
 
-__global__ void k_c64_to_c128(const float2* __restrict__ in, double2* __restrict__ out, size_t count) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += gridDim.x * (size_t)blockDim.x) {
-        const float2 v = in[i];
-        out[i] = make_double2((double)v.x, (double)v.y);
+// The complex float32 start X_0 = K_k^{-1}: one CTA per block, Gauss-Jordan with the matrix in
+// registers.  Thread t holds row i = t / TPR and the column pairs (2 (t % TPR) + 2 TPR q, +1), so
+// the TPR threads of a row read consecutive 16-byte pairs of the pivot row (no bank conflicts).
+// Pivoting is implicit: step p pivots on the unused row r_p with the largest |T(r, p)|^2 (compared
+// on its leading 25 bits, lowest row on ties) without moving rows; every warp repeats the search on
+// the pivot column in shared memory (one packed-key max reduction), with the used rows replicated in
+// each thread, and the pivot row's threads publish it unscaled.  In-place update at step p,
+// inv = 1 / T(r_p, p):
+//   row r_p:  T(r_p, c) <- T(r_p, c) inv,  T(r_p, p) <- inv
+//   row i:    f = T(i, p) inv,  T(i, c) <- T(i, c) - f T(r_p, c),  T(i, p) <- -f
+// after which K^{-1}(step(i), r_c) = T(i, c), step(r_p) = p; the result is staged in shared memory
+// in that order and written out widened to complex128, column-major ([k][m][j] = K^{-1}(j, m)).
+// A zero or non-finite pivot column sets *poor to the bit pattern of +inf (the range then takes the
+// float64 Gauss-Jordan fallback, which reports a truly singular block).
+template <int TPR>   // threads per row
+__global__ void __launch_bounds__(128 * TPR, 1)
+k_gj32_regs(int nx, double beta, double2 sigma, const double* __restrict__ Dx, const double* __restrict__ xi_x,
+            const double* __restrict__ xi_y, const double* __restrict__ nu, double2* __restrict__ out,
+            unsigned* __restrict__ poor) {
+    constexpr int NP = 64 / TPR, NT = 128 * TPR;    // column pairs per thread, threads
+    extern __shared__ __align__(16) float2 stage[];   // [nx][nx]: K^{-1}(j, m) at m nx + j
+    __shared__ float2 colp[2][128];
+    __shared__ __align__(16) float4 prow[2][64];      // pivot row as column pairs
+    __shared__ int s_piv[128], s_step[128];
+    const int t = threadIdx.x, i = t / TPR, sub = t % TPR, lane = t & 31;
+    const int k = blockIdx.x;
+    const bool live = i < nx;
+    float4 a[NP];   // pair q: columns 2 (sub + TPR q) and 2 (sub + TPR q) + 1
+    {
+        const double xix = xi_x[k], xiy = xi_y[k];
+        const bool bc = live && is_bc(i, nx, xix);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float v[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = 2 * (sub + TPR * q) + h;
+                double re = 0.0, im = 0.0;
+                if (live && c < nx) {
+                    if (bc) {
+                        re = c == i ? 1.0 : 0.0;
+                    } else {
+                        re = xix * Dx[i * nx + c];
+                        if (c == i) { re += nu[i] - sigma.x; im = beta * xiy - sigma.y; }
+                    }
+                }
+                v[2 * h] = (float)re;
+                v[2 * h + 1] = (float)im;
+            }
+            a[q] = make_float4(v[0], v[1], v[2], v[3]);
+        }
     }
+    unsigned used0 = 0u, used1 = 0u, used2 = 0u, used3 = 0u;
+    bool bad = false;
+#pragma unroll 1
+    for (int p = 0; p < nx; ++p) {
+        const int b = p & 1;
+        const int owner = (p >> 1) % TPR, qp = (p >> 1) / TPR, hp = p & 1;
+        if (live && sub == owner) {
+            float4 v = a[0];
+#pragma unroll
+            for (int q = 1; q < NP; ++q)
+                if (q == qp) v = a[q];
+            colp[b][i] = hp ? mkf(v.z, v.w) : mkf(v.x, v.y);
+        }
+        __syncthreads();
+        // key = leading bits of |T(r, p)|^2 (non-negative floats order as integers) | 127 - r
+        unsigned key = 0u;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int r = lane + 32 * h;
+            const unsigned u = h == 0 ? used0 : h == 1 ? used1 : h == 2 ? used2 : used3;
+            if (r < nx && !((u >> lane) & 1u)) {
+                const float m = abs2(colp[b][r]);
+                const unsigned bits = (m >= 0.0f && m <= 3.4e38f) ? (__float_as_uint(m) & ~127u) : 0u;
+                key = max(key, (bits | (unsigned)(127 - r)) + 128u);   // + 128: a candidate beats "none"
+            }
+        }
+        key = __reduce_max_sync(0xffffffffu, key);
+        int r;
+        bool ok;
+        if (key >= 128u) {
+            key -= 128u;
+            r = 127 - (int)(key & 127u);
+            ok = (key & ~127u) != 0u;
+        } else {
+            // no unused row compared (cannot happen while p < nx): the lowest unused row
+            r = 0;
+            ok = false;
+#pragma unroll
+            for (int h = 3; h >= 0; --h) {
+                const int cnt = min(32, max(0, nx - 32 * h));
+                const unsigned u = h == 0 ? used0 : h == 1 ? used1 : h == 2 ? used2 : used3;
+                const unsigned fr = ~u & (cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u));
+                if (fr) r = 32 * h + __ffs(fr) - 1;
+            }
+        }
+        const unsigned bit = 1u << (r & 31);
+        if ((r >> 5) == 0) used0 |= bit; else if ((r >> 5) == 1) used1 |= bit; else if ((r >> 5) == 2) used2 |= bit; else used3 |= bit;
+        if (t == 0) { s_piv[p] = r; s_step[r] = p; }
+        bad |= !ok;
+        const float2 inv = ok ? cinv(colp[b][r]) : mkf(1.0f, 0.0f);
+        if (i == r) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) prow[b][sub + TPR * q] = a[q];
+        }
+        __syncthreads();
+        if (i == r) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 lo = mkf(a[q].x, a[q].y) * inv, hi = mkf(a[q].z, a[q].w) * inv;
+                float4 v = make_float4(lo.x, lo.y, hi.x, hi.y);
+                if (q == qp && sub == owner) {
+                    if (hp) { v.z = inv.x; v.w = inv.y; } else { v.x = inv.x; v.y = inv.y; }
+                }
+                a[q] = v;
+            }
+        } else if (live) {
+            const float2 f = colp[b][i] * inv;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float4 pr = prow[b][sub + TPR * q];
+                float4 v;
+                v.x = a[q].x - (f.x * pr.x - f.y * pr.y);
+                v.y = a[q].y - (f.x * pr.y + f.y * pr.x);
+                v.z = a[q].z - (f.x * pr.z - f.y * pr.w);
+                v.w = a[q].w - (f.x * pr.w + f.y * pr.z);
+                if (q == qp && sub == owner) {
+                    if (hp) { v.z = -f.x; v.w = -f.y; } else { v.x = -f.x; v.y = -f.y; }
+                }
+                a[q] = v;
+            }
+        }
+    }
+    if (bad && t == 0) atomicMax(poor, 0x7FF00000u);
+    __syncthreads();
+    if (live) {
+        const int j = s_step[i];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int c = 2 * (sub + TPR * q);
+            if (c < nx) stage[s_piv[c] * nx + j] = mkf(a[q].x, a[q].y);
+            if (c + 1 < nx) stage[s_piv[c + 1] * nx + j] = mkf(a[q].z, a[q].w);
+        }
+    }
+    __syncthreads();
+    double2* o = out + (size_t)k * nx * nx;
+    for (int e = t; e < nx * nx; e += NT) o[e] = to_d(stage[e]);
 }
 
+template <int TPR>
+int launch_gj32_t(klst_factor f, int k0, int nk, double2* X, unsigned* poor, cudaStream_t s) {
+    static std::atomic<unsigned long long> attr{0};
+    klst_pencil p = f->p;
+    const size_t smem = sizeof(float2) * p->nx * p->nx;
+    if (once_per_device(attr))
+        KLST_CK(cudaFuncSetAttribute(k_gj32_regs<TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(float2) * 128 * 128)));
+    k_gj32_regs<TPR><<<nk, 128 * TPR, smem, s>>>(p->nx, p->desc.beta, f->sigma, p->Dx, p->xi_x + k0, p->xi_y + k0, p->nu,
+                                                X, poor);
+    note_launch();
+    KLST_CK_LAUNCH();
+    return KLST_OK;
+}
+
+// threads per row of the float32 Gauss-Jordan: 4 (512 threads, 2.2 ms for 1,098 blocks of 128 on a
+// B300), or 8 with KLST_GJ32_TPR=8 (2.6 ms)
+int launch_gj32(klst_factor f, int k0, int nk, double2* X, unsigned* poor, cudaStream_t s) {
+    const char* env = getenv("KLST_GJ32_TPR");
+    if (env && atoi(env) == 8) return launch_gj32_t<8>(f, k0, nk, X, poor, s);
+    return launch_gj32_t<4>(f, k0, nk, X, poor, s);
+}
+
+// single_a: one A buffer, so that two CTAs fit on an SM when B and A together take <= 113 KB
 template <class Dst>
 int launch_gemm(const unsigned short* As, const unsigned short* Bs, const int* ea, const int* eb, int Kp, int ntx,
-                int nty, int N, int batched, const Dst& dst, Status* st, cudaStream_t s) {
+                int nty, int N, int batched, const Dst& dst, Status* st, cudaStream_t s, bool single_a = false) {
     static std::atomic<unsigned long long> attr{0};
     const size_t bytesB = (size_t)Kp * OZ_NT * 16, bytesA = (size_t)Kp * 256;
-    const size_t smem = bytesB + (bytesB + 2 * bytesA <= kOzSmemCap ? 2 : 1) * bytesA;
+    const size_t smem = bytesB + (!single_a && bytesB + 2 * bytesA <= kOzSmemCap ? 2 : 1) * bytesA;
     if (once_per_device(attr))
         KLST_CK(cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap));
     k_oz_gemm<Dst><<<dim3(ntx, nty), 128, smem, s>>>(As, Bs, ea, eb, Kp, dst, st, nullptr, 1, N, batched);
@@ -196,7 +363,9 @@ int ns_step(klst_factor f, const NsShape& sh, int k0, int nk, const double2* X, 
         const int* ea = (const int*)((const char*)p->dx_oz + (size_t)128 * sh.Kp1 * OZ_S * 2);
         DstResid dst{X, reinterpret_cast<double*>(R), p->xi_x + k0, p->xi_y + k0, p->nu, p->desc.beta, f->sigma,
                      nx, N, rmax};
-        int rc = launch_gemm(A, B, ea, eb, sh.Kp1, nt, 1, N, 0, dst, f->status, s);
+        // one A buffer (96 KB at Nx = 128): two CTAs per SM overlap each other's loads, MMAs and
+        // float64 epilogues (3.5 against 5.1 ms for the two steps at Nx = 128, Nxi = 1,098)
+        int rc = launch_gemm(A, B, ea, eb, sh.Kp1, nt, 1, N, 0, dst, f->status, s, true);
         if (rc) return rc;
     }
     prof_end("factor_ns_resid", s);
@@ -265,14 +434,9 @@ int ns_block_inverses(klst_factor f, double2* K64, cudaStream_t s, int info[2], 
         const int nk = std::min(nkmax, nxi - k0);
         double2* Xa = K64 + (size_t)k0 * nx * nx;
         cudaMemsetAsync(rmax, 0, sizeof(unsigned) * kNsMaxSteps, s);
-        // X_0: complex float32 Gauss-Jordan (into R's storage), widened into Xa
+        // X_0: complex float32 Gauss-Jordan, widened into Xa
         prof_begin("factor_gj32", s);
-        if ((rc = block_gj_range<float2>(f, k0, nk, (float2*)R, s)) != KLST_OK) break;
-        {
-            const size_t cnt = (size_t)nk * nx * nx;
-            k_c64_to_c128<<<(int)std::min<size_t>((cnt + 255) / 256, 8192), 256, 0, s>>>((const float2*)R, Xa, cnt);
-            note_launch();
-        }
+        if ((rc = launch_gj32(f, k0, nk, Xa, rmax, s)) != KLST_OK) break;
         prof_end("factor_gj32", s);
         int steps = 0;
         unsigned hr[kNsMaxSteps];

@@ -54,8 +54,11 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(const unsigned short* __rest
     const uint32_t bytesA = (uint32_t)Kp * 256;          // nkc x 128 x 16 B
     unsigned char* sB = oz_smem;
     unsigned char* sA0 = oz_smem + bytesB;
-    // two A buffers when they fit (the next slice loads while the current one multiplies)
-    const bool dbuf = (size_t)bytesB + 2 * (size_t)bytesA <= kOzSmemCap;
+    // two A buffers when the launch gave room for them (the next slice loads while the current one
+    // multiplies); a launch with room for one leaves space for a second CTA on the SM instead
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const bool dbuf = bytesB + 2 * bytesA <= dyn;
     unsigned char* sA1 = dbuf ? sA0 + bytesA : sA0;
     constexpr uint32_t kCols = 256;                      // 8 diagonal blocks x OZ_NT
     if (tid == 0) {

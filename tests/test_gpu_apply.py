@@ -90,24 +90,26 @@ def test_exactly_singular_block_is_reported(klst):
     assert ei.value.code == klst.KLST_ESINGULAR
 
 
-@pytest.mark.parametrize("nx", [32, 64, 96], ids=["r128", "r256", "r384"])
-def test_capacitance_inverse_cluster_equals_per_pivot(klst, nx, monkeypatch):
-    """C^{-1} by one thread-block-cluster launch (8 CTAs up to r = 256, 16 at r = 384) follows the
-    per-pivot Gauss-Jordan launches operation for operation: the applies agree bit for bit, and
-    the cluster factorisation launches about r fewer kernels."""
-    spec = wl.tiny(nx=nx, qx=6, qy=4, mach=3.0, beta=0.5)
+@pytest.mark.parametrize("nx", [32, 64, 96, 128], ids=["r128", "r256", "r384", "r512"])
+def test_capacitance_inverse_cluster_coop_and_per_pivot_agree(klst, nx, monkeypatch):
+    """C^{-1} by one thread-block-cluster launch (8 CTAs up to r = 256, 16 at r = 384; r = 512 does
+    not fit), by one cooperative launch with grid barriers between the pivots (KLST_NO_CLUSTER_GJ=1)
+    and by one launch per pivot (also KLST_NO_COOP_GJ=1) follow the same operations: the applies
+    agree bit for bit, and the per-pivot factorisation launches about r more kernels."""
+    spec = wl.tiny(nx=nx, qx=6, qy=4, mach=3.0, beta=0.5) if nx < 128 else wl.tiny(nx=nx, qx=4, qy=2, mach=3.0, beta=0.5)
     x = to_dev(wl.start_vector(spec.n, 7))
     P = klst.Pencil(spec)
     lib = klst.load()
-    c0 = lib.klst_launch_count()
-    y1 = to_host(P.factor(0.1j, precision=0).apply(x))
-    c1 = lib.klst_launch_count()
-    monkeypatch.setenv("KLST_NO_CLUSTER_GJ", "1")
-    y2 = to_host(P.factor(0.1j, precision=0).apply(x))
-    c2 = lib.klst_launch_count()
+    ys, counts = [], []
+    for env in ({}, {"KLST_NO_CLUSTER_GJ": "1"}, {"KLST_NO_CLUSTER_GJ": "1", "KLST_NO_COOP_GJ": "1"}):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        c0 = lib.klst_launch_count()
+        ys.append(to_host(P.factor(0.1j, precision=0).apply(x)))
+        counts.append(lib.klst_launch_count() - c0)
     r = 4 * nx
-    assert (c2 - c1) - (c1 - c0) >= r - 2, ((c1 - c0), (c2 - c1))
-    assert np.array_equal(y1, y2)
+    assert counts[2] - counts[1] >= r - 2 and counts[2] - counts[0] >= r - 2, counts
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
 
 
 def test_refinement_shortfall_reports_erefine(klst):
