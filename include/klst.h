@@ -112,6 +112,34 @@ typedef struct {
     int64_t schur_rotations; /* Givens rotations logged by the Schur step, summed over restarts */
 } klst_eigs_info;
 
+/* Jacobi-Davidson options (klst_jd_eigs; Sec. 4.2 and the solver table of the paper) */
+typedef enum { KLST_JD_PREC_FULL = 0, KLST_JD_PREC_BLOCK = 1 } klst_jd_precond;
+typedef struct {
+    int32_t nev;          /* eigenpairs wanted (nearest sigma), 1..64 */
+    int32_t ncv;          /* largest search space, 4..64 (the paper: 150-200 at 281,088 unknowns) */
+    int32_t kmin;         /* search directions kept at a restart, 1 <= kmin < ncv (the paper's k_min = 6) */
+    int32_t max_outer;    /* outer iterations before KLST_ENOCONV */
+    double tol;           /* a harmonic Ritz pair locks when ||r|| <= tol |theta| (||u|| = 1) */
+    int32_t gmres_m;      /* GMRES restart length of the correction equation, 1..64 (the paper: 30) */
+    int32_t gmres_max;    /* GMRES iterations per correction equation (the paper: 200) */
+    double gmres_rtol;    /* relative tolerance on the preconditioned correction residual (1e-6) */
+    double gmres_atol;    /* absolute tolerance (1e-12) */
+    int32_t precond;      /* KLST_JD_PREC_FULL: the factored (A - sigma B)^{-1} (Woodbury);
+                             KLST_JD_PREC_BLOCK: the block inverses K_k^{-1} alone (no moment coupling) */
+    const void* v0;       /* device complex128 start vector (length n) or NULL */
+    uint64_t seed;        /* start vector seed when v0 == NULL */
+} klst_jd_opts;
+typedef struct {
+    int32_t nconv;        /* eigenpairs returned (locked) */
+    int32_t outer;        /* outer iterations */
+    int32_t inner;        /* GMRES iterations in total */
+    int32_t restarts;     /* search-space restarts */
+    int64_t applies_op;   /* applications of A - theta B */
+    int64_t applies_prec; /* preconditioner applications */
+    double t_ms;          /* wall time */
+    double max_resid;     /* max ||A x - omega B x|| over the returned pairs, ||x|| = 1 */
+} klst_jd_info;
+
 typedef struct klst_pencil_s* klst_pencil;
 typedef struct klst_factor_s* klst_factor;
 
@@ -329,6 +357,27 @@ int klst_factor_check(klst_factor f, klst_stream stream);
  */
 int klst_eigs(klst_factor f, const klst_eigs_opts* opts, double* evals_host, void* evecs,
               double* resid_host, klst_eigs_info* info, klst_stream stream);
+
+/*
+ * klst_jd_eigs -- the nev eigenvalues nearest sigma by Jacobi-Davidson with harmonic Ritz extraction
+ * (Sec. 4.2, the paper's second solver; JDQZ form for A q = omega B q with target tau = sigma):
+ * search space V and test space W with (A - tau B) V = Z C + W R, harmonic pairs from
+ * G = R^{-1} W^H B V (mu = 1 / (theta - tau), the largest |mu| nearest tau; the float64 Schur step
+ * of klst_eigs), residual r = (I - Z Z^H)(A - theta B) u; ||r|| <= tol |theta| locks u and its test
+ * vector into the partial Schur bases Q, Z; otherwise the correction equation
+ * (I - z~ z~^H)(A - theta B)(I - q~ q~^H) t = -r is solved by GMRES(gmres_m) (rtol, atol, at most
+ * gmres_max iterations) preconditioned by K = A - sigma B (precond FULL, the factor's exact Woodbury
+ * solve) or by the block inverses alone (BLOCK), projected onto q~'s complement, and t expands V.  A
+ * full search space (ncv) restarts to its kmin leading Schur directions.  The returned pairs come from
+ * the harmonic extraction on the locked space, with explicit residuals ||A x - omega B x||, ||x|| = 1,
+ * nearest sigma first.  f must be a KLST_FP64 factor.  evals_host: complex float64[nev] (re, im);
+ * evecs: device complex128 n x nev (column-major) or NULL; resid_host: float64[nev] or NULL.  All
+ * float64 on the device.  Errors: KLST_EINVAL (options, non-FP64 factor), KLST_ENOCONV (fewer than nev
+ * pairs locked within max_outer iterations, or a breakdown; the locked pairs are returned), KLST_ENOMEM.
+ * Synchronising.
+ */
+int klst_jd_eigs(klst_factor f, const klst_jd_opts* opts, double* evals_host, void* evecs, double* resid_host,
+                 klst_jd_info* info, klst_stream stream);
 
 /*
  * klst_batch_eigs -- many independent pencils at once (wavenumber, shift and Mach sweeps): pencil i

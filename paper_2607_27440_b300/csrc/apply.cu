@@ -222,10 +222,15 @@ template <> const char* pass_name<float4>(int pass) { return pass == 1 ? "solve_
 template <> const char* pass_name<float2>(int pass) { return pass == 1 ? "solve_pass1_c64" : "solve_pass2_c64"; }
 
 // the float64 Woodbury solve with both block passes on the tensor cores
+// kinv_only: y = K^{-1} b, the block inverses alone (s = 0, no first pass)
 static int woodbury_solve_tc(klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
-                             cudaStream_t s, const int* done) {
+                             cudaStream_t s, const int* done, int kinv_only = 0) {
     klst_pencil p = f->p;
     const int ng = tc_solve_groups(p->nxi, f->ngroups);
+    if (kinv_only) {
+        KLST_CK(cudaMemsetAsync(f->sv, 0, sizeof(double2) * f->r * nrhs, s));
+        return tc_solve_pass(2, f, b, mask, y, accumulate, nrhs, s, done);
+    }
     prof_begin("solve_pass1_tc", s);
     int rc = tc_solve_pass(1, f, b, mask, nullptr, 0, nrhs, s, done);
     prof_end("solve_pass1_tc", s);
@@ -242,10 +247,20 @@ static int woodbury_solve_tc(klst_factor f, const double2* b, int mask, double2*
 
 template <typename C>
 static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y, int accumulate, int nrhs,
-                          cudaStream_t s, const int* done) {
+                          cudaStream_t s, const int* done, int kinv_only = 0) {
     klst_pencil p = f->p;
-    if (std::is_same<C, double2>::value && f->tc_solve) return woodbury_solve_tc(f, b, mask, y, accumulate, nrhs, s, done);
+    if (std::is_same<C, double2>::value && f->tc_solve)
+        return woodbury_solve_tc(f, b, mask, y, accumulate, nrhs, s, done, kinv_only);
     const int nx = p->nx, nxi = p->nxi, NXP = nxp_of(nx), KB = 256 / NXP;
+    if (kinv_only) {
+        KLST_CK(cudaMemsetAsync(f->sv, 0, sizeof(double2) * f->r * nrhs, s));
+        const int nb2 = std::min((nxi + KB - 1) / KB, 4 * device_sm_count());
+        k_solve_pass2<C><<<dim3(nb2, nrhs), dim3(NXP, KB), sizeof(C) * KB * 2 * NXP, s>>>(
+            nx, nxi, (const C*)f->KinvT, p->G, p->xi_x, b, p->n, mask, f->sv, y, accumulate, done);
+        klst::note_launch();
+        KLST_CK_LAUNCH();
+        return KLST_OK;
+    }
     const int ng = f->ngroups, kpg = ((nxi + ng - 1) / ng + KB - 1) / KB * KB;
     dim3 blk(NXP, KB);
     const size_t sm1 = std::max(sizeof(C) * KB * 2 * NXP, sizeof(double2) * 4 * KB * NXP);
@@ -264,6 +279,16 @@ static int woodbury_solve(klst_factor f, const double2* b, int mask, double2* y,
     prof_end(pass_name<C>(2), s);
     KLST_CK_LAUNCH();
     return KLST_OK;
+}
+
+// The preconditioner of the Jacobi-Davidson correction equation (one vector): mode 0 the exact
+// y = (A - sigma B)^{-1} x (the Woodbury solve on x itself, its inflow rows included), mode 1 the
+// block inverses alone y = K^{-1} x.  float64 factors.
+int apply_inv(klst_factor f, const double2* x, double2* y, int mode, cudaStream_t s) {
+    if (f->precision != KLST_FP64) { set_error("apply_inv needs a float64 factor"); return KLST_EINVAL; }
+    int rc = factor_reserve(f, 1, s);
+    if (rc) return rc;
+    return woodbury_solve<double2>(f, x, 0, y, 0, 1, s, nullptr, mode == 1 ? 1 : 0);
 }
 
 int apply_T(klst_factor f, const double2* x, double2* y, int nrhs, cudaStream_t s) {

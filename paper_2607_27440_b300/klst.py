@@ -17,6 +17,7 @@ KLST_OK, KLST_EINVAL, KLST_ENOMEM, KLST_ESINGULAR, KLST_ENOCONV, KLST_EREFINE, K
 FP64, MIXED, DF64 = 0, 1, 2
 CONV_REL, CONV_RESID = 0, 1
 ARITH_F64, ARITH_DF64 = 0, 1
+JD_PREC_FULL, JD_PREC_BLOCK = 0, 1
 BASES = {"tanh": 0, "mott_smith": 1}
 
 
@@ -41,6 +42,20 @@ class EigsInfo(ctypes.Structure):
                 ("t_restart_ms", c_double), ("t_schur_ms", c_double),
                 ("reorths", c_int32), ("schur_sweeps", c_int32), ("schur_swaps", c_int32),
                 ("schur_rotations", c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class JdOpts(ctypes.Structure):
+    _fields_ = [("nev", c_int32), ("ncv", c_int32), ("kmin", c_int32), ("max_outer", c_int32), ("tol", c_double),
+                ("gmres_m", c_int32), ("gmres_max", c_int32), ("gmres_rtol", c_double), ("gmres_atol", c_double),
+                ("precond", c_int32), ("v0", c_void_p), ("seed", c_uint64)]
+
+
+class JdInfo(ctypes.Structure):
+    _fields_ = [("nconv", c_int32), ("outer", c_int32), ("inner", c_int32), ("restarts", c_int32),
+                ("applies_op", c_int64), ("applies_prec", c_int64), ("t_ms", c_double), ("max_resid", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +93,8 @@ EXPORTS = {
     "klst_factor_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "klst_factor_inverse_info": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "klst_apply_shift_invert": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    "klst_jd_eigs": (c_int32, [c_void_p, ctypes.POINTER(JdOpts), c_void_p, c_void_p, c_void_p,
+                               ctypes.POINTER(JdInfo), c_void_p]),
     "klst_factor_set_refine": (c_int32, [c_void_p, c_int32, c_double]),
     "klst_factor_check": (c_int32, [c_void_p, c_void_p]),
     "klst_debug_fail_alloc_after": (None, [c_int64]),
@@ -367,6 +384,34 @@ class Factor:
         d["status"] = code
         d["ritz_est"] = est
         return omega, vec, res, d
+
+
+    def jd_eigs(self, nev, ncv=40, kmin=6, tol=1e-10, max_outer=2000, gmres_m=30, gmres_max=200, gmres_rtol=1e-6,
+                gmres_atol=1e-12, precond=JD_PREC_FULL, v0=None, seed=0, vectors=False, stream=None, check=True):
+        """klst_jd_eigs: Jacobi-Davidson with harmonic Ritz extraction; returns (omega[nconv],
+        vecs (nconv, n) or None, resid[nconv], info) with info = the klst_jd_info fields plus ``status``."""
+        torch = _torch()
+        n = self.pencil.n
+        ev = np.zeros(2 * nev)
+        res = np.zeros(nev)
+        vec = torch.empty((nev, n), dtype=torch.complex128, device="cuda") if vectors else None
+        if v0 is not None:
+            v0 = _check_in(v0, n, "v0")
+            if v0.dim() != 1:
+                raise ValueError("v0 must be one vector of length n")
+        opts = JdOpts(nev=nev, ncv=ncv, kmin=kmin, max_outer=max_outer, tol=tol, gmres_m=gmres_m,
+                      gmres_max=gmres_max, gmres_rtol=gmres_rtol, gmres_atol=gmres_atol, precond=precond,
+                      v0=v0.data_ptr() if v0 is not None else None, seed=seed)
+        info = JdInfo()
+        code = load().klst_jd_eigs(self.handle, ctypes.byref(opts), ev.ctypes.data_as(c_void_p),
+                                   _ptr(vec) if vec is not None else None, res.ctypes.data_as(c_void_p),
+                                   ctypes.byref(info), _stream(stream))
+        if check:
+            _check(code)
+        k = info.nconv
+        d = info.as_dict()
+        d["status"] = code
+        return (ev[0:2 * k:2] + 1j * ev[1:2 * k:2], vec[:k] if vec is not None else None, res[:k], d)
 
 
 def _opts(nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, seed=0, conv=CONV_REL, keep=0,
