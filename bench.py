@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 latency figures")
+    ap.add_argument("--no-jd", action="store_true", help="skip the Jacobi-Davidson leg")
     ap.add_argument("--max-restarts", type=int, default=None,
                     help="cap the eigensolve's restarts (bounded runs for profiling; the line is then not a bench value)")
     ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
@@ -363,6 +364,7 @@ def run_ours(args):
                                     v0=v0_dev, vectors=vec_out, check=False, keep=es.keep, arith=arith,
                                     **PATH_OPTS[path])
         good = int(np.sum(res <= RESID_MAX)) if info["status"] in RETURNED else 0
+        info["factor_inverse"] = F.inverse_info()
         return good, om, vec, res, info, P, F
 
     def barrier():
@@ -490,6 +492,7 @@ def run_ours(args):
                    "l2": "working set > L2 (K^-1 288 MB, Krylov basis 544 MB), no flush needed"},
         "per_step": {"restarts": info["restarts"], "applies": info["applies"], "refine_sweeps": info["refine_sweeps"],
                      "reorths": info.get("reorths"), "t_factor_ms": info["t_factor_ms"],
+                     "factor_inverse": info.get("factor_inverse"),
                      "t_eigs_ms": info["t_eigs_ms"], "t_apply_ms": info["t_apply_ms"],
                      "t_orth_ms": info["t_orth_ms"], "t_restart_ms": info["t_restart_ms"],
                      "t_schur_ms": info["t_schur_ms"], "max_resid": info["max_resid"],
@@ -507,6 +510,11 @@ def run_ours(args):
         "peaks_source": src,
         "fp64_peak_tflops": {"value": fp64_peak, "source": fp64_src},
     }
+    if not args.no_jd:
+        try:
+            line["jacobi_davidson"] = jd_leg(klst, spec, sigma, v0)
+        except Exception as ex:  # the headline line must still print
+            line["jacobi_davidson"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_small:
         try:
             line["small_configs"] = small_configs(klst, args.precision)
@@ -528,6 +536,41 @@ def run_ours(args):
     print(json.dumps(line, default=_jsonable), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+JD_NEV = 10
+JD_OPTS = {"ncv": 30, "kmin": 6, "tol": 1e-11, "gmres_m": 20, "gmres_max": 20, "gmres_rtol": 1e-2}
+
+
+def jd_leg(klst, spec, sigma, v0):
+    """The paper's second solver on the same pencil: Jacobi-Davidson with harmonic Ritz extraction
+    (klst_jd_eigs, float64 factor as preconditioner), JD_NEV eigenpairs, against Krylov-Schur for the
+    same JD_NEV on the same factor.  One untimed run of each first; times by CUDA events."""
+    import torch
+    P = klst.Pencil(spec)
+    F = P.factor(sigma, precision=klst.FP64)
+    stream = torch.cuda.current_stream()
+    out = {"nev": JD_NEV, "opts": dict(JD_OPTS), "precond": "factored (A - sigma B)^-1 (Woodbury)"}
+    for name, run in (("jd", lambda: F.jd_eigs(JD_NEV, v0=v0, check=False, **JD_OPTS)),
+                      ("krylov_schur", lambda: F.eigs(JD_NEV, 40, tol=1e-12, v0=v0, check=False))):
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        om, _, res, info = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        good = int(np.sum(res <= RESID_MAX)) if info["status"] in RETURNED else 0
+        out[name] = {"ms": ms, "eigenpairs_per_s": good / (ms / 1e3), "good_eigenpairs": good,
+                     "max_resid": float(np.max(res)) if len(res) else None, "status": info["status"],
+                     **({k: info[k] for k in ("outer", "inner", "restarts", "applies_op", "applies_prec")}
+                        if name == "jd" else {"applies": info["applies"], "restarts": info["restarts"]}),
+                     "_om": om}
+    a, b = out["jd"].pop("_om"), out["krylov_schur"].pop("_om")
+    if len(a) and len(b):
+        perm = np.array([int(np.argmin(np.abs(b - z))) for z in a])
+        out["max_rel_eig_diff_jd_vs_ks"] = float(np.max(np.abs(b[perm] - a) / np.abs(b[perm])))
+    return out
 
 
 def small_configs(klst, path="fp64", reps=100):
