@@ -287,6 +287,25 @@ def kernel_rooflines(groups, spec, es, info_list, steps, peaks, path="fp64", fp6
                 by = sum(per * (j + 1) * n * 16 for j in js)
                 what = f"sum over steps of (j+1) n x 16 B x {per:.3g}"
             e.update(bound="hbm", unit="GB/s", algorithmic=what, achieved=by / (ms / 1e3) / 1e9, peak=hbm)
+        elif name in ("factor_ns_resid", "factor_ns_update"):
+            # the block inverses' Newton-Schulz products as bfloat16 integer-slice MMAs (36 slice pairs,
+            # 128-row tiles, 32-column N tiles): P = D_x X over all 2 Nx Nxi columns (K = Nx padded to
+            # 16), and Y = X R per block (K = 2 Nx padded to 16, N = 2 Nx padded to 32)
+            nsteps = sum((i.get("factor_inverse") or {}).get("steps", 0) for i in info_list)
+            if name == "factor_ns_resid":
+                tiles, kp = (2 * nx * nxi + 31) // 32, (nx + 15) // 16 * 16
+            else:
+                tiles, kp = nxi * ((2 * nx + 31) // 32), (2 * nx + 15) // 16 * 16
+            fl = nsteps * tiles * 36 * 32 * 128 * kp * 2.0
+            pk = peaks.get("bf16_tflops_sustained", 1386.9)
+            e.update(bound="tensor", unit="TFLOP/s (bf16 MMA)",
+                     algorithmic=f"{tiles} tiles x 36 slice pairs x 32 x 128 x {kp} x 2 bf16 flops per step",
+                     achieved=fl / (ms / 1e3) / 1e12, peak=pk,
+                     peak_note="bf16_tflops_sustained (MEASURED_PEAKS.json): timed inside a long step")
+        elif name == "factor_gj32":
+            fl = 8.0 * nxi * nx ** 3   # nx pivots x nx^2 complex multiply-adds per block
+            e.update(bound="alu", unit="T FP32 lane-ops/s", algorithmic=f"{fl:.4g} FP32 ops (8 Nx^3 per block)",
+                     achieved=fl / 2 / (ms / 1e3) / 1e12, peak=FP32_LANE_OPS_PEAK_T)
         elif name == "rotate":
             kp = es.keep or es.nev + (es.ncv - es.nev) // 2
             by = (es.ncv * n + kp * n) * 16

@@ -1,6 +1,7 @@
 // Internal helpers shared by the kLST CUDA sources (not part of the public ABI).
 #pragma once
 #include <atomic>
+#include <mutex>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -137,13 +138,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Kernel launches issued by this library (process-wide counter, read by klst_launch_count).
 void note_launch();
-// true the first time it is called for the current device with this flag word (thread-safe); used
-// to set per-device kernel attributes once
-inline bool once_per_device(std::atomic<unsigned long long>& mask) {
+// Runs set() (a cudaFuncSetAttribute call or a few) once per device and flag word, before any
+// caller returns: a caller that finds the flag unset takes a process-wide lock and re-checks it, so
+// no thread can launch a kernel ahead of the attribute the launch needs.  Returns set()'s error (the
+// flag stays unset then).
+std::mutex& attr_mutex();
+template <class F>
+cudaError_t set_once_per_device(std::atomic<unsigned long long>& mask, F&& set) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return set();
     const unsigned long long bit = 1ull << dev;
-    return !(mask.fetch_or(bit) & bit);
+    if (mask.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(attr_mutex());
+    if (mask.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    const cudaError_t e = set();
+    if (e == cudaSuccess) mask.fetch_or(bit, std::memory_order_release);
+    return e;
 }
 void note_launches(unsigned long long k);
 void set_capturing(bool on);

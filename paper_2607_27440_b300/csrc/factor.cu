@@ -535,7 +535,10 @@ static int launch_block_gj(klst_factor f, C* out, cudaStream_t s) {
     klst_pencil p = f->p;
     const size_t bytes = sizeof(C) * p->nx * p->nx;
     const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
-    if (use_smem) KLST_CK(cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    static std::atomic<unsigned long long> attr{0};
+    KLST_CK(set_once_per_device(attr, [] {
+        return cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }));
     k_block_gj<C><<<p->nxi, 256, use_smem ? bytes : 0, s>>>(p->nx, p->nxi, p->desc.beta, f->sigma, p->Dx, p->xi_x,
                                                            p->xi_y, p->nu, out, use_smem, f->status); klst::note_launch();
     KLST_CK_LAUNCH();
@@ -549,7 +552,10 @@ int block_gj_range(klst_factor f, int k0, int nk, C* out, cudaStream_t s) {
     klst_pencil p = f->p;
     const size_t bytes = sizeof(C) * p->nx * p->nx;
     const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
-    if (use_smem) KLST_CK(cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    static std::atomic<unsigned long long> attr{0};
+    KLST_CK(set_once_per_device(attr, [] {
+        return cudaFuncSetAttribute(k_block_gj<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }));
     k_block_gj<C><<<nk, 256, use_smem ? bytes : 0, s>>>(p->nx, nk, p->desc.beta, f->sigma, p->Dx, p->xi_x + k0,
                                                         p->xi_y + k0, p->nu, out, use_smem, f->status); klst::note_launch();
     KLST_CK_LAUNCH();

@@ -311,9 +311,10 @@ int launch_gj32_t(klst_factor f, int k0, int nk, double2* X, unsigned* poor, cud
     static std::atomic<unsigned long long> attr{0};
     klst_pencil p = f->p;
     const size_t smem = sizeof(float2) * p->nx * p->nx;
-    if (once_per_device(attr))
-        KLST_CK(cudaFuncSetAttribute(k_gj32_regs<TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(float2) * 128 * 128)));
+    KLST_CK(set_once_per_device(attr, [] {
+        return cudaFuncSetAttribute(k_gj32_regs<TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(float2) * 128 * 128));
+    }));
     k_gj32_regs<TPR><<<nk, 128 * TPR, smem, s>>>(p->nx, p->desc.beta, f->sigma, p->Dx, p->xi_x + k0, p->xi_y + k0, p->nu,
                                                 X, poor);
     note_launch();
@@ -336,8 +337,9 @@ int launch_gemm(const unsigned short* As, const unsigned short* Bs, const int* e
     static std::atomic<unsigned long long> attr{0};
     const size_t bytesB = (size_t)Kp * OZ_NT * 16, bytesA = (size_t)Kp * 256;
     const size_t smem = bytesB + (!single_a && bytesB + 2 * bytesA <= kOzSmemCap ? 2 : 1) * bytesA;
-    if (once_per_device(attr))
-        KLST_CK(cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap));
+    KLST_CK(set_once_per_device(attr, [] {
+        return cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap);
+    }));
     k_oz_gemm<Dst><<<dim3(ntx, nty), 128, smem, s>>>(As, Bs, ea, eb, Kp, dst, st, nullptr, 1, N, batched);
     note_launch();
     KLST_CK_LAUNCH();

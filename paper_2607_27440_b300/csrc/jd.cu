@@ -642,9 +642,10 @@ extern "C" int klst_jd_eigs(klst_factor f, const klst_jd_opts* o, double* evals_
     };
     {
         static std::atomic<unsigned long long> attr{0};
-        if (once_per_device(attr))
-            JD_CK(cudaFuncSetAttribute(k_jd_rotate_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(double2) * 3 * kJdMaxM * kJdMaxM)));
+        JD_CK(set_once_per_device(attr, [] {
+            return cudaFuncSetAttribute(k_jd_rotate_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double2) * 3 * kJdMaxM * kJdMaxM));
+        }));
     }
     // ---- the iteration
     int k = 0, m = 0, outer = 0, inner = 0, restarts = 0;

@@ -286,10 +286,11 @@ int pencil_rows_dev(klst_pencil p, const double2* m, const double2* x, int64_t l
     const int NXP = nxp_of(p->nx), KB = 256 / NXP;
     const size_t smem = pencil_rows_smem(p);
     static std::atomic<unsigned long long> attr_set{0};
-    if (once_per_device(attr_set)) {
-        cudaFuncSetAttribute(k_pencil_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_pencil_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    }
+    set_once_per_device(attr_set, [] {
+        cudaError_t e = cudaFuncSetAttribute(k_pencil_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pencil_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return e;
+    });
     dim3 blk(NXP, KB), grd(pencil_rows_blocks(p), nrhs);
     if (df_arith)
         k_pencil_rows<true><<<grd, blk, smem, s>>>(p->nx, p->nxi, p->desc.beta, p->DxT, p->xi_x, p->xi_y, p->nu, p->G,

@@ -394,10 +394,11 @@ int gs_update_tc(const unsigned short* SL, int64_t n, const double2* h, double2*
                  int j, const int* jd, Status* st, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const size_t sm9 = tcstream_smem<UpdPolicy<9, false>>(), sm6 = tcstream_smem<UpdPolicy<6, true>>();
-    if (once_per_device(attr)) {
-        KLST_CK(cudaFuncSetAttribute(k_upd_tc<9, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm9));
-        KLST_CK(cudaFuncSetAttribute(k_upd_tc<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm6));
-    }
+    KLST_CK(set_once_per_device(attr, [&] {
+        cudaError_t e = cudaFuncSetAttribute(k_upd_tc<9, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm9);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_upd_tc<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm6);
+        return e;
+    }));
     GsArgs a{};
     a.SL = SL; a.n = n; a.ntiles = (int)((n + 127) / 128); a.h = h; a.w = w; a.npart = npart; a.jd = jd; a.j = j;
     a.st = st;
@@ -414,7 +415,9 @@ int gs_dots_tc(const unsigned short* SL, int64_t n, const double2* w, double2* p
                Status* st, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const size_t sm = tcstream_smem<DotPolicy>();
-    if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_dot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KLST_CK(set_once_per_device(attr, [&] {
+        return cudaFuncSetAttribute(k_dot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    }));
     GsArgs a{};
     a.SL = SL; a.n = n; a.ntiles = (int)((n + 127) / 128); a.w = const_cast<double2*>(w); a.part = part; a.ldp = ldp;
     a.jd = jd; a.j = j; a.st = st;

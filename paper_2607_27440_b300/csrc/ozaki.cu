@@ -146,7 +146,9 @@ static int oz_launch_gemm(const OzWork& w, int M, int N, int Kp, Dst dst, Status
     static std::atomic<unsigned long long> attr{0};
     const size_t bytesB = (size_t)Kp * OZ_NT * 16, bytesA = (size_t)Kp * 256;
     const size_t smem = bytesB + (bytesB + 2 * bytesA <= kOzSmemCap ? 2 : 1) * bytesA;
-    if (once_per_device(attr)) KLST_CK(cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap));
+    KLST_CK(set_once_per_device(attr, [] {
+        return cudaFuncSetAttribute(k_oz_gemm<Dst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemCap);
+    }));
     dim3 grid((N + OZ_NT - 1) / OZ_NT, (M + 127) / 128);
     k_oz_gemm<Dst><<<grid, 128, smem, s>>>(w.A, w.B, w.ea, w.eb, Kp, dst, st, skip, cols_per_flag, N, 0);
     note_launch();

@@ -21,6 +21,11 @@ static std::atomic<unsigned long long> g_launches{0};
 // the graph is launched (note_launches with the graph's kernel-node count).
 static thread_local bool t_capturing = false;
 void set_capturing(bool on) { t_capturing = on; }
+std::mutex& attr_mutex() {
+    static std::mutex m;
+    return m;
+}
+
 void note_launch() {
     if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
 }

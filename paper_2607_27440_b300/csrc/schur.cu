@@ -526,10 +526,11 @@ __global__ void __launch_bounds__(256) k_schur_post(SchurArgs a) {
 
 int launch_schur(const SchurArgs& a, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
-    if (once_per_device(attr)) {
-        KLST_CK(cudaFuncSetAttribute(k_schur_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-        KLST_CK(cudaFuncSetAttribute(k_schur_q, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    }
+    KLST_CK(set_once_per_device(attr, [] {
+        cudaError_t e = cudaFuncSetAttribute(k_schur_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_schur_q, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        return e;
+    }));
     const int m = a.m;
     const size_t packed = sizeof(double2) * (size_t)m * (m + 3) / 2;
     prof_begin("schur_house", s);

@@ -742,10 +742,11 @@ __global__ void __launch_bounds__(kQThreads) k_schur_defer64(SchurArgs a, int ph
 
 int launch_schur64(const SchurArgs& a, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
-    if (once_per_device(attr)) {
-        KLST_CK(cudaFuncSetAttribute(k_schur_qr64, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-        KLST_CK(cudaFuncSetAttribute(k_schur_reorder64, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-    }
+    KLST_CK(set_once_per_device(attr, [] {
+        cudaError_t e = cudaFuncSetAttribute(k_schur_qr64, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_schur_reorder64, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        return e;
+    }));
     const int m = a.m;
     const size_t packed = sizeof(double2) * (size_t)m * (m + 3) / 2;
     prof_begin("schur_house", s);

@@ -290,10 +290,11 @@ int tc_solve_pass(int pass, klst_factor f, const double2* b, int mask, double2* 
                   cudaStream_t s, const int* done) {
     static std::atomic<unsigned long long> attr{0};
     const size_t smem = tcstream_smem<SolvePolicy<1>>();
-    if (once_per_device(attr)) {
-        KLST_CK(cudaFuncSetAttribute(k_solve_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        KLST_CK(cudaFuncSetAttribute(k_solve_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
+    KLST_CK(set_once_per_device(attr, [&] {
+        cudaError_t e = cudaFuncSetAttribute(k_solve_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_solve_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
+    }));
     klst_pencil p = f->p;
     TcSolveArgs a;
     a.nx = p->nx; a.nxi = p->nxi; a.Kp = tc_kp(p->nx); a.nrhs = nrhs;

@@ -207,3 +207,30 @@ def test_server_and_batch_reject_bad_options(klst):
     with pytest.raises(klst.KlstError) as ei:
         klst.batch_eigs([SMALL[0][0]], [0.1j], 6, 6, precision=0)
     assert ei.value.code == klst.KLST_EINVAL and "invalid eigs options" in str(ei.value)
+
+
+_FRESH_BATCH = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+from paper_2607_27440_b300 import klst, workloads as wl
+klst.load()
+specs = [wl.tiny(nx=128, qx=4 + (i % 3), qy=2, mach=1.2 + 0.3 * i) for i in range(8)]
+sig = [0.05 + 0.2j + 0.01j * i for i in range(8)]
+om, res, st, infos = klst.batch_eigs(specs, sig, 4, 12, precision=klst.FP64, nworkers=8, tol=1e-10)
+print(list(st))
+sys.exit(0 if all(s == 0 for s in st) else 1)
+"""
+
+
+def test_first_use_in_concurrent_workers_is_safe():
+    """A fresh process whose first GPU work is eight Nx = 128 pencils on eight worker threads: the
+    kernels that need more than 48 KB of shared memory get their attribute set before any thread
+    launches them (a set-once flag that a second thread could pass before the first thread had set
+    the attribute made such launches fail with KLST_ECUDA)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _FRESH_BATCH, root], capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, (r.stdout, r.stderr[-2000:])
