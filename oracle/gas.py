@@ -243,8 +243,9 @@ def collision_map(g, h, W, xi_x, xi_y, spec):
     return nu[:, None] * (ge - g), nu[:, None] * (he - h)
 
 
-def pencil_data(spec):
-    """All per-point and per-node tables the pencil is assembled from.
+def pencil_data(spec, base=None):
+    """All per-point and per-node tables the pencil is assembled from (``base``: optional (g_c, h_c)
+    of shape (Nx, Nxi) in node order, used in place of the synthetic base flow).
 
     Returns a dict with x, Dx, xi_x, xi_y, W, gc, hc, gce, hce, rho, u, E, T, P,
     mu, nu, C (fixed, 2x4xNxxNxi), w (moment weights), G (collision coupling
@@ -264,7 +265,10 @@ def pencil_data(spec):
     nx, qx, qy = _p(spec, "nx"), _p(spec, "qx"), _p(spec, "qy")
     x, Dx = grids.mapped_diff(nx, _p(spec, "map_L"), _p(spec, "map_sinf"))
     xi_x, xi_y, W = grids.velocity_grid(qx, qy)
-    gc, hc = base_flow(spec, x, xi_x, xi_y)
+    if base is None:
+        gc, hc = base_flow(spec, x, xi_x, xi_y)
+    else:  # given base distributions at the nodes (e.g. the BE-BGK steady state of Sec. 3.3)
+        gc, hc = (np.array(a, dtype=np.float64) for a in base)
     rho, u, v, E = moments(gc, hc, W, xi_x, xi_y)
     v = np.zeros_like(v)
     cons = _p(spec, "conservative")
