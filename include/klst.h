@@ -140,6 +140,26 @@ typedef struct {
     double max_resid;     /* max ||A x - omega B x|| over the returned pairs, ||x|| = 1 */
 } klst_jd_info;
 
+/* BE-BGK base-flow solver options and report (klst_bgk_base_flow; Sec. 3.3) */
+typedef struct {
+    int32_t max_steps;      /* RK4 steps at most (whole multiples of check_every are taken) */
+    double cfl;             /* dt = cfl min(dx) / max|xi_x|, and at most 2 / max(nu); e.g. 0.5 */
+    double dt;              /* > 0: this fixed time step instead */
+    double tol;             /* stop once max|RHS| <= tol max|g| at a check; 0: run max_steps */
+    int32_t check_every;    /* RK4 steps per residual check (one CUDA graph launch), >= 1 */
+    int32_t recentre_every; /* steps between re-centring checks, a multiple of check_every; 0: off */
+    double recentre_tol;    /* re-centre when the shock has moved more than this from the map centre */
+} klst_bgk_opts;
+typedef struct {
+    int32_t steps;          /* RK4 steps taken */
+    int32_t recentres;      /* grid rebuilds */
+    double resid;           /* max|RHS| / max|g| at the last check */
+    double centre;          /* final map centre: the shock's position in the solve's frame */
+    double dt;              /* time step of the last check interval */
+    double t_ms;            /* wall time */
+    double newton_avg;      /* Newton updates per node and equilibrium evaluation */
+} klst_bgk_info;
+
 typedef struct klst_pencil_s* klst_pencil;
 typedef struct klst_factor_s* klst_factor;
 
@@ -267,6 +287,33 @@ int klst_base_noneq(klst_pencil p, double* eneq_host);
  */
 int klst_eigvec_macro(klst_pencil p, const void* q, int32_t nvec, double* macro_host, double* umax_host,
                       klst_stream stream);
+
+/*
+ * klst_bgk_base_flow -- the steady 1-D shock of the reduced 1D2V BGK equations (Sec. 3.3, Eq.
+ * BoltzmannBGK_reduced) on the pencil's mapped Chebyshev nodes and velocity grid (desc; base, noneq
+ * and width only shape the Mott-Smith start).  dq/dt = nu (q^e - q) - xi_x dq/dx for q = (g, h):
+ * second-order finite volumes with MUSCL reconstruction and the minmod limiter (the paper's form:
+ * plain neighbour differences), relaxation toward the discrete equilibrium of each node's moments
+ * (the one klst_build_pencil linearises), nu = P / mu(T); Dirichlet ends: the upstream Maxwellian and
+ * the Rankine-Hugoniot Maxwellian refined so that its discrete mass, momentum and energy fluxes equal
+ * the upstream ones; classical RK4; optional adaptive re-centring (the interval of largest |dU/dx|
+ * locates the shock; past recentre_tol the nodes are rebuilt about it and g, h moved by linear
+ * interpolation in x).  Starts from a Mott-Smith profile about x = 0.  g_out, h_out: device float64
+ * [Nx][Nxi], node j = 0 at the downstream end (the pencil's order), in the frame centred on the final
+ * map centre (info->centre), ready for klst_build_pencil_base.  Errors: KLST_EINVAL, KLST_ENOMEM,
+ * KLST_ENOCONV (non-finite residual).  Synchronising.
+ */
+int klst_bgk_base_flow(const klst_pencil_desc* desc, const klst_bgk_opts* opts, void* g_out, void* h_out,
+                       klst_bgk_info* info, klst_stream stream);
+
+/*
+ * klst_build_pencil_base -- klst_build_pencil with given base distributions in place of the
+ * synthetic base flow (e.g. the BE-BGK steady state of klst_bgk_base_flow): gc, hc are device float64
+ * [Nx][Nxi] (node j = 0 downstream); with desc->noneq = 0 the pencil uses their discrete equilibrium
+ * instead (EQ).  The caller keeps gc, hc (they are read during the call).  Errors as klst_build_pencil.
+ */
+int klst_build_pencil_base(const klst_pencil_desc* desc, const void* gc, const void* hc, klst_stream stream,
+                           klst_pencil* out);
 
 /*
  * klst_factor_shift -- factor A - sigma B for the shift-and-invert transform

@@ -163,21 +163,25 @@ def initial_state(spec, x, xi_x, xi_y, W):
     return g, h
 
 
-def steady(spec, steps, cfl=0.5, recentre_every=0, recentre_tol=0.25, tol=0.0):
+def steady(spec, steps, cfl=0.5, recentre_every=0, recentre_tol=0.25, tol=0.0, dt=0.0):
     """Integrate from the Mott-Smith start for at most ``steps`` RK4 steps (stopping once
-    max|RHS| <= tol max|g|); returns dict(g, h (pencil order), centre, steps, resid)."""
+    max|RHS| <= tol max|g|; dt > 0: a fixed time step); returns dict(g, h (pencil order), centre,
+    steps, resid, recentres)."""
     xi_x, xi_y, W = grids.velocity_grid(gas._p(spec, "qx"), gas._p(spec, "qy"))
     c = 0.0
     x = grid(spec, c)
     g, h = initial_state(spec, x, xi_x, xi_y, W)
     ends = end_states(spec, xi_x, xi_y, W)
     resid = np.inf
-    n = 0
+    n = recentres = 0
     for n in range(1, steps + 1):
-        rho, u, v, E = gas.moments(g, h, W, xi_x, xi_y)
-        nu = gas.transport(rho, u, np.zeros_like(v), E, spec)[3]
-        dt = time_step(x, xi_x, np.max(nu), cfl)
-        g, h = rk4_step(g, h, dt, x, xi_x, xi_y, W, spec)
+        if dt > 0:
+            step = dt
+        else:
+            rho, u, v, E = gas.moments(g, h, W, xi_x, xi_y)
+            nu = gas.transport(rho, u, np.zeros_like(v), E, spec)[3]
+            step = time_step(x, xi_x, np.max(nu), cfl)
+        g, h = rk4_step(g, h, step, x, xi_x, xi_y, W, spec)
         if recentre_every and n % recentre_every == 0:
             rho, u, v, E = gas.moments(g, h, W, xi_x, xi_y)
             xs = shock_location(u, x)
@@ -185,12 +189,13 @@ def steady(spec, steps, cfl=0.5, recentre_every=0, recentre_tol=0.25, tol=0.0):
                 x_new = grid(spec, xs)
                 g, h = regrid(g, h, x, x_new, ends)
                 x, c = x_new, xs
+                recentres += 1
         if tol > 0:
             rg, rh = rhs(g, h, x, xi_x, xi_y, W, spec)
             resid = max(np.max(np.abs(rg)), np.max(np.abs(rh))) / np.max(np.abs(g))
             if resid <= tol:
                 break
-    return dict(g=to_pencil_order(g), h=to_pencil_order(h), centre=c, steps=n, resid=resid)
+    return dict(g=to_pencil_order(g), h=to_pencil_order(h), centre=c, steps=n, resid=resid, recentres=recentres)
 
 
 def to_pencil_order(a):

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "factor.cuh"
+#include "kinetic.cuh"
 
 namespace klst {
 
@@ -159,66 +160,15 @@ struct BaseParams {
     double rho1, u1, T1, rho2, u2, T2, uinf;
 };
 
-__device__ __forceinline__ double maxw(double rho, double u, double T, double xx, double xy) {
-    double dx = xx - u;
-    return rho / (M_PI * T) * exp(-(dx * dx + xy * xy) / T);
-}
-
-// Block-wide sum of NV doubles per thread; result broadcast to all threads.
-template <int NV>
-__device__ void block_sum(double (&v)[NV], double* sm /* >= 32*NV */) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double a = v[i];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) sm[wid * NV + i] = a;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            double a = lane < nw ? sm[lane * NV + i] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) sm[32 * NV + i] = a;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = sm[32 * NV + i];
-    __syncthreads();
-}
-
-// Solve the small dense system J d = r (n <= 4) by Gaussian elimination with partial pivoting.
-__device__ void small_solve(int n, double* J /* n*n row-major */, double* r) {
-    for (int p = 0; p < n; ++p) {
-        int piv = p;
-        for (int i = p + 1; i < n; ++i)
-            if (fabs(J[i * n + p]) > fabs(J[piv * n + p])) piv = i;
-        if (piv != p) {
-            for (int c = 0; c < n; ++c) { double t = J[p * n + c]; J[p * n + c] = J[piv * n + c]; J[piv * n + c] = t; }
-            double t = r[p]; r[p] = r[piv]; r[piv] = t;
-        }
-        for (int i = p + 1; i < n; ++i) {
-            double f = J[i * n + p] / J[p * n + p];
-            for (int c = p; c < n; ++c) J[i * n + c] -= f * J[p * n + c];
-            r[i] -= f * r[p];
-        }
-    }
-    for (int p = n - 1; p >= 0; --p) {
-        double s = r[p];
-        for (int c = p + 1; c < n; ++c) s -= J[p * n + c] * r[c];
-        r[p] = s / J[p * n + p];
-    }
-}
-
-// One CTA per collocation point j.  Computes the base distributions at the nodes, their
+// One CTA per collocation point j.  Computes the base distributions at the nodes (or takes the
+// given ones), their
 // discrete moments (rho, u, E; v = 0), the discrete equilibrium (Newton on the Maxwellian
 // parameters when conservative), nu = P/mu, the raw equilibrium derivatives C, the moment
 // functionals w, the conservative fix C <- C (M C)^{-1}, and G = nu C + (f^e - f) d.
 __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x, const double* xi_y,
                              const double* W, double* gbuf, double* hbuf, double* nu_out, double* macro,
-                             double* G, double* w, double* eneq, Status* st) {
+                             double* G, double* w, double* eneq, Status* st, const double* user_g,
+                             const double* user_h) {
     __shared__ double sm[32 * 16 + 16];
     __shared__ double s_th[4];
     __shared__ double s_MCinv[16];
@@ -239,7 +189,10 @@ __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x,
     double mom[4] = {0, 0, 0, 0};
     for (int k = threadIdx.x; k < nxi; k += blockDim.x) {
         double xx = xi_x[k], xy = xi_y[k], gk, hk;
-        if (bp.base == KLST_BASE_TANH_MAXWELL) {
+        if (user_g) {  // given base distributions, [j][k]
+            gk = user_g[(size_t)j * nxi + k];
+            hk = user_h[(size_t)j * nxi + k];
+        } else if (bp.base == KLST_BASE_TANH_MAXWELL) {
             gk = maxw(rho_t, u_t, T_t, xx, xy);
             hk = 0.5 * T_t * gk;
         } else {
@@ -450,7 +403,25 @@ extern "C" void klst_pencil_destroy(klst_pencil p) {
     delete p;
 }
 
+static int build_pencil(const klst_pencil_desc* d, const double* user_g, const double* user_h, klst_stream stream,
+                        klst_pencil* out);
+
 extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, klst_pencil* out) {
+    return build_pencil(d, nullptr, nullptr, stream, out);
+}
+
+extern "C" int klst_build_pencil_base(const klst_pencil_desc* d, const void* gc, const void* hc, klst_stream stream,
+                                      klst_pencil* out) {
+    if (!gc || !hc) {
+        if (out) *out = nullptr;
+        set_error("gc and hc must be device arrays of the base distributions");
+        return KLST_EINVAL;
+    }
+    return build_pencil(d, (const double*)gc, (const double*)hc, stream, out);
+}
+
+static int build_pencil(const klst_pencil_desc* d, const double* user_g, const double* user_h, klst_stream stream,
+                        klst_pencil* out) {
     if (!out) { set_error("out is NULL"); return KLST_EINVAL; }
     *out = nullptr;
     if (!d) { set_error("desc is NULL"); return KLST_EINVAL; }
@@ -511,7 +482,7 @@ extern "C" int klst_build_pencil(const klst_pencil_desc* d, klst_stream stream, 
     const double p1 = 0.5, p2 = p1 * (1.0 + 2.0 * g * (M * M - 1.0) / (g + 1.0));
     bp.rho2 = r; bp.u2 = bp.u1 / r; bp.T2 = 2.0 * p2 / bp.rho2;
     k_base_state<<<nx, 256, 0, s>>>(bp, p->x, p->xi_x, p->xi_y, p->W, gbuf, gbuf + (size_t)nx * nxi, p->nu,
-                                    p->macro, p->G, p->w, p->eneq, p->status); klst::note_launch();
+                                    p->macro, p->G, p->w, p->eneq, p->status, user_g, user_h); klst::note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "pencil kernels", __FILE__, __LINE__));
     // D_x as integer slices for the float64-accurate tensor-core D_x products of the operator
     {

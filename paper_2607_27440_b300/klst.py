@@ -61,6 +61,19 @@ class JdInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BgkOpts(ctypes.Structure):
+    _fields_ = [("max_steps", c_int32), ("cfl", c_double), ("dt", c_double), ("tol", c_double),
+                ("check_every", c_int32), ("recentre_every", c_int32), ("recentre_tol", c_double)]
+
+
+class BgkInfo(ctypes.Structure):
+    _fields_ = [("steps", c_int32), ("recentres", c_int32), ("resid", c_double), ("centre", c_double),
+                ("dt", c_double), ("t_ms", c_double), ("newton_avg", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class KlstError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} [{code}]")
@@ -78,6 +91,10 @@ EXPORTS = {
     "klst_prof_entry": (c_int32, [c_int32, ctypes.c_char_p, c_int32, ctypes.POINTER(c_double),
                                   ctypes.POINTER(c_int64)]),
     "klst_build_pencil": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, ctypes.POINTER(c_void_p)]),
+    "klst_build_pencil_base": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, c_void_p, c_void_p,
+                                         ctypes.POINTER(c_void_p)]),
+    "klst_bgk_base_flow": (c_int32, [ctypes.POINTER(PencilDesc), ctypes.POINTER(BgkOpts), c_void_p, c_void_p,
+                                     ctypes.POINTER(BgkInfo), c_void_p]),
     "klst_pencil_destroy": (None, [c_void_p]),
     "klst_pencil_dims": (c_int32, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int32),
                                    ctypes.POINTER(c_int32), ctypes.POINTER(c_int64)]),
@@ -219,13 +236,26 @@ def _check_out(out, x, name="out"):
 class Pencil:
     """Device-resident kLST pencil (klst_build_pencil)."""
 
-    def __init__(self, spec, stream=None):
+    def __init__(self, spec, stream=None, base=None):
+        """``base``: optional (g_c, h_c) float64 CUDA tensors of shape (Nx, Nxi) in node order (e.g. from
+        bgk_base_flow), used in place of the synthetic base flow (klst_build_pencil_base)."""
         lib = load()
-        _torch()
+        torch = _torch()
         self.spec = spec
         self._desc = make_desc(spec)
         h = c_void_p()
-        _check(lib.klst_build_pencil(ctypes.byref(self._desc), _stream(stream), ctypes.byref(h)))
+        if base is None:
+            _check(lib.klst_build_pencil(ctypes.byref(self._desc), _stream(stream), ctypes.byref(h)))
+        else:
+            shape = (spec.nx, spec.nxi)
+            gb = []
+            for a in base:
+                if (not isinstance(a, torch.Tensor) or a.dtype != torch.float64 or a.device.type != "cuda"
+                        or tuple(a.shape) != shape):
+                    raise ValueError(f"base arrays must be float64 CUDA tensors of shape {shape}")
+                gb.append(a.contiguous())
+            _check(lib.klst_build_pencil_base(ctypes.byref(self._desc), _ptr(gb[0]), _ptr(gb[1]), _stream(stream),
+                                              ctypes.byref(h)))
         self.handle = h
         n, nx, nxi, fp = c_int64(), c_int32(), c_int32(), c_int64()
         _check(lib.klst_pencil_dims(h, ctypes.byref(n), ctypes.byref(nx), ctypes.byref(nxi), ctypes.byref(fp)))
@@ -412,6 +442,23 @@ class Factor:
         d = info.as_dict()
         d["status"] = code
         return (ev[0:2 * k:2] + 1j * ev[1:2 * k:2], vec[:k] if vec is not None else None, res[:k], d)
+
+
+def bgk_base_flow(spec, max_steps=20000, cfl=0.5, dt=0.0, tol=0.0, check_every=100, recentre_every=0,
+                  recentre_tol=0.25, stream=None):
+    """klst_bgk_base_flow: the BE-BGK steady shock on the pencil's grid; returns (g, h, info) with g, h
+    float64 CUDA tensors of shape (Nx, Nxi) in node order (j = 0 downstream)."""
+    lib = load()
+    torch = _torch()
+    d = make_desc(spec)
+    g = torch.empty((spec.nx, spec.nxi), dtype=torch.float64, device="cuda")
+    h = torch.empty_like(g)
+    o = BgkOpts(max_steps=max_steps, cfl=cfl, dt=dt, tol=tol, check_every=check_every,
+                recentre_every=recentre_every, recentre_tol=recentre_tol)
+    info = BgkInfo()
+    _check(lib.klst_bgk_base_flow(ctypes.byref(d), ctypes.byref(o), _ptr(g), _ptr(h), ctypes.byref(info),
+                                  _stream(stream)))
+    return g, h, info.as_dict()
 
 
 def _opts(nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, seed=0, conv=CONV_REL, keep=0,
