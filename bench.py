@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the serving run")
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 latency figures")
     ap.add_argument("--no-jd", action="store_true", help="skip the Jacobi-Davidson leg")
+    ap.add_argument("--no-base-flow", action="store_true", help="skip the BE-BGK base-flow leg")
     ap.add_argument("--max-restarts", type=int, default=None,
                     help="cap the eigensolve's restarts (bounded runs for profiling; the line is then not a bench value)")
     ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
@@ -529,6 +530,11 @@ def run_ours(args):
         "peaks_source": src,
         "fp64_peak_tflops": {"value": fp64_peak, "source": fp64_src},
     }
+    if not args.no_base_flow:
+        try:
+            line["base_flow"] = base_flow_leg(klst)
+        except Exception as ex:  # the headline line must still print
+            line["base_flow"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_jd:
         try:
             line["jacobi_davidson"] = jd_leg(klst, spec, sigma, v0)
@@ -555,6 +561,44 @@ def run_ours(args):
     print(json.dumps(line, default=_jsonable), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def base_flow_leg(klst):
+    """NEXT-2, the BE-BGK base-flow solver (klst_bgk_base_flow): RK4 throughput on the C3 shape
+    (Nx = 128, 61 x 18 nodes, M = 4; 4,000 steps from the Mott-Smith start), and C2 end to end: the
+    steady BGK shock (t = 100 shock thicknesses), a pencil on it, and 20 eigenpairs near 0.1i."""
+    import torch
+    from paper_2607_27440_b300 import workloads as wl
+    out = {}
+    spec3 = wl.c3()[0]
+    klst.bgk_base_flow(spec3, max_steps=500, cfl=0.5, check_every=500)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, h, info = klst.bgk_base_flow(spec3, max_steps=4000, cfl=0.5, check_every=500)
+    torch.cuda.synchronize()
+    s3 = time.perf_counter() - t0
+    out["c3_shape"] = {"steps": info["steps"], "s": s3, "rk4_steps_per_s": info["steps"] / s3,
+                       "rhs_evals_per_s": 4 * info["steps"] / s3,
+                       "unknown_updates_per_s": 4 * info["steps"] * spec3.n / s3, "dt": info["dt"],
+                       "newton_per_equilibrium": info["newton_avg"], "resid_after": info["resid"]}
+    spec2, es2 = wl.c2()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, h, info = klst.bgk_base_flow(spec2, max_steps=16000, cfl=0.5, check_every=500, recentre_every=4000,
+                                    recentre_tol=0.5)
+    torch.cuda.synchronize()
+    t_bgk = time.perf_counter() - t0
+    P = klst.Pencil(spec2, base=(g, h))
+    F = P.factor(es2.sigma, precision=klst.FP64)
+    t1 = time.perf_counter()
+    om, _, res, inf = F.eigs(20, 60, tol=CONV_TOL, conv=klst.CONV_RESID, check=False)
+    t_eigs = time.perf_counter() - t1
+    good = int(np.sum(res <= RESID_MAX)) if inf["status"] in RETURNED else 0
+    out["c2_end_to_end"] = {"bgk_steps": info["steps"], "bgk_s": t_bgk, "bgk_resid": info["resid"],
+                            "recentres": info["recentres"], "centre": info["centre"], "eigs_s": t_eigs,
+                            "good_eigenpairs": good, "max_resid": float(np.max(res)) if len(res) else None,
+                            "base_noneq_max": float(np.max(P.base_noneq()))}
+    return out
 
 
 JD_NEV = 10
