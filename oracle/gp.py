@@ -1,0 +1,102 @@
+"""Gilbarg-Paolucci continuum shock structure (oracle; test infrastructure only): Sec. 2.1, Eq.
+GB1DShockeqn, and the shock thickness of Eq. ShockThickness.
+
+The printed pair is garbled (its dtheta/dOmega carries 8/15, which its own z-equations give as 2/5,
+and beta, delta are not defined), so the equations are restated from the steady one-dimensional
+Navier-Stokes balances they come from, for a monatomic gas in the kLST units (R = 1/2,
+rho_inf = T_inf = 1, u_inf = M sqrt(gamma/2), c_v = 3R/2, c_p = 5R/2):
+    mass         rho u = m
+    momentum     (4/3) mu(T) du/dx = m u + m R T / u - P
+    energy       (c_p / Pr) mu(T) dT/dx = m c_v T - m u^2 / 2 + P u - m H
+with P = p_inf + m u_inf and H = c_p T_inf + u_inf^2 / 2 (the paper's m, P, E), mu = (u_inf / Re) T^s.
+In the paper's variables Omega = (m/P) u, theta = (m/P)^2 R T, alpha = 2 H m^2 / P^2 - 1 the ratio of
+the two is  dtheta/dOmega = (4/5) Pr Omega (theta - [(1 - Omega)^2 + alpha] / 3) / (Omega^2 - Omega + theta),
+the printed relation's form (its 8/15 is Pr = 2/3).  Pr = 1 (the BGK model's Prandtl number) is the
+reading taken: with it the thickness Delta = (u_inf - u_2) / max|du/dx| of the computed profile
+reproduces Table 1DShockThickness's Re_Delta (test_oracle_gp.py).
+
+The profile is integrated from the downstream Rankine-Hugoniot state (a saddle of the system)
+toward the upstream one, along the saddle's stable direction followed backward in x.
+"""
+import numpy as np
+from scipy.integrate import solve_ivp
+from scipy.optimize import minimize_scalar
+
+from . import gas
+
+
+def constants(M, gamma=5.0 / 3.0):
+    """(m, P, H, (rho1, u1, T1), (rho2, u2, T2)) of the shock in the kLST units."""
+    r1, u1, T1 = gas.upstream_state(M, gamma)
+    st2 = gas.rankine_hugoniot(M, gamma)
+    m = r1 * u1
+    P = 0.5 * r1 * T1 + m * u1
+    H = 1.25 * T1 + 0.5 * u1 * u1
+    return m, P, H, (r1, u1, T1), st2
+
+
+def rhs(u, T, M, Re, s=0.5, Pr=1.0, gamma=5.0 / 3.0):
+    """(du/dx, dT/dx) of the Navier-Stokes shock balances above."""
+    m, P, H, (r1, u1, T1), _ = constants(M, gamma)
+    mu = (u1 / Re) * T ** s
+    du = (m * u + m * 0.5 * T / u - P) / ((4.0 / 3.0) * mu)
+    dT = (m * 0.75 * T - 0.5 * m * u * u + P * u - m * H) / ((1.25 / Pr) * mu)
+    return du, dT
+
+
+def dtheta_domega(Omega, theta, alpha, Pr=1.0):
+    """The printed dtheta/dOmega relation with its Prandtl-number constant (4/5) Pr."""
+    return 0.8 * Pr * Omega * (theta - ((1.0 - Omega) ** 2 + alpha) / 3.0) / (Omega * Omega - Omega + theta)
+
+
+def profile(M, Re, s=0.5, Pr=1.0, gamma=5.0 / 3.0, span=None, eps=1e-6):
+    """Integrated profile: dict(x, u, T, rho, Delta, x_shock) with x increasing from upstream, x_shock
+    the location of max|du/dx| on the continuous solution (bounded search about the largest sample)."""
+    m, P, H, (r1, u1, T1), (r2, u2, T2) = constants(M, gamma)
+
+    def f(x, y):
+        return list(rhs(y[0], y[1], M, Re, s, Pr, gamma))
+
+    y2 = np.array([u2, T2])
+    J = np.zeros((2, 2))
+    for b in range(2):
+        d = np.zeros(2)
+        d[b] = 1e-7 * max(1.0, abs(y2[b]))
+        J[:, b] = (np.array(f(0, y2 + d)) - np.array(f(0, y2 - d))) / (2 * d[b])
+    w, V = np.linalg.eig(J)
+    v = V[:, int(np.argmin(w.real))].real
+    if v[0] < 0:
+        v = -v
+    if span is None:
+        span = 400.0 / Re
+    sol = solve_ivp(f, [0.0, -span], y2 + eps * u2 * v, rtol=1e-12, atol=1e-14, dense_output=True,
+                    max_step=span / 4000)
+    x, u, T = sol.t[::-1], sol.y[0][::-1], sol.y[1][::-1]
+    du = np.array([rhs(a, b, M, Re, s, Pr, gamma)[0] for a, b in zip(u, T)])
+    i = int(np.argmax(np.abs(du)))
+
+    def slope(xx):  # |du/dx| on the continuous (dense-output) solution
+        y = sol.sol(xx)
+        return abs(rhs(y[0], y[1], M, Re, s, Pr, gamma)[0])
+
+    r = minimize_scalar(lambda xx: -slope(xx), bounds=(x[max(i - 1, 0)], x[min(i + 1, len(x) - 1)]),
+                        method="bounded", options={"xatol": 1e-12 * span})
+    return dict(x=x, u=u, T=T, rho=m / u, Delta=(u1 - u2) / slope(r.x), x_shock=float(r.x), sol=sol)
+
+
+def re_delta(M, s=0.5, Pr=1.0, gamma=5.0 / 3.0):
+    """The self-consistent Re_Delta: the profile's thickness with Re = 1 (x scales as 1/Re)."""
+    return profile(M, 1.0, s, Pr, gamma)["Delta"]
+
+
+def base_at(M, Re, x_nodes, s=0.5, Pr=1.0, gamma=5.0 / 3.0):
+    """(rho, u, T) of the profile at x_nodes measured from the shock (max|du/dx|), the end states
+    beyond the integrated range."""
+    p = profile(M, Re, s, Pr, gamma)
+    xq = np.asarray(x_nodes) + p["x_shock"]
+    (r1, u1, T1), (r2, u2, T2) = constants(M, gamma)[3:]
+    lo, hi = p["x"][0], p["x"][-1]
+    y = p["sol"].sol(np.clip(xq, lo, hi))
+    u = np.where(xq < lo, u1, np.where(xq > hi, u2, y[0]))
+    T = np.where(xq < lo, T1, np.where(xq > hi, T2, y[1]))
+    return constants(M, gamma)[0] / u, u, T
