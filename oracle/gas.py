@@ -77,6 +77,8 @@ def base_flow(spec, x, xi_x, xi_y):
       (mass flux) and T = 2 (P1 + rho1 u1^2 - rho u^2) / rho (momentum flux).
     * base 'mott_smith': g_c = (1 - s) g^e_1 + s g^e_2 and h_c likewise with
       (T_i / 2) g^e_i -- a bimodal, non-equilibrium distribution.
+    * base 'gilbarg_paolucci': local Maxwellian of the continuum shock profile (gp.base_at with
+      Re = re_delta, mu ~ T^visc_s, Pr = 1), max|du/dx| at x = 0; width is not used.
     """
     M, gamma, width = _p(spec, "mach"), _p(spec, "gamma"), _p(spec, "width")
     rho1, u1, T1 = upstream_state(M, gamma)
@@ -95,6 +97,11 @@ def base_flow(spec, x, xi_x, xi_y):
         g2 = maxwellian(rho2 + z, u2 + z, z, T2 + z, xi_x, xi_y)
         gc = (1.0 - s)[:, None] * g1 + s[:, None] * g2
         hc = (1.0 - s)[:, None] * (0.5 * T1) * g1 + s[:, None] * (0.5 * T2) * g2
+    elif _p(spec, "base") == "gilbarg_paolucci":
+        from . import gp   # the continuum profile (Pr = 1, mu ~ T^s, Re = Re_Delta), shock at x = 0
+        rho, u, T = gp.base_at(M, _p(spec, "re_delta"), x, s=_p(spec, "visc_s"), gamma=gamma)
+        gc = maxwellian(rho, u, 0.0 * u, T, xi_x, xi_y)
+        hc = 0.5 * T[:, None] * gc
     else:
         raise ValueError("unknown base flow")
     return gc, hc

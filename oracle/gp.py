@@ -49,26 +49,37 @@ def dtheta_domega(Omega, theta, alpha, Pr=1.0):
     return 0.8 * Pr * Omega * (theta - ((1.0 - Omega) ** 2 + alpha) / 3.0) / (Omega * Omega - Omega + theta)
 
 
+def _jacobian(u, T, M, Re, s, Pr, gamma):
+    """Central-difference Jacobian of rhs at (u, T)."""
+    y = np.array([u, T])
+    J = np.zeros((2, 2))
+    for b in range(2):
+        d = np.zeros(2)
+        d[b] = 1e-7 * max(1.0, abs(y[b]))
+        J[:, b] = (np.array(rhs(*(y + d), M, Re, s, Pr, gamma)) - np.array(rhs(*(y - d), M, Re, s, Pr, gamma))) / (2 * d[b])
+    return J
+
+
 def profile(M, Re, s=0.5, Pr=1.0, gamma=5.0 / 3.0, span=None, eps=1e-6):
-    """Integrated profile: dict(x, u, T, rho, Delta, x_shock) with x increasing from upstream, x_shock
-    the location of max|du/dx| on the continuous solution (bounded search about the largest sample)."""
+    """Integrated profile: dict(x, u, T, rho, Delta, x_shock, lam_s, v, eps) with x increasing from
+    upstream and x = 0 the start point y_2 + eps u_2 v on the saddle's stable direction v (eigenvalue
+    lam_s < 0); x_shock the location of max|du/dx| on the continuous solution (bounded search about
+    the largest sample).  The default span is 60 decay lengths of the slowest end-state eigenvalue,
+    so that the profile has reached the upstream state to rounding at x = -span."""
     m, P, H, (r1, u1, T1), (r2, u2, T2) = constants(M, gamma)
 
     def f(x, y):
         return list(rhs(y[0], y[1], M, Re, s, Pr, gamma))
 
     y2 = np.array([u2, T2])
-    J = np.zeros((2, 2))
-    for b in range(2):
-        d = np.zeros(2)
-        d[b] = 1e-7 * max(1.0, abs(y2[b]))
-        J[:, b] = (np.array(f(0, y2 + d)) - np.array(f(0, y2 - d))) / (2 * d[b])
-    w, V = np.linalg.eig(J)
-    v = V[:, int(np.argmin(w.real))].real
+    w, V = np.linalg.eig(_jacobian(u2, T2, M, Re, s, Pr, gamma))
+    k = int(np.argmin(w.real))
+    lam_s, v = float(w[k].real), V[:, k].real
     if v[0] < 0:
         v = -v
     if span is None:
-        span = 400.0 / Re
+        w1 = np.linalg.eigvals(_jacobian(u1, T1, M, Re, s, Pr, gamma))
+        span = 60.0 / min(abs(lam_s), float(np.min(np.abs(w1))))
     sol = solve_ivp(f, [0.0, -span], y2 + eps * u2 * v, rtol=1e-12, atol=1e-14, dense_output=True,
                     max_step=span / 4000)
     x, u, T = sol.t[::-1], sol.y[0][::-1], sol.y[1][::-1]
@@ -81,7 +92,8 @@ def profile(M, Re, s=0.5, Pr=1.0, gamma=5.0 / 3.0, span=None, eps=1e-6):
 
     r = minimize_scalar(lambda xx: -slope(xx), bounds=(x[max(i - 1, 0)], x[min(i + 1, len(x) - 1)]),
                         method="bounded", options={"xatol": 1e-12 * span})
-    return dict(x=x, u=u, T=T, rho=m / u, Delta=(u1 - u2) / slope(r.x), x_shock=float(r.x), sol=sol)
+    return dict(x=x, u=u, T=T, rho=m / u, Delta=(u1 - u2) / slope(r.x), x_shock=float(r.x), sol=sol,
+                lam_s=lam_s, v=v, eps=eps)
 
 
 def re_delta(M, s=0.5, Pr=1.0, gamma=5.0 / 3.0):
@@ -90,13 +102,15 @@ def re_delta(M, s=0.5, Pr=1.0, gamma=5.0 / 3.0):
 
 
 def base_at(M, Re, x_nodes, s=0.5, Pr=1.0, gamma=5.0 / 3.0):
-    """(rho, u, T) of the profile at x_nodes measured from the shock (max|du/dx|), the end states
-    beyond the integrated range."""
+    """(rho, u, T) of the profile at x_nodes measured from the shock (max|du/dx|).  Past the start
+    point (downstream) the saddle's linear solution y_2 + eps u_2 v exp(lam_s x); past the integrated
+    range (upstream) the upstream state."""
     p = profile(M, Re, s, Pr, gamma)
-    xq = np.asarray(x_nodes) + p["x_shock"]
+    xq = np.asarray(x_nodes, dtype=np.float64) + p["x_shock"]
     (r1, u1, T1), (r2, u2, T2) = constants(M, gamma)[3:]
-    lo, hi = p["x"][0], p["x"][-1]
-    y = p["sol"].sol(np.clip(xq, lo, hi))
-    u = np.where(xq < lo, u1, np.where(xq > hi, u2, y[0]))
-    T = np.where(xq < lo, T1, np.where(xq > hi, T2, y[1]))
+    lo = p["x"][0]
+    y = p["sol"].sol(np.clip(xq, lo, 0.0))
+    tail = p["eps"] * u2 * np.exp(p["lam_s"] * np.maximum(xq, 0.0))
+    u = np.where(xq < lo, u1, np.where(xq > 0.0, u2 + tail * p["v"][0], y[0]))
+    T = np.where(xq < lo, T1, np.where(xq > 0.0, T2 + tail * p["v"][1], y[1]))
     return constants(M, gamma)[0] / u, u, T

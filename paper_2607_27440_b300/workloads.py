@@ -33,7 +33,7 @@ class PencilSpec:
     qy: int
     mach: float
     beta: float = 1.0
-    base: str = "mott_smith"     # 'tanh' (local Maxwellian) or 'mott_smith' (bimodal)
+    base: str = "mott_smith"     # "tanh" (local Maxwellian), "mott_smith" (bimodal), "gilbarg_paolucci"
     noneq: int = 1                # 0: EQ (f_c := f_c^e), 1: NONEQ
     conservative: int = 1         # discrete-conservative equilibrium and coefficients
     width: float = 0.5            # tanh width in shock thicknesses
