@@ -20,7 +20,7 @@ toward the upstream one, along the saddle's stable direction followed backward i
 """
 import numpy as np
 from scipy.integrate import solve_ivp
-from scipy.optimize import minimize_scalar
+from scipy.optimize import brentq, minimize_scalar
 
 from . import gas
 
@@ -49,13 +49,13 @@ def dtheta_domega(Omega, theta, alpha, Pr=1.0):
     return 0.8 * Pr * Omega * (theta - ((1.0 - Omega) ** 2 + alpha) / 3.0) / (Omega * Omega - Omega + theta)
 
 
-def _jacobian(u, T, M, Re, s, Pr, gamma):
+def _jacobian(u, T, M, Re, s, Pr, gamma, rel=1e-7):
     """Central-difference Jacobian of rhs at (u, T)."""
     y = np.array([u, T])
     J = np.zeros((2, 2))
     for b in range(2):
         d = np.zeros(2)
-        d[b] = 1e-7 * max(1.0, abs(y[b]))
+        d[b] = rel * max(1.0, abs(y[b]))
         J[:, b] = (np.array(rhs(*(y + d), M, Re, s, Pr, gamma)) - np.array(rhs(*(y - d), M, Re, s, Pr, gamma))) / (2 * d[b])
     return J
 
@@ -63,8 +63,8 @@ def _jacobian(u, T, M, Re, s, Pr, gamma):
 def profile(M, Re, s=0.5, Pr=1.0, gamma=5.0 / 3.0, span=None, eps=1e-6):
     """Integrated profile: dict(x, u, T, rho, Delta, x_shock, lam_s, v, eps) with x increasing from
     upstream and x = 0 the start point y_2 + eps u_2 v on the saddle's stable direction v (eigenvalue
-    lam_s < 0); x_shock the location of max|du/dx| on the continuous solution (bounded search about
-    the largest sample).  The default span is 60 decay lengths of the slowest end-state eigenvalue,
+    lam_s < 0); x_shock the location of max|du/dx| on the continuous solution: the zero of d^2u/dx^2
+    next to the largest sample (a bounded search for the maximum if it has no sign change there).  The default span is 60 decay lengths of the slowest end-state eigenvalue,
     so that the profile has reached the upstream state to rounding at x = -span."""
     m, P, H, (r1, u1, T1), (r2, u2, T2) = constants(M, gamma)
 
@@ -90,9 +90,18 @@ def profile(M, Re, s=0.5, Pr=1.0, gamma=5.0 / 3.0, span=None, eps=1e-6):
         y = sol.sol(xx)
         return abs(rhs(y[0], y[1], M, Re, s, Pr, gamma)[0])
 
-    r = minimize_scalar(lambda xx: -slope(xx), bounds=(x[max(i - 1, 0)], x[min(i + 1, len(x) - 1)]),
-                        method="bounded", options={"xatol": 1e-12 * span})
-    return dict(x=x, u=u, T=T, rho=m / u, Delta=(u1 - u2) / slope(r.x), x_shock=float(r.x), sol=sol,
+    def curvature(xx):  # d^2u/dx^2 = grad(du/dx) . (du/dx, dT/dx), the gradient by central differences
+        y = sol.sol(xx)
+        gu = _jacobian(y[0], y[1], M, Re, s, Pr, gamma, rel=1e-6)[0]
+        return gu @ np.array(rhs(y[0], y[1], M, Re, s, Pr, gamma))
+
+    a, b = x[max(i - 1, 0)], x[min(i + 1, len(x) - 1)]
+    if curvature(a) * curvature(b) < 0:     # the maximum is where d^2u/dx^2 changes sign
+        xs = brentq(curvature, a, b, xtol=1e-15 * span, rtol=4 * np.finfo(float).eps)
+    else:
+        xs = minimize_scalar(lambda xx: -slope(xx), bounds=(a, b), method="bounded",
+                             options={"xatol": 1e-12 * span}).x
+    return dict(x=x, u=u, T=T, rho=m / u, Delta=(u1 - u2) / slope(xs), x_shock=float(xs), sol=sol,
                 lam_s=lam_s, v=v, eps=eps)
 
 
