@@ -50,7 +50,11 @@ typedef enum {
 } klst_status;
 
 typedef enum { KLST_FP64 = 0, KLST_MIXED = 1, KLST_DF64 = 2 } klst_precision;
-typedef enum { KLST_BASE_TANH_MAXWELL = 0, KLST_BASE_MOTT_SMITH = 1 } klst_base;
+/* Synthetic base flows of klst_build_pencil: a tanh-profile local Maxwellian, the bimodal Mott-Smith
+ * mixture of the two end-state Maxwellians, or the local Maxwellian of the Gilbarg-Paolucci
+ * continuum shock profile (klst_gp_shock with Re = re_delta, s = visc_s, Pr = 1; gamma must be 5/3;
+ * width is not used), each with its steepest point at x = 0. */
+typedef enum { KLST_BASE_TANH_MAXWELL = 0, KLST_BASE_MOTT_SMITH = 1, KLST_BASE_GILBARG_PAOLUCCI = 2 } klst_base;
 
 /* Pencil description (all nondimensional: T by T_inf, rho by rho_inf, velocity by
  * sqrt(2 R T_inf), length by the shock thickness; Sec. 2.2). */
@@ -159,6 +163,27 @@ typedef struct {
     double t_ms;            /* wall time */
     double newton_avg;      /* Newton updates per node and equilibrium evaluation */
 } klst_bgk_info;
+
+/* Gilbarg-Paolucci continuum shock (klst_gp_shock; Sec. 2.1, Eqs. GB1DShockeqn, ShockThickness) */
+typedef struct {
+    double mach;            /* free-stream Mach number, 1.01..100 (monatomic: gamma = 5/3) */
+    double re;              /* Reynolds number of the length unit: mu = (u_inf / re) T^visc_s */
+    double visc_s;          /* viscosity exponent s, 0..2 */
+    double prandtl;         /* Prandtl number (1 for the BGK model), 0 < Pr <= 10 */
+} klst_gp_case;
+typedef struct {
+    double step;            /* RK4 step times the largest end-state eigenvalue modulus (0: 0.02) */
+    double eps;             /* start offset from the downstream state, relative to u_2 (0: 1e-6) */
+    int32_t max_steps;      /* RK4 steps per case at most (0: 2^20) */
+} klst_gp_opts;
+typedef struct {
+    double delta;           /* thickness (u_inf - u_2) / max|du/dx| in the length unit (= Re_Delta at re = 1) */
+    double x_shock;         /* the steepest point, measured from the start point (x < 0: upstream) */
+    double x_up;            /* where the upstream state was reached, from the start point */
+    double lambda_s;        /* the saddle's stable eigenvalue (< 0) */
+    int32_t steps;          /* RK4 steps taken */
+    int32_t status;         /* KLST_OK or KLST_ENOCONV (max_steps reached first) */
+} klst_gp_result;
 
 typedef struct klst_pencil_s* klst_pencil;
 typedef struct klst_factor_s* klst_factor;
@@ -314,6 +339,26 @@ int klst_bgk_base_flow(const klst_pencil_desc* desc, const klst_bgk_opts* opts, 
  */
 int klst_build_pencil_base(const klst_pencil_desc* desc, const void* gc, const void* hc, klst_stream stream,
                            klst_pencil* out);
+
+/*
+ * klst_gp_shock -- the Gilbarg-Paolucci continuum shock structure (Sec. 2.1, Eq. GB1DShockeqn) and
+ * its thickness (Eq. ShockThickness) for a batch of cases, one device thread per case.  The printed
+ * pair is restated from the steady 1-D Navier-Stokes balances it comes from (monatomic gas, R = 1/2,
+ * rho_inf = T_inf = 1, u_inf = M sqrt(5/6)):
+ *     (4/3) mu du/dx = m u + m T/(2u) - P,   (5/4)(mu/Pr) dT/dx = (3/4) m T - m u^2/2 + P u - m H
+ * (m, P, H the fluxes of mass, momentum and enthalpy; their ratio in the paper's Omega, theta is the
+ * printed dtheta/dOmega with the constant (4/5) Pr).  Classical RK4 with a fixed step from the
+ * downstream Rankine-Hugoniot state displaced by eps u_2 along the saddle's stable eigenvector,
+ * backward in x until the upstream state is reached to 1e-13; the steepest point is the sign change
+ * of d^2u/dx^2 next to the largest sampled |du/dx|.  With re = 1, delta is the self-consistent
+ * Re_Delta.  cases (host, ncases >= 0), opts (host; NULL: defaults), x (host float64[npts]: points
+ * measured from the steepest point, any order), profile (device float64 [3][ncases][npts]: rho, u, T
+ * at the points; past the start point the saddle's linear solution, past x_up the upstream state;
+ * may be NULL when npts = 0), results (host, ncases).  Errors: KLST_EINVAL (a case or option out of
+ * range), KLST_ENOCONV (a case's status; all results are written), KLST_ENOMEM.  Synchronising.
+ */
+int klst_gp_shock(const klst_gp_case* cases, int32_t ncases, const klst_gp_opts* opts, const double* x,
+                  int32_t npts, void* profile, klst_gp_result* results, klst_stream stream);
 
 /*
  * klst_factor_shift -- factor A - sigma B for the shift-and-invert transform

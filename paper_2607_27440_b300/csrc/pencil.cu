@@ -168,7 +168,7 @@ struct BaseParams {
 __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x, const double* xi_y,
                              const double* W, double* gbuf, double* hbuf, double* nu_out, double* macro,
                              double* G, double* w, double* eneq, Status* st, const double* user_g,
-                             const double* user_h) {
+                             const double* user_h, const double* gp) {
     __shared__ double sm[32 * 16 + 16];
     __shared__ double s_th[4];
     __shared__ double s_MCinv[16];
@@ -184,6 +184,8 @@ __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x,
         rho_t = bp.rho1 * bp.u1 / u_t;
         double P1 = 0.5 * bp.rho1 * bp.T1;
         T_t = 2.0 * (P1 + bp.rho1 * bp.u1 * bp.u1 - rho_t * u_t * u_t) / rho_t;
+    } else if (bp.base == KLST_BASE_GILBARG_PAOLUCCI) {   // the continuum profile at the nodes
+        rho_t = gp[j]; u_t = gp[nx + j]; T_t = gp[2 * nx + j];
     }
     // base distributions and their moments
     double mom[4] = {0, 0, 0, 0};
@@ -192,7 +194,7 @@ __global__ void k_base_state(BaseParams bp, const double* x, const double* xi_x,
         if (user_g) {  // given base distributions, [j][k]
             gk = user_g[(size_t)j * nxi + k];
             hk = user_h[(size_t)j * nxi + k];
-        } else if (bp.base == KLST_BASE_TANH_MAXWELL) {
+        } else if (bp.base == KLST_BASE_TANH_MAXWELL || bp.base == KLST_BASE_GILBARG_PAOLUCCI) {
             gk = maxw(rho_t, u_t, T_t, xx, xy);
             hk = 0.5 * T_t * gk;
         } else {
@@ -429,9 +431,15 @@ static int build_pencil(const klst_pencil_desc* d, const double* user_g, const d
         set_error("unsupported sizes nx=%d qx=%d qy=%d (4<=nx<=128, 1<=q<=256)", d->nx, d->qx, d->qy);
         return KLST_EINVAL;
     }
-    if (!(d->mach > 1.0) || !(d->gamma > 1.0) || !(d->re_delta > 0) || !(d->width > 0) || !(d->map_L > 0) ||
-        !(d->map_sinf > 0) || (d->base != KLST_BASE_TANH_MAXWELL && d->base != KLST_BASE_MOTT_SMITH)) {
+    if (!(d->mach > 1.0) || !(d->gamma > 1.0) || !(d->re_delta > 0) || !(d->map_L > 0) || !(d->map_sinf > 0) ||
+        (d->base != KLST_BASE_TANH_MAXWELL && d->base != KLST_BASE_MOTT_SMITH && d->base != KLST_BASE_GILBARG_PAOLUCCI) ||
+        (d->base != KLST_BASE_GILBARG_PAOLUCCI && !(d->width > 0))) {
         set_error("invalid physical parameters");
+        return KLST_EINVAL;
+    }
+    klst_gp_case gpc = {d->mach, d->re_delta, d->visc_s, 1.0};
+    if (d->base == KLST_BASE_GILBARG_PAOLUCCI && !user_g && (fabs(d->gamma - 5.0 / 3.0) > 1e-12 || !gp_case_valid(gpc))) {
+        set_error("the Gilbarg-Paolucci base needs gamma = 5/3, 1.01 <= mach <= 100 and 0 <= visc_s <= 2");
         return KLST_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -481,8 +489,27 @@ static int build_pencil(const klst_pencil_desc* d, const double* user_g, const d
     const double r = (g + 1.0) * M * M / ((g - 1.0) * M * M + 2.0);
     const double p1 = 0.5, p2 = p1 * (1.0 + 2.0 * g * (M * M - 1.0) / (g + 1.0));
     bp.rho2 = r; bp.u2 = bp.u1 / r; bp.T2 = 2.0 * p2 / bp.rho2;
+    double* gp = nullptr;   // the Gilbarg-Paolucci profile at the nodes: rho, u, T, then the case and its result
+    if (d->base == KLST_BASE_GILBARG_PAOLUCCI && !user_g) {
+        const size_t words = 3 * (size_t)nx + 8 + 8;
+        if ((e = dmalloc((void**)&gp, sizeof(double) * words, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+        klst_gp_case* dc = (klst_gp_case*)(gp + 3 * nx);
+        klst_gp_result* dr = (klst_gp_result*)(gp + 3 * nx + 8);
+        int rc = KLST_OK;
+        if ((e = cudaMemcpyAsync(dc, &gpc, sizeof(gpc), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+        // the nodes are in decreasing x (node 0 downstream): the order the integration visits them
+        if (!rc) rc = gp_shock_device(dc, 1, 0.02, 1e-6, 1 << 20, p->x, nullptr, nx, gp, dr, s);
+        klst_gp_result r;
+        if (!rc && (e = cudaMemcpyAsync(&r, dr, sizeof(r), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+        if (!rc && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e, "gp sync", __FILE__, __LINE__);
+        if (!rc && r.status != KLST_OK) { set_error("Gilbarg-Paolucci profile did not reach the upstream state"); rc = KLST_ENOCONV; }
+        if (rc) { dfree(gp, s); return fail(rc); }
+    }
     k_base_state<<<nx, 256, 0, s>>>(bp, p->x, p->xi_x, p->xi_y, p->W, gbuf, gbuf + (size_t)nx * nxi, p->nu,
-                                    p->macro, p->G, p->w, p->eneq, p->status, user_g, user_h); klst::note_launch();
+                                    p->macro, p->G, p->w, p->eneq, p->status, user_g, user_h, gp); klst::note_launch();
+    if (gp) dfree(gp, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "pencil kernels", __FILE__, __LINE__));
     // D_x as integer slices for the float64-accurate tensor-core D_x products of the operator
     {

@@ -18,7 +18,7 @@ FP64, MIXED, DF64 = 0, 1, 2
 CONV_REL, CONV_RESID = 0, 1
 ARITH_F64, ARITH_DF64 = 0, 1
 JD_PREC_FULL, JD_PREC_BLOCK = 0, 1
-BASES = {"tanh": 0, "mott_smith": 1}
+BASES = {"tanh": 0, "mott_smith": 1, "gilbarg_paolucci": 2}
 
 
 class PencilDesc(ctypes.Structure):
@@ -74,6 +74,19 @@ class BgkInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GpCase(ctypes.Structure):
+    _fields_ = [("mach", c_double), ("re", c_double), ("visc_s", c_double), ("prandtl", c_double)]
+
+
+class GpOpts(ctypes.Structure):
+    _fields_ = [("step", c_double), ("eps", c_double), ("max_steps", c_int32)]
+
+
+class GpResult(ctypes.Structure):
+    _fields_ = [("delta", c_double), ("x_shock", c_double), ("x_up", c_double), ("lambda_s", c_double),
+                ("steps", c_int32), ("status", c_int32)]
+
+
 class KlstError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} [{code}]")
@@ -93,6 +106,8 @@ EXPORTS = {
     "klst_build_pencil": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, ctypes.POINTER(c_void_p)]),
     "klst_build_pencil_base": (c_int32, [ctypes.POINTER(PencilDesc), c_void_p, c_void_p, c_void_p,
                                          ctypes.POINTER(c_void_p)]),
+    "klst_gp_shock": (c_int32, [c_void_p, c_int32, ctypes.POINTER(GpOpts), ctypes.POINTER(c_double), c_int32,
+                                c_void_p, c_void_p, c_void_p]),
     "klst_bgk_base_flow": (c_int32, [ctypes.POINTER(PencilDesc), ctypes.POINTER(BgkOpts), c_void_p, c_void_p,
                                      ctypes.POINTER(BgkInfo), c_void_p]),
     "klst_pencil_destroy": (None, [c_void_p]),
@@ -459,6 +474,28 @@ def bgk_base_flow(spec, max_steps=20000, cfl=0.5, dt=0.0, tol=0.0, check_every=1
     _check(lib.klst_bgk_base_flow(ctypes.byref(d), ctypes.byref(o), _ptr(g), _ptr(h), ctypes.byref(info),
                                   _stream(stream)))
     return g, h, info.as_dict()
+
+
+def gp_shock(mach, re=1.0, visc_s=0.5, prandtl=1.0, x=None, step=0.0, eps=0.0, max_steps=0, stream=None):
+    """klst_gp_shock over a batch of cases (mach, re, visc_s, prandtl broadcast to one length).
+    Returns (res, prof): res a dict of numpy arrays (delta, x_shock, x_up, lambda_s, steps, status) and
+    prof a float64 CUDA tensor (3, ncases, len(x)) of rho, u, T at the points x (measured from the
+    steepest point), or None without x.  With re = 1, res["delta"] is the self-consistent Re_Delta."""
+    lib = load()
+    torch = _torch()
+    cols = np.broadcast_arrays(*[np.atleast_1d(np.asarray(v, dtype=np.float64)) for v in (mach, re, visc_s, prandtl)])
+    n = cols[0].size
+    cases = (GpCase * n)(*[GpCase(*(float(c.flat[i]) for c in cols)) for i in range(n)])
+    res = (GpResult * n)()
+    xs = None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    npts = 0 if xs is None else xs.size
+    prof = torch.empty((3, n, npts), dtype=torch.float64, device="cuda") if npts else None
+    o = GpOpts(step=step, eps=eps, max_steps=max_steps)
+    _check(lib.klst_gp_shock(cases, n, ctypes.byref(o),
+                             None if xs is None else xs.ctypes.data_as(ctypes.POINTER(c_double)), npts,
+                             _ptr(prof) if prof is not None else None, res, _stream(stream)))
+    out = {k: np.array([getattr(r, k) for r in res]) for k, _ in GpResult._fields_}
+    return out, prof
 
 
 def _opts(nev, ncv, tol=1e-12, max_restarts=200, max_refine=4, refine_tol=1e-12, seed=0, conv=CONV_REL, keep=0,
