@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 latency figures")
     ap.add_argument("--no-jd", action="store_true", help="skip the Jacobi-Davidson leg")
     ap.add_argument("--no-base-flow", action="store_true", help="skip the BE-BGK base-flow leg")
+    ap.add_argument("--no-gp", action="store_true", help="skip the Gilbarg-Paolucci continuum-shock leg")
     ap.add_argument("--max-restarts", type=int, default=None,
                     help="cap the eigensolve's restarts (bounded runs for profiling; the line is then not a bench value)")
     ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
@@ -535,6 +536,13 @@ def run_ours(args):
             line["base_flow"] = base_flow_leg(klst)
         except Exception as ex:  # the headline line must still print
             line["base_flow"] = {"error": f"{type(ex).__name__}: {ex}"}
+    if not args.no_gp:
+        try:
+            line["continuum_shock"] = continuum_shock_leg(klst)
+            if not args.no_cpu:
+                line["continuum_shock"]["cpu_baseline"] = cpu_baseline_gp()
+        except Exception as ex:  # the headline line must still print
+            line["continuum_shock"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_jd:
         try:
             line["jacobi_davidson"] = jd_leg(klst, spec, sigma, v0)
@@ -566,7 +574,8 @@ def run_ours(args):
 def base_flow_leg(klst):
     """NEXT-2, the BE-BGK base-flow solver (klst_bgk_base_flow): RK4 throughput on the C3 shape
     (Nx = 128, 61 x 18 nodes, M = 4; 4,000 steps from the Mott-Smith start), and C2 end to end: the
-    steady BGK shock (t = 100 shock thicknesses), a pencil on it, and 20 eigenpairs near 0.1i."""
+    steady BGK shock (t = 100 shock thicknesses), a pencil on it, and 20 eigenpairs near 0.1i; and
+    the RK4 steps that the Mott-Smith and the Gilbarg-Paolucci starts take to a residual of 1e-4."""
     import torch
     from paper_2607_27440_b300 import workloads as wl
     out = {}
@@ -598,7 +607,61 @@ def base_flow_leg(klst):
                             "recentres": info["recentres"], "centre": info["centre"], "eigs_s": t_eigs,
                             "good_eigenpairs": good, "max_resid": float(np.max(res)) if len(res) else None,
                             "base_noneq_max": float(np.max(P.base_noneq()))}
+    # the two starts: RK4 steps (in checks of 500) until max|RHS| <= 1e-4 max|g| on the C2 grid
+    starts = {}
+    for start in ("mott_smith", "gilbarg_paolucci"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, inf2 = klst.bgk_base_flow(spec2, max_steps=16000, cfl=0.5, tol=1e-4, check_every=500, start=start)
+        torch.cuda.synchronize()
+        starts[start] = {"steps": inf2["steps"], "s": time.perf_counter() - t0, "resid": inf2["resid"]}
+    out["c2_steps_to_resid_1e-4"] = starts
     return out
+
+
+GP_CASES = 8192
+
+
+def continuum_shock_leg(klst):
+    """NEXT-4, the Gilbarg-Paolucci continuum shock (klst_gp_shock): GP_CASES cases in one launch
+    (M uniform in 1.1..10, mu ~ T^s with s uniform in 0.5..1, Pr = 1, Re = 1, so that each thickness
+    is the self-consistent Re_Delta), one thread per case; then the three table shocks with their
+    profiles at 128 points.  Wall time of the synchronising call (host copies of the cases and
+    results included), after one untimed call."""
+    import torch
+    rng = np.random.default_rng(2026)
+    M = rng.uniform(1.1, 10.0, GP_CASES)
+    s = rng.uniform(0.5, 1.0, GP_CASES)
+    klst.gp_shock(M[:256], 1.0, s[:256], 1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, _ = klst.gp_shock(M, 1.0, s, 1.0)
+    t = time.perf_counter() - t0
+    x = np.linspace(-5.0, 5.0, 128)
+    Ms = [1.2, 3.0, 4.0]
+    t1 = time.perf_counter()
+    tab, prof = klst.gp_shock(Ms, 1.0, 0.5, 1.0, x=x)
+    t_tab = time.perf_counter() - t1
+    return {"cases": GP_CASES, "s": t, "cases_per_s": GP_CASES / t,
+            "rk4_steps_per_s": float(np.sum(res["steps"])) / t, "steps_per_case_mean": float(np.mean(res["steps"])),
+            "steps_per_case_max": int(np.max(res["steps"])),
+            "table_re_delta": {str(m): float(d) for m, d in zip(Ms, tab["delta"])},
+            "table_with_profiles_s": t_tab}
+
+
+def cpu_baseline_gp(n=8):
+    """The oracle's adaptive integration (scipy, one thread) of the first n cases of the
+    continuum-shock leg, in cases/s."""
+    from oracle import gp
+    rng = np.random.default_rng(2026)
+    M = rng.uniform(1.1, 10.0, GP_CASES)[:n]
+    s = rng.uniform(0.5, 1.0, GP_CASES)[:n]
+    t0 = time.perf_counter()
+    for m, e in zip(M, s):
+        gp.profile(m, 1.0, s=e)
+    t = time.perf_counter() - t0
+    return {"value": n / t, "unit": "cases/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} of the leg's {GP_CASES} cases (scipy solve_ivp, rtol 1e-12)"}
 
 
 JD_NEV = 10

@@ -153,6 +153,8 @@ typedef struct {
     int32_t check_every;    /* RK4 steps per residual check (one CUDA graph launch), >= 1 */
     int32_t recentre_every; /* steps between re-centring checks, a multiple of check_every; 0: off */
     double recentre_tol;    /* re-centre when the shock has moved more than this from the map centre */
+    int32_t start;          /* 0: Mott-Smith profile (desc->width); 1: local Maxwellian of the
+                               Gilbarg-Paolucci profile (Re = re_delta, s = visc_s, Pr = 1; gamma 5/3) */
 } klst_bgk_opts;
 typedef struct {
     int32_t steps;          /* RK4 steps taken */
@@ -323,10 +325,12 @@ int klst_eigvec_macro(klst_pencil p, const void* q, int32_t nvec, double* macro_
  * the Rankine-Hugoniot Maxwellian refined so that its discrete mass, momentum and energy fluxes equal
  * the upstream ones; classical RK4; optional adaptive re-centring (the interval of largest |dU/dx|
  * locates the shock; past recentre_tol the nodes are rebuilt about it and g, h moved by linear
- * interpolation in x).  Starts from a Mott-Smith profile about x = 0.  g_out, h_out: device float64
- * [Nx][Nxi], node j = 0 at the downstream end (the pencil's order), in the frame centred on the final
- * map centre (info->centre), ready for klst_build_pencil_base.  Errors: KLST_EINVAL, KLST_ENOMEM,
- * KLST_ENOCONV (non-finite residual).  Synchronising.
+ * interpolation in x).  Starts from a Mott-Smith profile about x = 0 or (opts->start = 1) from the
+ * Gilbarg-Paolucci profile with its steepest point at x = 0 (klst_gp_shock).  g_out, h_out: device
+ * float64 [Nx][Nxi], node j = 0 at the downstream end (the pencil's order), in the frame centred on
+ * the final map centre (info->centre), ready for klst_build_pencil_base.  Errors: KLST_EINVAL,
+ * KLST_ENOMEM, KLST_ENOCONV (non-finite residual; a Gilbarg-Paolucci start that did not reach the
+ * upstream state).  Synchronising.
  */
 int klst_bgk_base_flow(const klst_pencil_desc* desc, const klst_bgk_opts* opts, void* g_out, void* h_out,
                        klst_bgk_info* info, klst_stream stream);

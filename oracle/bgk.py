@@ -19,6 +19,8 @@ dq/dt = RHS(q) with q = (g, h):
     the grid is rebuilt about it and g, h are moved onto the new nodes by linear interpolation in
     x, the end values re-imposed.
 
+The start is the Mott-Smith profile or the Gilbarg-Paolucci one (initial_state).
+
 Arrays here are in physical order (index i = 0 at x = c - s_inf upstream, increasing x), shape
 (Nx, Nxi); `to_pencil_order` reverses to the pencil's node order (j = 0 at the downstream end).
 """
@@ -153,24 +155,26 @@ def regrid(g, h, x_old, x_new, ends):
     return gn, hn
 
 
-def initial_state(spec, x, xi_x, xi_y, W):
-    """Mott-Smith profile about x = 0 (gas.base_flow), the ends set to the end states."""
+def initial_state(spec, x, xi_x, xi_y, W, start="mott_smith"):
+    """The start (gas.base_flow): the Mott-Smith profile about x = 0, or ('gilbarg_paolucci') the local
+    Maxwellian of the continuum profile with its steepest point at x = 0 (the paper aligns the grid
+    with the peak slope of an initial Gilbarg-Paolucci profile); the ends set to the end states."""
     s2 = dict(spec.as_dict() if hasattr(spec, "as_dict") else spec)
-    s2["base"] = "mott_smith"
+    s2["base"] = start
     g, h = gas.base_flow(s2, x, xi_x, xi_y)
     (gu, hu), (gd, hd) = end_states(spec, xi_x, xi_y, W)
     g[0], h[0], g[-1], h[-1] = gu, hu, gd, hd
     return g, h
 
 
-def steady(spec, steps, cfl=0.5, recentre_every=0, recentre_tol=0.25, tol=0.0, dt=0.0):
-    """Integrate from the Mott-Smith start for at most ``steps`` RK4 steps (stopping once
+def steady(spec, steps, cfl=0.5, recentre_every=0, recentre_tol=0.25, tol=0.0, dt=0.0, start="mott_smith"):
+    """Integrate from the start (initial_state) for at most ``steps`` RK4 steps (stopping once
     max|RHS| <= tol max|g|; dt > 0: a fixed time step); returns dict(g, h (pencil order), centre,
     steps, resid, recentres)."""
     xi_x, xi_y, W = grids.velocity_grid(gas._p(spec, "qx"), gas._p(spec, "qy"))
     c = 0.0
     x = grid(spec, c)
-    g, h = initial_state(spec, x, xi_x, xi_y, W)
+    g, h = initial_state(spec, x, xi_x, xi_y, W, start)
     ends = end_states(spec, xi_x, xi_y, W)
     resid = np.inf
     n = recentres = 0

@@ -16,7 +16,8 @@
 // * adaptive re-centring: the interval of largest |dU/dx| of the bulk velocity locates the shock;
 //   when it has moved more than `recentre_tol` from the map centre the nodes are rebuilt about it and
 //   g, h are moved onto them by linear interpolation in x, the ends re-imposed.
-// The start is a Mott-Smith profile about x = 0.  Layout: q[(c Nxi + k) Nx + i], c in (g, h), i the
+// The start is a Mott-Smith profile about x = 0, or the local Maxwellian of the Gilbarg-Paolucci
+// continuum profile with its steepest point at x = 0 (gp.cu).  Layout: q[(c Nxi + k) Nx + i], c in (g, h), i the
 // node in increasing x (i = 0 upstream).  The result is written in the pencil's node order.
 #include <algorithm>
 #include <chrono>
@@ -130,7 +131,7 @@ __global__ void k_bgk_grid(int nx, int nxi, const double* x_pencil, double centr
 
 // the Mott-Smith start about x = 0 (continuous end states in the mixture), ends set to the end states
 __global__ void k_bgk_init(BgkConst c, const double* x, const double* xi_x, const double* xi_y, const double* ends,
-                           double* q) {
+                           const double* gp, double* q) {
     const int nx = c.nx, nxi = c.nxi;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nx * nxi; idx += gridDim.x * blockDim.x) {
         const int k = idx / nx, i = idx - k * nx;
@@ -140,6 +141,10 @@ __global__ void k_bgk_init(BgkConst c, const double* x, const double* xi_x, cons
             const double* e = ends + (i == 0 ? 0 : 3);
             g = maxw(e[0], e[1], e[2], xx, xy);
             h = 0.5 * e[2] * g;
+        } else if (gp) {   // the Gilbarg-Paolucci profile, [3][nx] in the pencil's node order
+            const int j = nx - 1 - i;
+            g = maxw(gp[j], gp[nx + j], gp[2 * nx + j], xx, xy);
+            h = 0.5 * gp[2 * nx + j] * g;
         } else {
             const double sx = 0.5 * (1.0 + tanh(x[i] / c.width));
             const double g1 = maxw(c.rho1, c.u1, c.T1, xx, xy), g2 = maxw(c.rho2, c.u2, c.T2, xx, xy);
@@ -373,8 +378,13 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
     if (!d || !o || !g_out || !h_out) { set_error("invalid arguments to klst_bgk_base_flow"); return KLST_EINVAL; }
     if (o->max_steps < 0 || !(o->cfl > 0) || o->check_every < 1 || o->recentre_every < 0 ||
         (o->recentre_every > 0 && o->recentre_every % o->check_every != 0) || !(o->tol >= 0) || !(o->dt >= 0) ||
-        !(o->recentre_tol > 0)) {
-        set_error("invalid BE-BGK options (cfl > 0, check_every >= 1, recentre_every a multiple of check_every)");
+        !(o->recentre_tol > 0) || (o->start != 0 && o->start != 1)) {
+        set_error("invalid BE-BGK options (cfl > 0, check_every >= 1, recentre_every a multiple of check_every, start 0 or 1)");
+        return KLST_EINVAL;
+    }
+    const klst_gp_case gpc = {d->mach, d->re_delta, d->visc_s, 1.0};
+    if (o->start == 1 && (fabs(d->gamma - 5.0 / 3.0) > 1e-12 || !gp_case_valid(gpc))) {
+        set_error("the Gilbarg-Paolucci start needs gamma = 5/3, 1.01 <= mach <= 100 and 0 <= visc_s <= 2");
         return KLST_EINVAL;
     }
     auto t0 = std::chrono::steady_clock::now();
@@ -405,7 +415,7 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
         (e = cudaEventRecord(ev, user)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev, 0)) != cudaSuccess)
         return fail(cuda_fail(e, "bgk stream", __FILE__, __LINE__));
     // workspace: q0, two stage buffers, acc, a regrid buffer, node arrays, per-node tables
-    const size_t nd = 5 * nq + 4 * (size_t)nx + 4 * (size_t)nx + 2 * (size_t)nx + 16;
+    const size_t nd = 5 * nq + 4 * (size_t)nx + 4 * (size_t)nx + 2 * (size_t)nx + 16 + 3 * (size_t)nx + 16;
     if ((e = dmalloc((void**)&buf, sizeof(double) * nd, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     double *q0 = buf, *qa = q0 + nq, *qb = qa + nq, *acc = qb + nq, *qr = acc + nq;
     double *x = qr + nq, *xnew = x + nx, *dxinv = xnew + nx, *ubulk = dxinv + nx;
@@ -417,6 +427,7 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
     unsigned long long* res = (unsigned long long*)(scratch + 10);     // 2: max|r|, max|g|
     unsigned long long* numax = (unsigned long long*)(scratch + 12);   // 1
     unsigned long long* newton = (unsigned long long*)(scratch + 13);  // 1: Newton updates in total
+    double* gpb = scratch + 16;      // the Gilbarg-Paolucci start: rho, u, T at the nodes, its case and result
     cudaMemsetAsync(th, 0, sizeof(double) * 4 * nx, s);
     cudaMemsetAsync(nu, 0, sizeof(double) * nx, s);
     cudaMemsetAsync(ubulk, 0, sizeof(double) * nx, s);
@@ -436,7 +447,18 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
     double centre = 0.0;
     k_bgk_grid<<<1, 128, 0, s>>>(nx, nxi, p->x, 0.0, p->xi_x, x, dxinv, lim); note_launch();
     k_bgk_ends<<<1, 256, 0, s>>>(c, p->xi_x, p->xi_y, p->W, ends); note_launch();
-    k_bgk_init<<<nb, 256, 0, s>>>(c, x, p->xi_x, p->xi_y, ends, q0); note_launch();
+    klst_gp_result gpr;
+    gpr.status = KLST_OK;
+    if (o->start == 1) {   // the pencil's nodes are in decreasing x: the order the integration visits them
+        klst_gp_case* dc = (klst_gp_case*)(gpb + 3 * nx);
+        klst_gp_result* dr = (klst_gp_result*)(gpb + 3 * nx + 8);
+        if ((e = cudaMemcpyAsync(dc, &gpc, sizeof gpc, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__));
+        if ((rc = gp_shock_device(dc, nullptr, 1, 0.02, 1e-6, 1 << 20, p->x, nullptr, nx, gpb, dr, s))) return fail(rc);
+        if ((e = cudaMemcpyAsync(&gpr, dr, sizeof gpr, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__));
+    }
+    k_bgk_init<<<nb, 256, 0, s>>>(c, x, p->xi_x, p->xi_y, ends, o->start == 1 ? gpb : nullptr, q0); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "bgk setup", __FILE__, __LINE__));
     // the stage buffers carry the end values too (never written by the stages)
     cudaMemcpyAsync(qa, q0, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
@@ -449,6 +471,10 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
         (e = cudaMemcpyAsync(&hnu, numax, sizeof hnu, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(cuda_fail(e, "bgk setup", __FILE__, __LINE__));
+    if (gpr.status != KLST_OK) {
+        set_error("the Gilbarg-Paolucci start did not reach the upstream state");
+        return fail(KLST_ENOCONV);
+    }
     auto pick_dt = [&](double numax_v) {
         if (o->dt > 0) return o->dt;
         return std::min(o->cfl * hlim[0] / hlim[1], numax_v > 0 ? 2.0 / numax_v : 1e300);

@@ -165,10 +165,11 @@ cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s);
 void dfree(void* ptr, cudaStream_t s);
 
 // ------------------------------------------------------------------ Gilbarg-Paolucci shock (gp.cu)
-// One thread per case; cases, results and the [3][n][npts] profile in device memory, xs (device)
-// in decreasing order, perm the output column of each sorted point (null: the identity).
-int gp_shock_device(const klst_gp_case* cases, int n, double step, double eps, int max_steps, const double* xs,
-                    const int* perm, int npts, double* prof, klst_gp_result* res, cudaStream_t s);
+// One thread per case; cases, results and the [3][n][npts] profile in device memory, cidx the
+// caller's index of each case, xs (device) in decreasing order, perm the output column of each sorted
+// point (null: the identity).
+int gp_shock_device(const klst_gp_case* cases, const int* cidx, int n, double step, double eps, int max_steps,
+                    const double* xs, const int* perm, int npts, double* prof, klst_gp_result* res, cudaStream_t s);
 bool gp_case_valid(const klst_gp_case& c);
 // test hook behind klst_debug_fail_alloc_after: the n-th next dmalloc fails (n < 0: off)
 void fail_alloc_after(long long n);

@@ -31,7 +31,7 @@ constexpr double kGamma = 5.0 / 3.0;
 constexpr double kReach = 1e-13;   // relative distance to the upstream state that ends the integration
 
 struct GpSys {
-    double m, P, H, u1, T1, u2, T2, cmu, s, Pr;
+    double m, P, H, u1, T1, u2, T2, rmu, s, Pr;   // rmu = 1 / mu(T = 1) = Re / u_inf
 
     __device__ void init(const klst_gp_case& c) {
         const double M = c.mach;
@@ -44,11 +44,14 @@ struct GpSys {
         m = u1;
         P = 0.5 + m * u1;
         H = 1.25 + 0.5 * u1 * u1;
-        cmu = u1 / c.re;
+        rmu = c.re / u1;
         s = c.visc_s;
         Pr = c.prandtl;
     }
-    __device__ __forceinline__ double inv_mu(double T) const { return 1.0 / (cmu * pow(T, s)); }
+    // 1 / mu(T); FP64 is a narrow pipe on this part, so the common exponents avoid the general power
+    __device__ __forceinline__ double inv_mu(double T) const {
+        return rmu * (s == 0.5 ? rsqrt(T) : s == 1.0 ? 1.0 / T : pow(T, -s));
+    }
     __device__ __forceinline__ void f(double u, double T, double& du, double& dT) const {
         const double im = inv_mu(T);
         du = 0.75 * im * (m * u + 0.5 * m * T / u - P);
@@ -121,12 +124,13 @@ __device__ void eig2(const double J[4], double& lo, double& hi, double& absmax) 
     }
 }
 
-__global__ void k_gp_shock(const klst_gp_case* cases, int n, double step, double eps, int max_steps, const double* xs,
-                           const int* perm, int npts, double* prof, klst_gp_result* res) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+__global__ void k_gp_shock(const klst_gp_case* cases, const int* cidx, int n, double step, double eps, int max_steps,
+                           const double* xs, const int* perm, int npts, double* prof, klst_gp_result* res) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int c = cidx ? cidx[t] : t;   // the case's index in the caller's order
     GpSys S;
-    S.init(cases[c]);
+    S.init(cases[t]);
     klst_gp_result out;
     out.status = KLST_OK;
     // the end states' Jacobians: the stable direction at the saddle and the step length
@@ -226,12 +230,14 @@ __global__ void k_gp_shock(const klst_gp_case* cases, int n, double step, double
 
 }  // namespace
 
-// Launches the batch: cases, result and profile in device memory; xs (device) sorted in decreasing
-// order, perm (device, or null for the identity) the output column of each sorted point.
-int gp_shock_device(const klst_gp_case* cases, int n, double step, double eps, int max_steps, const double* xs,
-                    const int* perm, int npts, double* prof, klst_gp_result* res, cudaStream_t s) {
+// Launches the batch: cases, result and profile in device memory; cidx (device, or null for the
+// identity) the caller's index of each case (results and profile rows are written there); xs (device)
+// sorted in decreasing order, perm (device, or null) the output column of each sorted point.
+int gp_shock_device(const klst_gp_case* cases, const int* cidx, int n, double step, double eps, int max_steps,
+                    const double* xs, const int* perm, int npts, double* prof, klst_gp_result* res, cudaStream_t s) {
     if (n <= 0) return KLST_OK;
-    k_gp_shock<<<(n + 63) / 64, 64, 0, s>>>(cases, n, step, eps, max_steps, xs, perm, npts, prof, res);
+    // one warp per CTA: a batch of a few thousand cases still spreads over every SM
+    k_gp_shock<<<(n + 31) / 32, 32, 0, s>>>(cases, cidx, n, step, eps, max_steps, xs, perm, npts, prof, res);
     note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KLST_OK : cuda_fail(e, "k_gp_shock", __FILE__, __LINE__);
@@ -277,8 +283,15 @@ extern "C" int klst_gp_shock(const klst_gp_case* cases, int32_t ncases, const kl
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return x[a] > x[b]; });
     std::vector<double> xsorted(npts);
     for (int i = 0; i < npts; ++i) xsorted[i] = x[order[i]];
+    // cases in decreasing Mach number: the steps a case takes grow as M -> 1, and a warp runs as long
+    // as its longest case, so neighbours of similar length keep the lanes busy
+    std::vector<int> corder(ncases);
+    std::iota(corder.begin(), corder.end(), 0);
+    std::stable_sort(corder.begin(), corder.end(), [&](int a, int b) { return cases[a].mach > cases[b].mach; });
+    std::vector<klst_gp_case> csorted(ncases);
+    for (int i = 0; i < ncases; ++i) csorted[i] = cases[corder[i]];
     const size_t bytes = sizeof(klst_gp_case) * ncases + sizeof(klst_gp_result) * ncases + sizeof(double) * npts +
-                         sizeof(int) * npts + 64;
+                         sizeof(int) * npts + sizeof(int) * ncases + 64;
     char* buf = nullptr;
     cudaError_t e = dmalloc((void**)&buf, bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
@@ -286,12 +299,14 @@ extern "C" int klst_gp_shock(const klst_gp_case* cases, int32_t ncases, const kl
     klst_gp_result* dr = (klst_gp_result*)(dc + ncases);
     double* dx = (double*)(((uintptr_t)(dr + ncases) + 15) & ~(uintptr_t)15);
     int* dp = (int*)(dx + npts);
+    int* di = dp + npts;
     int rc = KLST_OK;
-    if ((e = cudaMemcpyAsync(dc, cases, sizeof(klst_gp_case) * ncases, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(dc, csorted.data(), sizeof(klst_gp_case) * ncases, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(di, corder.data(), sizeof(int) * ncases, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (npts > 0 && ((e = cudaMemcpyAsync(dx, xsorted.data(), sizeof(double) * npts, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
                       (e = cudaMemcpyAsync(dp, order.data(), sizeof(int) * npts, cudaMemcpyHostToDevice, s)) != cudaSuccess)))
         rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
-    if (!rc) rc = gp_shock_device(dc, ncases, step, eps, max_steps, dx, dp, npts, (double*)profile, dr, s);
+    if (!rc) rc = gp_shock_device(dc, di, ncases, step, eps, max_steps, dx, dp, npts, (double*)profile, dr, s);
     if (!rc && (e = cudaMemcpyAsync(results, dr, sizeof(klst_gp_result) * ncases, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
     if (!rc && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e, "gp sync", __FILE__, __LINE__);

@@ -499,7 +499,7 @@ static int build_pencil(const klst_pencil_desc* d, const double* user_g, const d
         if ((e = cudaMemcpyAsync(dc, &gpc, sizeof(gpc), cudaMemcpyHostToDevice, s)) != cudaSuccess)
             rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
         // the nodes are in decreasing x (node 0 downstream): the order the integration visits them
-        if (!rc) rc = gp_shock_device(dc, 1, 0.02, 1e-6, 1 << 20, p->x, nullptr, nx, gp, dr, s);
+        if (!rc) rc = gp_shock_device(dc, nullptr, 1, 0.02, 1e-6, 1 << 20, p->x, nullptr, nx, gp, dr, s);
         klst_gp_result r;
         if (!rc && (e = cudaMemcpyAsync(&r, dr, sizeof(r), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);

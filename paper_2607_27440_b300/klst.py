@@ -63,7 +63,8 @@ class JdInfo(ctypes.Structure):
 
 class BgkOpts(ctypes.Structure):
     _fields_ = [("max_steps", c_int32), ("cfl", c_double), ("dt", c_double), ("tol", c_double),
-                ("check_every", c_int32), ("recentre_every", c_int32), ("recentre_tol", c_double)]
+                ("check_every", c_int32), ("recentre_every", c_int32), ("recentre_tol", c_double),
+                ("start", c_int32)]
 
 
 class BgkInfo(ctypes.Structure):
@@ -459,17 +460,21 @@ class Factor:
         return (ev[0:2 * k:2] + 1j * ev[1:2 * k:2], vec[:k] if vec is not None else None, res[:k], d)
 
 
+BGK_STARTS = {"mott_smith": 0, "gilbarg_paolucci": 1}
+
+
 def bgk_base_flow(spec, max_steps=20000, cfl=0.5, dt=0.0, tol=0.0, check_every=100, recentre_every=0,
-                  recentre_tol=0.25, stream=None):
+                  recentre_tol=0.25, start="mott_smith", stream=None):
     """klst_bgk_base_flow: the BE-BGK steady shock on the pencil's grid; returns (g, h, info) with g, h
-    float64 CUDA tensors of shape (Nx, Nxi) in node order (j = 0 downstream)."""
+    float64 CUDA tensors of shape (Nx, Nxi) in node order (j = 0 downstream).  start: 'mott_smith' or
+    'gilbarg_paolucci' (the continuum profile's local Maxwellian)."""
     lib = load()
     torch = _torch()
     d = make_desc(spec)
     g = torch.empty((spec.nx, spec.nxi), dtype=torch.float64, device="cuda")
     h = torch.empty_like(g)
     o = BgkOpts(max_steps=max_steps, cfl=cfl, dt=dt, tol=tol, check_every=check_every,
-                recentre_every=recentre_every, recentre_tol=recentre_tol)
+                recentre_every=recentre_every, recentre_tol=recentre_tol, start=BGK_STARTS[start])
     info = BgkInfo()
     _check(lib.klst_bgk_base_flow(ctypes.byref(d), ctypes.byref(o), _ptr(g), _ptr(h), ctypes.byref(info),
                                   _stream(stream)))

@@ -34,6 +34,19 @@ def test_rk4_steps_match_oracle(klst, spec):
     assert np.abs(_host(h) - ref["h"]).max() <= 1e-11 * np.abs(ref["h"]).max()
 
 
+@pytest.mark.parametrize("steps", [0, 60])
+def test_gilbarg_paolucci_start_matches_oracle(klst, steps):
+    """The Gilbarg-Paolucci start (the continuum profile's local Maxwellian, steepest point at x = 0)
+    and 60 RK4 steps from it equal the oracle's; the start's profile agrees to ~2e-8 of the jump
+    (fixed-step RK4 on the device, adaptive integration in the oracle), hence the tolerance."""
+    spec = wl.tiny(nx=16, qx=8, qy=6, mach=3.0, re_delta=9.68)
+    g, h, info = klst.bgk_base_flow(spec, max_steps=steps, dt=0.02, check_every=20, start="gilbarg_paolucci")
+    assert info["steps"] == steps
+    ref = bgk.steady(spec, steps=steps, dt=0.02, start="gilbarg_paolucci")
+    assert np.abs(_host(g) - ref["g"]).max() <= 1e-7 * np.abs(ref["g"]).max()
+    assert np.abs(_host(h) - ref["h"]).max() <= 1e-7 * np.abs(ref["h"]).max()
+
+
 def test_recentring_matches_oracle(klst):
     """With re-centring every 20 steps and a tight threshold the grid is rebuilt about the shock and
     the state moved by linear interpolation; the same rebuilds and the same state as the oracle."""
@@ -95,3 +108,6 @@ def test_bgk_invalid_options(klst):
         with pytest.raises(klst.KlstError) as ei:
             klst.bgk_base_flow(spec, **kw)
         assert ei.value.code == klst.KLST_EINVAL
+    with pytest.raises(klst.KlstError) as ei:   # the continuum profile is monatomic
+        klst.bgk_base_flow(wl.tiny(nx=12, qx=6, qy=4, mach=1.5, gamma=1.4), start="gilbarg_paolucci")
+    assert ei.value.code == klst.KLST_EINVAL
