@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-gp", action="store_true", help="skip the Gilbarg-Paolucci continuum-shock leg")
     ap.add_argument("--max-restarts", type=int, default=None,
                     help="cap the eigensolve's restarts (bounded runs for profiling; the line is then not a bench value)")
+    ap.add_argument("--profile-leg", default=None, choices=["gp", "bgk"],
+                    help="run one small call for an ncu capture and exit (no bench line): 'gp' = the continuum-shock "
+                         "leg's 8,192 cases, 'bgk' = 20 BE-BGK RK4 steps on the C3 shape")
     ap.add_argument("--serve-rates", default="1,2,5,10,20,50",
                     help="Poisson arrival rates of the serving runs (1/s), comma-separated")
     ap.add_argument("--serve-window", type=float, default=6.0, help="arrival window of each serving run (s)")
@@ -877,6 +880,23 @@ def cpu_baseline(args, steps=1):
                       f"{dt:.1f} s on {cores} host cores"}
 
 
+def profile_leg(which):
+    """One small, bounded call of a leg's kernels for an ncu capture (prints what ran, not a bench value)."""
+    import torch
+    from paper_2607_27440_b300 import klst, workloads as wl
+    klst.load()
+    if which == "gp":
+        rng = np.random.default_rng(2026)
+        M, s = rng.uniform(1.1, 10.0, GP_CASES), rng.uniform(0.5, 1.0, GP_CASES)
+        res, _ = klst.gp_shock(M, 1.0, s, 1.0)
+        print(json.dumps({"leg": "gp", "cases": GP_CASES, "steps_total": int(np.sum(res["steps"]))}))
+    else:
+        spec = wl.c3()[0]
+        _, _, info = klst.bgk_base_flow(spec, max_steps=20, cfl=0.5, check_every=10)
+        print(json.dumps({"leg": "bgk", "shape": [spec.nx, spec.qx, spec.qy], "steps": info["steps"]}))
+    torch.cuda.synchronize()
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -906,6 +926,9 @@ if __name__ == "__main__":
         cpu_verify_main(sys.argv[2])
         sys.exit(0)
     a = parse()
+    if a.profile_leg:
+        profile_leg(a.profile_leg)
+        sys.exit(0)
     if a.impl == "reference":
         run_reference(a)
     else:
