@@ -31,7 +31,7 @@ namespace klst {
 namespace {
 
 struct BgkConst {
-    int nx, nxi;
+    int nx, nxi, qx, qy;               // nodes, velocity nodes (k = kx qy + ky on the tensor grid)
     double uinf, re, s, width;         // u_inf, Re_Delta, viscosity exponent, Mott-Smith width
     double rho1, u1, T1, rho2, u2, T2; // upstream and continuous Rankine-Hugoniot states
 };
@@ -172,11 +172,19 @@ __global__ void k_bgk_set_ends(BgkConst c, const double* xi_x, const double* xi_
 // (Newton, started from the node's previous parameters, or from the moments the first time),
 // nu = P / mu; th[4 i + (0, 1, 2)] = (rho', u', T'), nu[i], ubulk[i]; the largest nu into *numax
 // (its bits: non-negative doubles order as integers)
+//
+// The Maxwellian is separable on the tensor-product velocity grid: g^e(kx, ky) = rho / (pi T)
+// exp(-(xi_x,kx - u)^2 / T) exp(-xi_y,ky^2 / T), so a Newton iteration takes qx + qy exponentials
+// (kept in shared memory) instead of one per velocity node, and the reciprocals of T and rho once.
+// The final parameters' factors go to eqt for the stage kernel: eqt[kx nx + i] = rho / (pi T)
+// exp(-(xi_x,kx - u)^2 / T), eqt[(qx + ky) nx + i] = exp(-xi_y,ky^2 / T).
 __global__ void __launch_bounds__(128) k_bgk_eq(BgkConst c, const double* __restrict__ q, const double* xi_x,
                                                 const double* xi_y, const double* W, double* th, double* nu,
-                                                double* ubulk, unsigned long long* numax, unsigned long long* newton) {
+                                                double* ubulk, unsigned long long* numax, unsigned long long* newton,
+                                                double* eqt) {
     __shared__ double sm[32 * 12 + 12];
     __shared__ double s_th[4];
+    __shared__ double s_ex[256], s_ey[256];
     const int nx = c.nx, nxi = c.nxi, i = blockIdx.x + 1;
     double mom[4] = {0, 0, 0, 0};
     for (int k = threadIdx.x; k < nxi; k += blockDim.x) {
@@ -202,14 +210,26 @@ __global__ void __launch_bounds__(128) k_bgk_eq(BgkConst c, const double* __rest
     for (int it = 0; it < kNewtonMax; ++it) {
         ++its;
         const double r_ = s_th[0], u_ = s_th[1], T_ = s_th[2];
+        const double iT = 1.0 / T_, ir = 1.0 / r_, pref = r_ * iT * (1.0 / M_PI);
+        for (int a = threadIdx.x; a < c.qx + c.qy; a += blockDim.x) {
+            if (a < c.qx) {
+                const double d = xi_x[a * c.qy] - u_;
+                s_ex[a] = pref * exp(-(d * d) * iT);
+            } else {
+                const double y = xi_y[a - c.qx];
+                s_ey[a - c.qx] = exp(-(y * y) * iT);
+            }
+        }
+        __syncthreads();
         double acc[12];
 #pragma unroll
         for (int a = 0; a < 12; ++a) acc[a] = 0.0;
         for (int k = threadIdx.x; k < nxi; k += blockDim.x) {
+            const int kx = k / c.qy, ky = k - kx * c.qy;
             const double xx = xi_x[k], xy = xi_y[k], Wk = W[k];
-            const double ge = maxw(r_, u_, T_, xx, xy), dxu = xx - u_, e2 = xx * xx + xy * xy;
-            const double phi = -1.0 / T_ + (dxu * dxu + xy * xy) / (T_ * T_);
-            const double dg[3] = {ge / r_, ge * 2.0 * dxu / T_, ge * phi};
+            const double ge = s_ex[kx] * s_ey[ky], dxu = xx - u_, e2 = xx * xx + xy * xy;
+            const double phi = (dxu * dxu + xy * xy) * (iT * iT) - iT;
+            const double dg[3] = {ge * ir, ge * 2.0 * dxu * iT, ge * phi};
             acc[0] += Wk * ge;
             acc[1] += Wk * xx * ge;
             acc[2] += 0.5 * Wk * (e2 * ge + 0.5 * T_ * ge);
@@ -235,6 +255,21 @@ __global__ void __launch_bounds__(128) k_bgk_eq(BgkConst c, const double* __rest
         if (s_th[3] != 0.0) break;
         __syncthreads();
     }
+    {   // the final parameters' factors for the stage kernel
+        const double r_ = s_th[0], u_ = s_th[1], T_ = s_th[2];
+        const double iT = 1.0 / T_, pref = r_ * iT * (1.0 / M_PI);
+        for (int a = threadIdx.x; a < c.qx + c.qy; a += blockDim.x) {
+            double v;
+            if (a < c.qx) {
+                const double d = xi_x[a * c.qy] - u_;
+                v = pref * exp(-(d * d) * iT);
+            } else {
+                const double y = xi_y[a - c.qx];
+                v = exp(-(y * y) * iT);
+            }
+            eqt[(size_t)a * nx + i] = v;
+        }
+    }
     if (threadIdx.x == 0) {
         atomicAdd(newton, (unsigned long long)its);
         th[4 * i] = s_th[0];
@@ -258,17 +293,18 @@ __global__ void __launch_bounds__(128) k_bgk_eq(BgkConst c, const double* __rest
 __global__ void __launch_bounds__(256) k_bgk_stage(BgkConst c, int stage, const double* __restrict__ qs,
                                                    double* __restrict__ q0, double* __restrict__ qn,
                                                    double* __restrict__ acc, const double* __restrict__ dxinv,
-                                                   const double* xi_x, const double* xi_y, const double* __restrict__ th,
-                                                   const double* __restrict__ nu, const double* dtp, int track,
-                                                   unsigned long long* res) {
+                                                   const double* xi_x, const double* __restrict__ th,
+                                                   const double* __restrict__ eqt, const double* __restrict__ nu,
+                                                   const double* dtp, int track, unsigned long long* res) {
     const int nx = c.nx, nxi = c.nxi;
     const double dt = *dtp;
     double rmax = 0.0, gmax = 0.0;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nx * nxi; idx += gridDim.x * blockDim.x) {
         const int k = idx / nx, i = idx - k * nx;
         if (i == 0 || i == nx - 1) continue;
-        const double xx = xi_x[k], xy = xi_y[k];
-        const double ge = maxw(th[4 * i], th[4 * i + 1], th[4 * i + 2], xx, xy);
+        const double xx = xi_x[k];
+        const int kx = k / c.qy, ky = k - kx * c.qy;
+        const double ge = eqt[(size_t)kx * nx + i] * eqt[(size_t)(c.qx + ky) * nx + i];   // k_bgk_eq's factors
         const double eq[2] = {ge, 0.5 * th[4 * i + 2] * ge};
         const int im2 = max(i - 2, 0), ip2 = min(i + 2, nx - 1);
 #pragma unroll
@@ -415,7 +451,8 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
         (e = cudaEventRecord(ev, user)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev, 0)) != cudaSuccess)
         return fail(cuda_fail(e, "bgk stream", __FILE__, __LINE__));
     // workspace: q0, two stage buffers, acc, a regrid buffer, node arrays, per-node tables
-    const size_t nd = 5 * nq + 4 * (size_t)nx + 4 * (size_t)nx + 2 * (size_t)nx + 16 + 3 * (size_t)nx + 16;
+    const size_t nd = 5 * nq + 4 * (size_t)nx + 4 * (size_t)nx + 2 * (size_t)nx + 16 + 3 * (size_t)nx + 16 +
+                      (size_t)(d->qx + d->qy) * nx;
     if ((e = dmalloc((void**)&buf, sizeof(double) * nd, s)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     double *q0 = buf, *qa = q0 + nq, *qb = qa + nq, *acc = qb + nq, *qr = acc + nq;
     double *x = qr + nq, *xnew = x + nx, *dxinv = xnew + nx, *ubulk = dxinv + nx;
@@ -428,13 +465,14 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
     unsigned long long* numax = (unsigned long long*)(scratch + 12);   // 1
     unsigned long long* newton = (unsigned long long*)(scratch + 13);  // 1: Newton updates in total
     double* gpb = scratch + 16;      // the Gilbarg-Paolucci start: rho, u, T at the nodes, its case and result
+    double* eqt = gpb + 3 * nx + 16; // the equilibrium's separable factors per node ((qx + qy) x nx)
     cudaMemsetAsync(th, 0, sizeof(double) * 4 * nx, s);
     cudaMemsetAsync(nu, 0, sizeof(double) * nx, s);
     cudaMemsetAsync(ubulk, 0, sizeof(double) * nx, s);
     cudaMemsetAsync(acc, 0, sizeof(double) * nq, s);
     cudaMemsetAsync(newton, 0, sizeof(unsigned long long), s);
     BgkConst c;
-    c.nx = nx; c.nxi = nxi;
+    c.nx = nx; c.nxi = nxi; c.qx = d->qx; c.qy = d->qy;
     {
         const double g = d->gamma, M = d->mach;
         c.rho1 = 1.0; c.T1 = 1.0; c.u1 = M * sqrt(g / 2.0);
@@ -465,7 +503,7 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
     cudaMemcpyAsync(qb, q0, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s);
     double hlim[2];
     cudaMemsetAsync(numax, 0, sizeof(unsigned long long), s);
-    k_bgk_eq<<<nx - 2, 128, 0, s>>>(c, q0, p->xi_x, p->xi_y, p->W, th, nu, ubulk, numax, newton); note_launch();
+    k_bgk_eq<<<nx - 2, 128, 0, s>>>(c, q0, p->xi_x, p->xi_y, p->W, th, nu, ubulk, numax, newton, eqt); note_launch();
     unsigned long long hnu = 0;
     if ((e = cudaMemcpyAsync(hlim, lim, sizeof hlim, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&hnu, numax, sizeof hnu, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -488,8 +526,8 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
         const double* in[4] = {q0, qa, qb, qa};
         double* outb[4] = {qa, qb, qa, nullptr};
         for (int st = 0; st < 4; ++st) {
-            k_bgk_eq<<<nx - 2, 128, 0, s>>>(c, in[st], p->xi_x, p->xi_y, p->W, th, nu, ubulk, numax, newton);
-            k_bgk_stage<<<nb, 256, 0, s>>>(c, st, in[st], q0, outb[st] ? outb[st] : qa, acc, dxinv, p->xi_x, p->xi_y, th,
+            k_bgk_eq<<<nx - 2, 128, 0, s>>>(c, in[st], p->xi_x, p->xi_y, p->W, th, nu, ubulk, numax, newton, eqt);
+            k_bgk_stage<<<nb, 256, 0, s>>>(c, st, in[st], q0, outb[st] ? outb[st] : qa, acc, dxinv, p->xi_x, th, eqt,
                                            nu, dtd, st == 0 ? track : 0, res);
         }
     };
@@ -523,7 +561,7 @@ extern "C" int klst_bgk_base_flow(const klst_pencil_desc* d, const klst_bgk_opts
         if (o->tol > 0 && resid <= o->tol) break;
         if (o->recentre_every > 0 && steps % o->recentre_every == 0) {
             // the bulk velocity of the current state (the stages' last moments are of a stage input)
-            k_bgk_eq<<<nx - 2, 128, 0, s>>>(c, q0, p->xi_x, p->xi_y, p->W, th, nu, ubulk, numax, newton); note_launch();
+            k_bgk_eq<<<nx - 2, 128, 0, s>>>(c, q0, p->xi_x, p->xi_y, p->W, th, nu, ubulk, numax, newton, eqt); note_launch();
             k_bgk_shock<<<1, 32, 0, s>>>(nx, x, ubulk, ends, xs); note_launch();
             double hxs = 0;
             if ((e = cudaMemcpyAsync(&hxs, xs, sizeof hxs, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
