@@ -5,6 +5,10 @@
 // as the double-float kernels of schur.cu, with float64 operands, float64 deflation (unit
 // roundoff 2^-53) and float64 rotations; k_schur_post (Ritz estimates, selection, truncation) is
 // shared.
+#include <cooperative_groups.h>
+#include <cstdlib>
+#include <mutex>
+
 #include "factor.cuh"
 
 namespace klst {
@@ -171,6 +175,194 @@ __global__ void __launch_bounds__(256) k_schur_house64(SchurArgs a) {
         __syncthreads();
     }
 #undef HH
+}
+
+// The same reduction spread over one thread-block cluster of NC CTAs (one SM's float64 pipe is
+// the bound of the single-CTA kernel).  CTA q keeps the columns j with j % NC == q in shared
+// memory (cyclic, so the work stays spread as the reduction moves right).  Per column c:
+//   1. the owner of column c forms v, tau and the new subdiagonal entry exactly as above and
+//      publishes a decision (0: nothing to do, 1: the tail is negligible and zeroed, 2: reflect);
+//   2. every CTA copies the decision, tau and v through distributed shared memory and applies the
+//      left reflection to its columns > c, one warp per column;
+//   3. every CTA forms, for every row r, the partial sum of H[r, col] v over its columns col > c;
+//      the NC partials of each row are read back through distributed shared memory and added in
+//      rank order, and every CTA applies the right reflection to its columns.
+// Three cluster barriers per column, taken by every CTA whatever the decision.
+template <int NC>
+__global__ void __launch_bounds__(256) k_schur_house64_cl(SchurArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int m = a.m, q = (int)cl.block_rank(), tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    const int ncol = (m - q + NC - 1) / NC;          // this CTA's columns: q, q + NC, ...
+    const int ncmax = (m + NC - 1) / NC;             // the most any CTA keeps: the same layout in every CTA
+    extern __shared__ __align__(16) unsigned char hsm[];
+    double2* hs = reinterpret_cast<double2*>(hsm);   // [ncol][m], column-major
+    double2* part = hs + (size_t)ncmax * m;          // [m] this CTA's partial row sums (read by the others)
+    double2* prow = part + m;                        // [m] the summed row products
+    double2* Vh = reinterpret_cast<double2*>(a.Vh);
+    __shared__ double2 v[192];
+    __shared__ double2 s_bet;
+    __shared__ double s_tau;
+    __shared__ int s_flag;
+    __shared__ double red[8];
+#define HL(i, lc) hs[(size_t)(lc) * m + (i)]
+    for (int idx = tid; idx < ncol * m; idx += nt) {
+        const int lc = idx / m, i = idx - lc * m;
+        HL(i, lc) = a.S[(size_t)(q + lc * NC) * a.lds + i];
+    }
+    if (q == 0) {
+        for (int i = tid; i < m; i += nt) a.tau[i] = 0.0;
+        if (tid == 0) { *a.nconv = 0; *a.log_count = 0; }
+    }
+    cl.sync();
+    for (int c = 0; c + 2 < m; ++c) {
+        const int owner = c % NC, len = m - c - 1;
+        if (q == owner) {
+            const int lcc = c / NC;
+            double tail = 0.0;
+            for (int i = c + 2 + tid; i < m; i += nt) tail += abs2(HL(i, lcc));
+            tail = block_sum64(tail, red);
+            const double2 x0 = HL(c + 1, lcc);
+            const double ax02 = abs2(x0), s2 = tail + ax02;
+            int flag = 2;
+            if (tail == 0.0) flag = 0;
+            else if (s2 < 1e-60) flag = 1;  // every subdiagonal entry below 1e-30: negligible, zeroed
+            if (flag == 2) {
+                const double alpha = sqrt(s2);
+                double ax0 = 0.0;
+                double2 ph = make_double2(1.0, 0.0);
+                if (ax02 > 1e-200) {
+                    ax0 = sqrt(ax02);
+                    ph = make_double2(x0.x / ax0, x0.y / ax0);
+                }
+                const double2 bet = make_double2(-alpha * ph.x, -alpha * ph.y);
+                for (int i = tid; i < len; i += nt) {
+                    const double2 vi = (i == 0) ? x0 - bet : HL(c + 1 + i, lcc);
+                    v[i] = vi;
+                    Vh[(size_t)c * m + c + 1 + i] = vi;
+                }
+                if (tid == 0) {
+                    s_tau = 1.0 / (alpha * (alpha + ax0));  // 2 / ||v||^2
+                    s_bet = bet;
+                    a.tau[c] = s_tau;
+                }
+            }
+            if (tid == 0) s_flag = flag;
+            __syncthreads();
+            if (flag == 2) {
+                if (tid == 0) HL(c + 1, lcc) = s_bet;
+                for (int i = c + 2 + tid; i < m; i += nt) HL(i, lcc) = make_double2(0.0, 0.0);
+            } else if (flag == 1) {
+                for (int i = c + 2 + tid; i < m; i += nt) HL(i, lcc) = make_double2(0.0, 0.0);
+            }
+        }
+        cl.sync();  // 1: the owner's decision, tau and v are published
+        const int flag = *cl.map_shared_rank(&s_flag, owner);
+        const double tau = *cl.map_shared_rank(&s_tau, owner);
+        if (flag == 2 && q != owner) {
+            const double2* vo = cl.map_shared_rank(v, owner);
+            for (int i = tid; i < len; i += nt) v[i] = vo[i];
+        }
+        __syncthreads();
+        if (flag == 2) {
+            // left: H[c+1:, col] -= tau v (v^H H[c+1:, col]) for this CTA's columns col > c
+            for (int lc = wid; lc < ncol; lc += nw) {
+                const int col = q + lc * NC;
+                if (col <= c) continue;
+                double2 g = make_double2(0.0, 0.0);
+                for (int i = lane; i < len; i += 32) cfma_conj(g, v[i], HL(c + 1 + i, lc));
+                g = make_double2(warp_sum(g.x), warp_sum(g.y));
+                g = (-tau) * g;
+                for (int i = lane; i < len; i += 32) {
+                    double2 hv = HL(c + 1 + i, lc);
+                    cfma(hv, v[i], g);
+                    HL(c + 1 + i, lc) = hv;
+                }
+            }
+            __syncthreads();
+            // right, partial: part[r] = sum over this CTA's columns col > c of H[r, col] v[col - c - 1]
+            for (int r = tid; r < m; r += nt) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int lc = 0; lc < ncol; ++lc) {
+                    const int col = q + lc * NC;
+                    if (col > c) cfma(acc, HL(r, lc), v[col - c - 1]);
+                }
+                part[r] = acc;
+            }
+        }
+        cl.sync();  // 2: every CTA's partial row sums are published
+        if (flag == 2) {
+            for (int r = tid; r < m; r += nt) {
+                double2 sum = make_double2(0.0, 0.0);
+                for (int k = 0; k < NC; ++k) sum = sum + cl.map_shared_rank(part, k)[r];
+                prow[r] = (-tau) * sum;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < ncol * m; idx += nt) {
+                const int lc = idx / m, r = idx - lc * m, col = q + lc * NC;
+                if (col <= c) continue;
+                double2 hv = HL(r, lc);
+                cfma(hv, prow[r], conj(v[col - c - 1]));
+                HL(r, lc) = hv;
+            }
+        }
+        cl.sync();  // 3: the partials and v may be overwritten by the next column
+    }
+    for (int idx = tid; idx < ncol * m; idx += nt) {
+        const int lc = idx / m, i = idx - lc * m;
+        a.H[(size_t)(q + lc * NC) * m + i] = HL(i, lc);
+    }
+#undef HL
+}
+
+// Launches the cluster reduction when one cluster of NC CTAs with its shared memory fits on the
+// device (checked once), else returns false and launches nothing.  KLST_NO_CLUSTER_HOUSE=1 keeps
+// the single-CTA kernel.
+template <int NC>
+static bool launch_house_cluster(const SchurArgs& a, cudaStream_t s) {
+    static std::mutex mu;
+    static int ok = -1;
+    const int m = a.m, ncmax = (m + NC - 1) / NC;
+    const size_t smem = sizeof(double2) * ((size_t)ncmax * m + 2 * (size_t)m);
+    if (m > 192 || smem > 160 * 1024) return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = NC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(NC, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (ok < 0) {
+            ok = 0;
+            const char* off = getenv("KLST_NO_CLUSTER_HOUSE");
+            if (!(off && off[0] == '1') &&
+                cudaFuncSetAttribute(k_schur_house64_cl<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) ==
+                    cudaSuccess) {
+                cudaLaunchConfig_t probe = cfg;
+                probe.dynamicSmemBytes = 160 * 1024;
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, k_schur_house64_cl<NC>, &probe) == cudaSuccess &&
+                    nclusters > 0)
+                    ok = 1;
+            }
+            cudaGetLastError();
+        }
+    }
+    if (!ok) return false;
+    if (cudaLaunchKernelEx(&cfg, k_schur_house64_cl<NC>, a) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    note_launch();
+    return true;
 }
 
 // ---------------------------------------------------------------- 2. QR sweeps + reordering
@@ -750,7 +942,7 @@ int launch_schur64(const SchurArgs& a, cudaStream_t s) {
     const int m = a.m;
     const size_t packed = sizeof(double2) * (size_t)m * (m + 3) / 2;
     prof_begin("schur_house", s);
-    k_schur_house64<<<1, 256, 0, s>>>(a); note_launch();
+    if (!launch_house_cluster<8>(a, s)) { k_schur_house64<<<1, 256, 0, s>>>(a); note_launch(); }
     prof_end("schur_house", s);
     prof_begin("schur_qr", s);
     k_schur_qr64<<<1, kQrThreads, packed, s>>>(a); note_launch();

@@ -184,3 +184,41 @@ def test_tensor_core_rotation_matches_cuda_core_rotation(klst, monkeypatch):
     perm = eig.match(o2, o1)
     assert np.max(np.abs(o1[perm] - o2) / np.abs(o2)) <= 1e-11
     assert np.max(r1) <= 1e-10 and np.max(r2) <= 1e-10
+
+
+_C2_EIGS = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from paper_2607_27440_b300 import klst, workloads as wl
+from tests.helpers import to_dev
+klst.load()
+spec, es = wl.c2()
+P = klst.Pencil(spec)
+F = P.factor(es.sigma, precision=0)
+om, _, res, info = F.eigs(es.nev, es.ncv, tol=1e-13, v0=to_dev(wl.start_vector(P.n, es.seed)))
+print(json.dumps({"re": om.real.tolist(), "im": om.imag.tolist(), "res": res.tolist(), "restarts": info["restarts"]}))
+"""
+
+
+def test_cluster_householder_matches_single_cta(klst):
+    """The restart's Householder reduction on a cluster of eight CTAs (default) and on one CTA
+    (KLST_NO_CLUSTER_HOUSE=1, read once per process, hence the child processes) give the same C2
+    eigenpairs to float64 rounding."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for flag in ("0", "1"):
+        env = dict(os.environ, KLST_NO_CLUSTER_HOUSE=flag)
+        r = subprocess.run([sys.executable, "-c", _C2_EIGS, root], capture_output=True, text=True, timeout=600, env=env)
+        assert r.returncode == 0, r.stderr[-2000:]
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        out.append((np.array(d["re"]) + 1j * np.array(d["im"]), np.array(d["res"]), d["restarts"]))
+    (o1, r1, k1), (o2, r2, k2) = out
+    assert k1 == k2
+    perm = eig.match(o2, o1)
+    assert np.max(np.abs(o1[perm] - o2) / np.abs(o2)) <= 1e-11
+    assert np.max(r1) <= 1e-10 and np.max(r2) <= 1e-10
