@@ -222,3 +222,19 @@ def test_cluster_householder_matches_single_cta(klst):
     perm = eig.match(o2, o1)
     assert np.max(np.abs(o1[perm] - o2) / np.abs(o2)) <= 1e-11
     assert np.max(r1) <= 1e-10 and np.max(r2) <= 1e-10
+
+
+def test_large_basis_against_interior_oracle(klst):
+    """ncv = 157 (near the ABI's 160, not a multiple of the Householder cluster's 8 CTAs): the 20
+    eigenvalues nearest sigma of a small pencil equal the oracle's interior eigenvalues."""
+    spec = wl.tiny(nx=24, qx=8, qy=6, beta=1.0, mach=2.0)
+    d = gas.pencil_data(spec.as_dict())
+    A, B = pencil.assemble_dense(spec.as_dict(), d)
+    lam, X, kap = eig.interior(A, pencil.boundary_rows(d))
+    sigma = 0.1 + 0.2j
+    idx = eig.nearest(lam, sigma, 20)
+    P = klst.Pencil(spec)
+    F = P.factor(sigma, precision=0)
+    om, _, res, info = F.eigs(20, 157, tol=1e-13, v0=to_dev(wl.start_vector(P.n, 4)))
+    _check_against(om, lam[idx], kap[idx], np.linalg.norm(A, "fro"))
+    assert np.max(res) <= 1e-10
