@@ -127,8 +127,9 @@ int gs_update_tc(const unsigned short* SL, int64_t n, const double2* h, double2*
                  int j, const int* jd, Status* st, cudaStream_t s);
 int gs_dots_tc(const unsigned short* SL, int64_t n, const double2* w, double2* part, int ldp, int j, const int* jd,
                Status* st, cudaStream_t s);
-void scale64_split(const double2* w, int64_t n, const double* beta, double2* V, double2* vcopy, int col,
-                   unsigned short* SL, float2* V32, const int* jd, int nblk, cudaStream_t s);
+void finish_scale64_split(const double2* h1, const double2* h2, const double* npart, int nparts, double2* S, int lds,
+                          double* beta, Status* st, const double2* w, int64_t n, double2* V, double2* vcopy, int col,
+                          unsigned short* SL, float2* V32, const int* jd, int nblk, cudaStream_t s);
 // vcol = vcopy = w / *beta (the first basis vector)
 void k_scale64_ext(const double2* w, int64_t n, const double* beta, double2* vcol, double2* vcopy, int64_t ldv,
                    int nblk, cudaStream_t s);

@@ -339,10 +339,10 @@ int orth64_step(const Orth64Args& a, int j, const int* jd, cudaStream_t s) {
         prof_end("orth_tc_dots2", s);
         prof_begin("orth_tc_update2", s);
         if ((rc = gs_update_tc(a.sl, a.n, a.h2, a.w, a.npart, true, j, jd, a.st, s)) != KLST_OK) return rc;
-        k_finish64<<<1, 256, 0, s>>>(a.h1, a.h2, a.npart, a.ntc, j, a.S, a.lds, a.beta, a.st, jd); note_launch();
         prof_end("orth_tc_update2", s);
-        prof_begin("orth_scale", s);
-        scale64_split(a.w, a.n, a.beta, a.V, a.vcur, j + 1, a.sl, a.v32, jd, a.nscale, s);
+        prof_begin("orth_scale", s);   // column j of S, beta and the new basis column in one launch
+        finish_scale64_split(a.h1, a.h2, a.npart, a.ntc, a.S, a.lds, a.beta, a.st, a.w, a.n, a.V, a.vcur, j + 1, a.sl,
+                             a.v32, jd, a.nscale, s);
         prof_end("orth_scale", s);
         KLST_CK_LAUNCH();
         return KLST_OK;

@@ -73,18 +73,48 @@ int split_basis(const double2* V, int64_t n, int c0, int c1, unsigned short* SL,
     return KLST_OK;
 }
 
-// v_{j+1} = w'' / beta into the basis, into vcur and into the slices (column jdev[0] + 1)
-__global__ void k_scale64_split(const double2* __restrict__ w, int64_t n, const double* __restrict__ beta,
-                                double2* __restrict__ V, double2* __restrict__ vcopy, int col,
-                                unsigned short* __restrict__ SL, float2* __restrict__ V32,
-                                const int* __restrict__ jdev) {
+// The end of an Arnoldi step in one launch (column j = col - 1):
+// - every CTA sums the second update's per-CTA partial norms in one fixed order, giving the same
+//   beta = ||w''|| in every CTA;
+// - CTA 0 writes column j of the Krylov-Schur matrix (S[0..j, j] = h1 + h2, S[j+1, j] = beta),
+//   beta_out and the breakdown test;
+// - every CTA writes v_{j+1} = w'' / beta into the basis, into vcur and into the slices.
+// Launched with 256 threads, so the sums follow the order of a separate 256-thread reduction.
+__global__ void __launch_bounds__(256) k_finish_scale64_split(
+    const double2* __restrict__ h1, const double2* __restrict__ h2, const double* __restrict__ npart, int nparts,
+    double2* __restrict__ S, int lds, double* __restrict__ beta_out, Status* st, const double2* __restrict__ w,
+    int64_t n, double2* __restrict__ V, double2* __restrict__ vcopy, int col, unsigned short* __restrict__ SL,
+    float2* __restrict__ V32, const int* __restrict__ jdev) {
     if (jdev) col = *jdev + 1;
+    const int j = col - 1;
+    __shared__ double red[2][32];
     __shared__ double s_inv;
-    if (threadIdx.x == 0) {
-        const double b = *beta;
-        s_inv = b > 0 ? 1.0 / b : 0.0;
+    {
+        double sn = 0.0, hn = 0.0;
+        for (int b = threadIdx.x; b < nparts; b += blockDim.x) sn += npart[b];
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+                const double2 hv = h1[i] + h2[i];
+                S[(size_t)j * lds + i] = hv;
+                hn += abs2(hv);
+            }
+        sn = warp_sum(sn);
+        hn = warp_sum(hn);
+        if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sn; red[1][threadIdx.x >> 5] = hn; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, hs = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; hs += red[1][q]; }
+            const double b = sqrt(a);
+            if (blockIdx.x == 0) {
+                if (!(b > 1e-13 * sqrt(hs))) atomicOr(&st->flags, ST_BREAKDOWN);
+                S[(size_t)j * lds + j + 1] = make_double2(b, 0.0);
+                *beta_out = b;
+            }
+            s_inv = b > 0 ? 1.0 / b : 0.0;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const double inv = s_inv;
     double2* vcol = V + (int64_t)col * n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -427,9 +457,10 @@ int gs_dots_tc(const unsigned short* SL, int64_t n, const double2* w, double2* p
     return KLST_OK;
 }
 
-void scale64_split(const double2* w, int64_t n, const double* beta, double2* V, double2* vcopy, int col,
-                   unsigned short* SL, float2* V32, const int* jd, int nblk, cudaStream_t s) {
-    k_scale64_split<<<nblk, 256, 0, s>>>(w, n, beta, V, vcopy, col, SL, V32, jd);
+void finish_scale64_split(const double2* h1, const double2* h2, const double* npart, int nparts, double2* S, int lds,
+                          double* beta, Status* st, const double2* w, int64_t n, double2* V, double2* vcopy, int col,
+                          unsigned short* SL, float2* V32, const int* jd, int nblk, cudaStream_t s) {
+    k_finish_scale64_split<<<nblk, 256, 0, s>>>(h1, h2, npart, nparts, S, lds, beta, st, w, n, V, vcopy, col, SL, V32, jd);
     note_launch();
 }
 
