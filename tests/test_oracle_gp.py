@@ -98,3 +98,21 @@ def test_gp_base_is_a_local_maxwellian_of_the_profile():
     up = x < -3.0
     assert np.max(np.abs(rho[up] / rho_p[up] - 1)) < 1e-12 and np.max(np.abs(u[up] / u_p[up] - 1)) < 1e-12
     assert np.allclose(h, 0.5 * T_p[:, None] * g, rtol=1e-14, atol=0)
+
+
+def test_prandtl_number_enters_as_the_printed_constant():
+    """The energy balance carries 1/Pr: at Pr = 2/3 the ratio of the balances in (Omega, theta) is the
+    printed dtheta/dOmega with its 8/15 = (4/5)(2/3), and at Pr = 1/2 the 2/5 of the printed
+    z-equations; the momentum balance does not depend on Pr."""
+    M = 3.0
+    m, P, H, _, (r2, u2, T2) = gp.constants(M)
+    alpha = 2.0 * H * m * m / (P * P) - 1.0
+    u, T = 0.5 * (gp.constants(M)[3][1] + u2), 0.5 * (1.0 + T2)   # a state inside the shock
+    for Pr, const in ((2.0 / 3.0, 8.0 / 15.0), (0.5, 0.4)):
+        du, dT = gp.rhs(u, T, M, 10.0, Pr=Pr)
+        du1, _ = gp.rhs(u, T, M, 10.0, Pr=1.0)
+        assert du == du1
+        Om, th = m / P * u, (m / P) ** 2 * 0.5 * T
+        ratio = ((m / P) ** 2 * 0.5 * dT) / (m / P * du)
+        printed = const * Om * (th - ((1.0 - Om) ** 2 + alpha) / 3.0) / (Om * Om - Om + th)
+        assert abs(ratio / printed - 1.0) < 1e-12
