@@ -248,14 +248,16 @@ struct SolvePolicy {
         }
     }
     __device__ void finish(unsigned char*, int quarter, int lane) const {
-        const int j = quarter * 32 + lane;
-        if (PASS != 1 || j >= a.nx) return;
+        if constexpr (PASS == 1) {
+            const int j = quarter * 32 + lane;
+            if (j >= a.nx) return;
 #pragma unroll
-        for (int rl = 0; rl < 2; ++rl) {
-            if (!(rl == 0 ? on0 : on1)) continue;
-            double2* tp = a.tpart + ((size_t)(r0 + rl) * a.ngroups + g) * 4 * a.nx + j;
+            for (int rl = 0; rl < 2; ++rl) {
+                if (!(rl == 0 ? on0 : on1)) continue;
+                double2* tp = a.tpart + ((size_t)(r0 + rl) * a.ngroups + g) * 4 * a.nx + j;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tp[q * a.nx] = acc[rl][q];
+                for (int q = 0; q < 4; ++q) tp[q * a.nx] = acc[rl][q];
+            }
         }
     }
 };
