@@ -129,3 +129,20 @@ def test_invalid_cases_and_options(klst):
     with pytest.raises(klst.KlstError) as ei:
         klst.Pencil(wl.tiny(nx=9, qx=4, qy=2, mach=3.0, base="gilbarg_paolucci", gamma=1.4))
     assert ei.value.code == klst.KLST_EINVAL
+
+
+def test_several_cases_with_points_keep_the_callers_order(klst, oracle_profiles):
+    """Cases given out of Mach order (the launch sorts them) with points: row c of the profile and
+    result c belong to case c."""
+    cases = [CASES[6], CASES[1], CASES[3]]   # M = 10, 1.2, 3
+    M, Re, s, Pr = (np.array(v) for v in zip(*cases))
+    x = np.linspace(-40.0, 40.0, 23)
+    res, prof = klst.gp_shock(M, Re, s, Pr, x=x)
+    got = prof.cpu().numpy()
+    for c, case in enumerate(cases):
+        p = oracle_profiles[case]
+        assert abs(res["delta"][c] / p["Delta"] - 1.0) <= 1e-9
+        rho, u, T = gp.base_at(case[0], case[1], x, s=case[2], Pr=case[3])
+        (r1, u1, T1), (r2, u2, T2) = gp.constants(case[0])[3:]
+        assert np.max(np.abs(got[1, c] - u)) <= 2e-8 * (u1 - u2)
+        assert np.max(np.abs(got[2, c] - T)) <= 2e-8 * (T2 - T1)
